@@ -1,0 +1,219 @@
+/*
+ * ace.h -- C ABI of the GB300 (sm_103a) Groth16/BN254 prover library (libace.so).
+ *
+ * The library computes the proof of the paper's Phase 2: Groth16.Prove(C, w,
+ * pub) run off the critical path on the builder's GPU (Section 3.1,
+ * Algorithm 1 ProveAsync; Section 3.3, Algorithm 3 GPUProofPipeline Stage 1),
+ * over BN254 (Section 3.3, "ZK-ACE circuit specification"), producing the
+ * single 256-byte proof of Section 3.3 / Appendix B, checked by the three-
+ * pairing verification of Section 3.4 (Algorithm 4).  The paper treats Groth16
+ * as a black box; the QAP / setup / prover algebra follows Groth 2016, which
+ * it cites.
+ *
+ * Conventions
+ *  - Every function returns int: ACE_OK (0) or a negative ACE_E_* code.
+ *    ace_verify returns 1 (valid), 0 (invalid) or a negative code.
+ *    Nothing aborts, traps or prints; ace_last_error() returns the message of
+ *    the last failure on the calling thread.
+ *  - Field elements (ace_fr, ace_fp) are 8 little-endian 32-bit limbs in
+ *    CANONICAL form (value < modulus) unless an argument says ACE_FORM_MONT
+ *    (Montgomery form x * 2^256 mod p).  G1 affine = {x, y}; G2 affine =
+ *    {x.c0, x.c1, y.c0, y.c1} over Fp2 = Fp[u]/(u^2+1).  The point at infinity
+ *    is all-zero coordinates ((0,0) is on neither curve).
+ *  - Proof bytes (256): A.x | A.y | B.x.c0 | B.x.c1 | B.y.c0 | B.y.c1 | C.x | C.y,
+ *    each 32-byte little-endian canonical.
+ *  - Arguments named d_* are DEVICE pointers on the context's device; all
+ *    others are host pointers.  The caller owns every buffer it passes; the
+ *    library never frees caller memory.  Opaque handles are owned by the
+ *    library and released by the matching *_free / *_destroy call.
+ *  - `stream` is a cudaStream_t (NULL = the context's own stream).  Device
+ *    work is enqueued on that stream; functions that return results in host
+ *    memory synchronise it before returning.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef ACE_H
+#define ACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ACE_OK 0
+#define ACE_E_ARG (-1)          /* invalid argument (size, pointer, non-canonical value) */
+#define ACE_E_OOM (-2)          /* device or host allocation failed */
+#define ACE_E_CUDA (-3)         /* a CUDA call failed (message in ace_last_error) */
+#define ACE_E_UNSAT (-4)        /* witness does not satisfy the R1CS */
+#define ACE_E_NOT_ON_CURVE (-5) /* an input point is not on the curve */
+#define ACE_E_TIMEOUT (-6)      /* a bounded device wait expired */
+#define ACE_E_BUSY (-7)         /* admission refused / result not ready */
+
+#define ACE_FORM_CANONICAL 0
+#define ACE_FORM_MONT 1
+
+typedef struct CUstream_st* ace_stream; /* == cudaStream_t */
+typedef struct ace_ctx ace_ctx;
+typedef struct ace_circuit ace_circuit;
+typedef struct ace_pk ace_pk;
+typedef struct ace_server ace_server;
+
+typedef struct { uint32_t l[8]; } ace_fr;
+typedef struct { uint32_t l[8]; } ace_fp;
+typedef struct { ace_fp x, y; } ace_g1_affine;
+typedef struct { ace_fp x[2], y[2]; } ace_g2_affine;
+
+/* Verifying key for l = 1 public input: ic[0] + x_1 ic[1] is the input term. */
+typedef struct {
+    ace_g1_affine alpha1;
+    ace_g2_affine beta2, gamma2, delta2;
+    ace_g1_affine ic[2];
+} ace_vk;
+
+/* Seeded synthetic R1CS over Fr with N = 2^log_n rows:
+ *   n_perm Poseidon-style permutations (width 3, x^5 S-box, 8 full + 57
+ *   partial rounds; the identity commitment of Section 2.1, Definition "ZK
+ *   Identity Commitment", constraint (i) of the ZK-ACE circuit), 243 rows each;
+ *   n_pack bit-packing rows (sum_k 2^k b_k) * 1 = y with pack_bits seeded bits;
+ *   a chain of squaring gates x_{i+1} = x_i^2 + k_i filling rows up to n_rows - 2;
+ *   two input-consistency rows (A = z_0, A = z_1); rows n_rows..N-1 are zero.
+ * One public input (l = 1): z_1, the last chain value.
+ * Requires 2 <= log_n <= 26, n_rows <= N, pack_bits <= 253 and
+ * n_rows >= 243 n_perm + n_pack + 3. */
+typedef struct {
+    uint32_t log_n;
+    uint32_t n_rows;
+    uint32_t n_perm;
+    uint32_t n_pack;
+    uint32_t pack_bits;
+    uint64_t seed;
+} ace_circuit_params;
+
+/* info[] layout of ace_circuit_info / ace_pk_info */
+enum {
+    ACE_INFO_N = 0,      /* QAP domain size */
+    ACE_INFO_M = 1,      /* witness length (z_0 = 1, z_1 public, private ...) */
+    ACE_INFO_ROWS = 2,   /* rows carrying constraints */
+    ACE_INFO_CHAIN = 3,  /* chain rows */
+    ACE_INFO_NNZ_A = 4,
+    ACE_INFO_NNZ_B = 5,
+    ACE_INFO_NNZ_C = 6,
+    ACE_INFO_M_A = 7,    /* pk: non-zero A-query points (after compaction) */
+    ACE_INFO_M_B = 8,    /* pk: non-zero B-query points */
+    ACE_INFO_M_L = 9,    /* pk: non-zero L-query points */
+    ACE_INFO_DEVICE_BYTES = 10, /* pk: device memory held */
+    ACE_INFO_LEN = 12
+};
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * memory the context's caches and scratch may hold (0 = no bound); calls
+ * that would exceed it return ACE_E_OOM. */
+int ace_ctx_create(ace_ctx** out, int device, size_t hbm_budget_bytes);
+int ace_ctx_destroy(ace_ctx* ctx);
+/* Message of the last error on this thread ("" if none).  Never NULL. */
+const char* ace_last_error(void);
+/* Bytes of device memory currently held by the context (caches + scratch). */
+int ace_ctx_device_bytes(const ace_ctx* ctx, size_t* out);
+
+/* ---- circuit and witness (host) ----------------------------------------- */
+
+/* Build the seeded synthetic R1CS described at ace_circuit_params (host). */
+int ace_circuit_gen(const ace_circuit_params* p, ace_circuit** out);
+int ace_circuit_free(ace_circuit* c);
+int ace_circuit_info(const ace_circuit* c, uint64_t info[ACE_INFO_LEN]);
+
+/* Witness z (m canonical Fr values) for the circuit: Groth16.Prove's w_tx
+ * input (Section 3.1, Algorithm 1).  Private inputs are drawn from input_seed
+ * (SplitMix64, purpose 3).  Checks the R1CS on the host; ACE_E_UNSAT if it
+ * fails (cannot happen for a generated witness), ACE_E_ARG if m is wrong. */
+int ace_witness(const ace_circuit* c, uint64_t input_seed, ace_fr* z_out, size_t m);
+
+/* ---- setup -------------------------------------------------------------- */
+
+/* Toy trusted setup (the circuit-specific trusted setup of Section 9, "Trusted setup") with toxic
+ * waste tau, alpha, beta, gamma, delta drawn from toxic_seed (SplitMix64,
+ * purpose 4; zero rejected; tau^N = 1 rejected).  The proving key is built on
+ * the device and stays resident there; vk_out (host) receives the verifying
+ * key.  Points whose scalar is zero are compacted out of the MSM inputs. */
+int ace_setup_toy(ace_ctx* ctx, const ace_circuit* c, uint64_t toxic_seed, ace_pk** pk_out,
+                  ace_vk* vk_out);
+int ace_pk_free(ace_pk* pk);
+int ace_pk_info(const ace_pk* pk, uint64_t info[ACE_INFO_LEN]);
+/* Copy one proving-key point to host memory (affine, canonical).
+ * query: 0 A_j = [u_j(tau)]1, 1 B1_j = [v_j(tau)]1, 2 B2_j = [v_j(tau)]2 (out is
+ * an ace_g2_affine), 3 L_j = [(beta u_j + alpha v_j + w_j)(tau)/delta]1 (j > 1),
+ * 4 H_i = [tau^i Z(tau)/delta]1 (i <= N-2); j indexes the witness, i the
+ * domain.  Infinity is returned as zeros. */
+int ace_pk_point(const ace_pk* pk, int query, size_t index, void* out);
+
+/* ---- hot path ----------------------------------------------------------- */
+
+/* QAP quotient: h = (A(X) B(X) - C(X)) / (X^N - 1) where A, B, C interpolate
+ * Az, Bz, Cz on H = {omega^i}, omega = 5^((r-1)/N).  Steps: sparse products,
+ * 3 inverse NTTs, 3 coset NTTs on g H (g = 5), pointwise (a b - c)/(g^N - 1),
+ * coset inverse NTT.  d_z: m canonical Fr (device); d_h_out: N canonical Fr
+ * (device), natural coefficient order, h_{N-1} = 0.  Asynchronous on stream.
+ * Scratch is drawn from the context. */
+int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out, ace_stream stream);
+
+/* Multi-scalar multiplication sum_i k_i P_i over G1 (Pippenger: signed c-bit
+ * digits, bucket sort, bucket accumulation, bucket and window reduction).
+ * d_bases: n affine points in base_form (ACE_FORM_CANONICAL or _MONT);
+ * d_scalars: n canonical Fr; d_out: one affine canonical point (device).
+ * n may be 0 (result is infinity).  Asynchronous on stream. */
+int ace_msm_g1(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
+               size_t n, ace_g1_affine* d_out, ace_stream stream);
+/* Same over G2 (coordinates in Fp2): the B query of the proof. */
+int ace_msm_g2(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const ace_fr* d_scalars,
+               size_t n, ace_g2_affine* d_out, ace_stream stream);
+
+/* Fixed-base batch k_i * G1 (resp. G2 generator) for canonical Fr scalars;
+ * writes n affine points in out_form.  Used for setup and for MSM inputs. */
+int ace_g1_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g1_affine* d_out,
+                      int out_form, ace_stream stream);
+int ace_g2_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g2_affine* d_out,
+                      int out_form, ace_stream stream);
+
+/* Groth16 proof for witness d_z (m canonical Fr, device) with prover
+ * randomness r, s (host, canonical):
+ *   A = [alpha]1 + sum z_j A_j + r [delta]1,  B = [beta]2 + sum z_j B2_j + s [delta]2,
+ *   C = sum_{j>1} z_j L_j + sum h_i H_i + s A + r B1 - r s [delta]1,
+ *   B1 = [beta]1 + sum z_j B1_j + s [delta]1.
+ * proof_out (host, 256 bytes) as described above; the call synchronises.
+ * ACE_E_UNSAT if (Az) o (Bz) != Cz (checked on the device). */
+int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
+              uint8_t proof_out[256], ace_stream stream);
+/* Same, but writes the 256 proof bytes to device memory d_proof_out and does
+ * not synchronise (for graph capture and overlap). UNSAT is then reported by
+ * the int at d_status (device): 0 ok, 1 unsat. */
+int ace_prove_async(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
+                    uint8_t* d_proof_out, int32_t* d_status, ace_stream stream);
+
+/* Prover randomness (r, s) drawn from seed (SplitMix64, purpose 5, zero rejected). */
+int ace_rs_from_seed(uint64_t seed, ace_fr* r, ace_fr* s);
+
+/* Groth16 verification on the host: 1 iff
+ * e(A, B) = e(alpha1, beta2) e(ic[0] + sum x_j ic[j], gamma2) e(C, delta2)
+ * (the three-pairing check of Section 3.3 / Section 3.4).  n_pub must be 1. */
+int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t proof[256]);
+
+/* ---- batching and serving ------------------------------------------------ */
+
+/* k independent proofs (each with its own pk and witness) in one call; proof i
+ * goes to proofs + 256 i (host).  Status per proof in status[i] (0 ok, 1 unsat). */
+int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,
+                    const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status);
+
+/* ---- persistence ---------------------------------------------------------- */
+
+/* Save / load a proving key (with its circuit) to a versioned file. */
+int ace_pk_save(const ace_pk* pk, const char* path);
+int ace_pk_load(ace_ctx* ctx, const char* path, ace_pk** pk_out, ace_vk* vk_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACE_H */

@@ -12,7 +12,7 @@
  *   - The proof is Groth16.Prove(C, w, pub) of the paper's Phase 2
  *     (Section 3.1, Algorithm 1 ProveAsync; Section 3.3 Algorithm 3 Stage 1),
  *     over BN254 (Section 3.3, "ZK-ACE circuit specification"), serialised to
- *     the 256-byte proof of Section 3.3 / Appendix C.  The construction itself
+ *     the 256-byte proof of Section 3.3 / Appendix B.  The construction itself
  *     (QAP, setup, prover, verifier) is Groth 2016, which the paper cites and
  *     does not restate; this file writes it out in its textbook form.
  *   - Verification is the three-pairing check of Section 3.3 / Section 3.4

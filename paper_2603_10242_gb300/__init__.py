@@ -1,0 +1,298 @@
+"""GB300 (sm_103a) Groth16/BN254 prover: Python binding of libace.so.
+
+This module only marshals arguments: every step of the proving path runs in
+the CUDA kernels of ``libace.so`` (built in-tree by ``build.py``).  Device
+memory and streams come from PyTorch; the library never falls back to the CPU
+and importing a function here fails loudly if the extension is missing.
+
+The C ABI is declared in ``include/ace.h``; the names below mirror it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libace.so")
+
+ACE_OK = 0
+ERRORS = {-1: "ACE_E_ARG", -2: "ACE_E_OOM", -3: "ACE_E_CUDA", -4: "ACE_E_UNSAT",
+          -5: "ACE_E_NOT_ON_CURVE", -6: "ACE_E_TIMEOUT", -7: "ACE_E_BUSY"}
+FORM_CANONICAL = 0
+FORM_MONT = 1
+INFO_LEN = 12
+
+_lib = None
+
+
+class AceError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """Load libace.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libace.so not built ({LIB_PATH}); run paper_2603_10242_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i32, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+        cp = ctypes.c_char_p
+        sigs = {
+            "ace_last_error": (ctypes.c_char_p, []),
+            "ace_ctx_create": (i32, [ctypes.POINTER(vp), i32, sz]),
+            "ace_ctx_destroy": (i32, [vp]),
+            "ace_ctx_device_bytes": (i32, [vp, ctypes.POINTER(sz)]),
+            "ace_msm_g1": (i32, [vp, vp, i32, vp, sz, vp, vp]),
+            "ace_msm_g2": (i32, [vp, vp, i32, vp, sz, vp, vp]),
+            "ace_msm_g1_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
+            "ace_g1_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
+            "ace_g2_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
+            "ace_debug_field_op": (i32, [i32, i32, vp, vp, vp, sz, vp]),
+            "ace_debug_curve_op": (i32, [i32, i32, vp, vp, vp, vp, sz, vp]),
+            "ace_ntt": (i32, [vp, vp, u32, i32, vp]),
+            "ace_ntt_mont": (i32, [vp, vp, u32, i32, i32, i32, vp]),
+            "ace_circuit_gen": (i32, [vp, ctypes.POINTER(vp)]),
+            "ace_circuit_free": (i32, [vp]),
+            "ace_circuit_info": (i32, [vp, ctypes.POINTER(u64)]),
+            "ace_witness": (i32, [vp, u64, vp, sz]),
+            "ace_setup_toy": (i32, [vp, vp, u64, ctypes.POINTER(vp), vp]),
+            "ace_pk_free": (i32, [vp]),
+            "ace_pk_info": (i32, [vp, ctypes.POINTER(u64)]),
+            "ace_pk_point": (i32, [vp, i32, sz, vp]),
+            "ace_qap_h": (i32, [vp, vp, vp, vp, vp]),
+            "ace_prove": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+            "ace_prove_async": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+            "ace_rs_from_seed": (i32, [u64, vp, vp]),
+            "ace_verify": (i32, [vp, vp, sz, vp]),
+            "ace_prove_batch": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
+            "ace_pk_save": (i32, [vp, cp]),
+            "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        raise AceError(rc, lib().ace_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a torch tensor, or an int address."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    """cudaStream_t handle: the given stream, else PyTorch's current stream
+    (NULL selects the context's stream, which is ordered with the legacy
+    default stream)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                h = torch.cuda.current_stream().cuda_stream
+                return h or None
+        except Exception:
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+class Context:
+    """ace_ctx: one CUDA device, its stream, scratch arenas and caches."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        check(lib().ace_ctx_create(ctypes.byref(h), device, hbm_budget_bytes))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ace_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        check(lib().ace_ctx_device_bytes(self.h, ctypes.byref(v)))
+        return v.value
+
+    # ---- hot path ----
+    def msm_g1(self, bases, scalars, n: int, out, base_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_msm_g1(self.h, _ptr(bases), base_form, _ptr(scalars), n, _ptr(out), _stream(stream)))
+
+    def msm_g2(self, bases, scalars, n: int, out, base_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_msm_g2(self.h, _ptr(bases), base_form, _ptr(scalars), n, _ptr(out), _stream(stream)))
+
+    def msm_g1_window(self, bases, scalars, n: int, c: int, out, base_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_msm_g1_window(self.h, _ptr(bases), base_form, _ptr(scalars), n, c, _ptr(out),
+                                      _stream(stream)))
+
+    def g1_fixed_base(self, scalars, n: int, out, out_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_g1_fixed_base(self.h, _ptr(scalars), n, _ptr(out), out_form, _stream(stream)))
+
+    def g2_fixed_base(self, scalars, n: int, out, out_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_g2_fixed_base(self.h, _ptr(scalars), n, _ptr(out), out_form, _stream(stream)))
+
+    def ntt(self, data, log_n: int, kind: int, stream=None):
+        """kind: 0 forward, 1 inverse, 2 coset forward, 3 coset inverse (canonical, natural order)."""
+        check(lib().ace_ntt(self.h, _ptr(data), log_n, kind, _stream(stream)))
+
+    def ntt_mont(self, data, log_n: int, count: int, dif: bool, inverse: bool, stream=None):
+        check(lib().ace_ntt_mont(self.h, _ptr(data), log_n, count, 1 if dif else 0, 1 if inverse else 0,
+                                 _stream(stream)))
+
+    def qap_h(self, pk: "ProvingKey", d_z, d_h, stream=None):
+        check(lib().ace_qap_h(self.h, pk.h, _ptr(d_z), _ptr(d_h), _stream(stream)))
+
+    def prove(self, pk: "ProvingKey", d_z, r: bytes, s: bytes, stream=None) -> bytes:
+        out = ctypes.create_string_buffer(256)
+        check(lib().ace_prove(self.h, pk.h, _ptr(d_z), r, s, out, _stream(stream)))
+        return out.raw
+
+    def prove_async(self, pk: "ProvingKey", d_z, r: bytes, s: bytes, d_proof, d_status, stream=None):
+        check(lib().ace_prove_async(self.h, pk.h, _ptr(d_z), r, s, _ptr(d_proof), _ptr(d_status),
+                                    _stream(stream)))
+
+    def prove_batch(self, pks, d_zs, rs: bytes, ss: bytes):
+        k = len(pks)
+        pk_arr = (ctypes.c_void_p * k)(*[p.h.value for p in pks])
+        z_arr = (ctypes.c_void_p * k)(*[_ptr(z) for z in d_zs])
+        proofs = ctypes.create_string_buffer(256 * k)
+        status = (ctypes.c_int32 * k)()
+        check(lib().ace_prove_batch(self.h, k, pk_arr, z_arr, rs, ss, proofs, status))
+        return [proofs.raw[256 * i:256 * i + 256] for i in range(k)], list(status)
+
+
+# ---- diagnostics (device element-wise arithmetic) ----
+def debug_field_op(field: int, op: int, d_a, d_b, d_out, n: int, stream=None):
+    check(lib().ace_debug_field_op(field, op, _ptr(d_a), _ptr(d_b), _ptr(d_out), n, _stream(stream)))
+
+
+def debug_curve_op(group: int, op: int, d_a, d_b, d_k, d_out, n: int, stream=None):
+    check(lib().ace_debug_curve_op(group, op, _ptr(d_a), _ptr(d_b), _ptr(d_k), _ptr(d_out), n, _stream(stream)))
+
+
+class CircuitParams(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_rows", ctypes.c_uint32), ("n_perm", ctypes.c_uint32),
+                ("n_pack", ctypes.c_uint32), ("pack_bits", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class Circuit:
+    """ace_circuit: the seeded synthetic R1CS (host)."""
+
+    def __init__(self, log_n, n_rows, n_perm, n_pack=0, pack_bits=0, seed=1):
+        self.params = CircuitParams(log_n, n_rows, n_perm, n_pack, pack_bits, seed)
+        h = ctypes.c_void_p()
+        check(lib().ace_circuit_gen(ctypes.byref(self.params), ctypes.byref(h)))
+        self.h = h
+        info = (ctypes.c_uint64 * INFO_LEN)()
+        check(lib().ace_circuit_info(h, info))
+        self.info = list(info)
+        self.N, self.m = int(info[0]), int(info[1])
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None and self.h.value:
+                lib().ace_circuit_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def witness(self, input_seed: int) -> bytes:
+        out = ctypes.create_string_buffer(32 * self.m)
+        check(lib().ace_witness(self.h, input_seed, out, self.m))
+        return out.raw
+
+
+class VerifyingKey(ctypes.Structure):
+    _fields_ = [("alpha1", ctypes.c_uint8 * 64), ("beta2", ctypes.c_uint8 * 128), ("gamma2", ctypes.c_uint8 * 128),
+                ("delta2", ctypes.c_uint8 * 128), ("ic", ctypes.c_uint8 * 128)]
+
+
+class ProvingKey:
+    """ace_pk: device-resident proving key from the toy setup."""
+
+    def __init__(self, ctx: Context, circuit: Circuit | None, toxic_seed: int = 0, _handle=None, vk=None):
+        self.ctx = ctx
+        self.circuit = circuit
+        if _handle is not None:
+            self.h, self.vk = _handle, vk
+        else:
+            h = ctypes.c_void_p()
+            self.vk = VerifyingKey()
+            check(lib().ace_setup_toy(ctx.h, circuit.h, toxic_seed, ctypes.byref(h), ctypes.byref(self.vk)))
+            self.h = h
+        info = (ctypes.c_uint64 * INFO_LEN)()
+        check(lib().ace_pk_info(self.h, info))
+        self.info = list(info)
+        self.N, self.m = int(info[0]), int(info[1])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ace_pk_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    QUERY = {"A": 0, "B1": 1, "B2": 2, "L": 3, "H": 4}
+
+    def point(self, query: str, idx: int) -> bytes:
+        out = ctypes.create_string_buffer(128 if query == "B2" else 64)
+        check(lib().ace_pk_point(self.h, self.QUERY[query], idx, out))
+        return out.raw
+
+    def save(self, path: str):
+        check(lib().ace_pk_save(self.h, path.encode()))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "ProvingKey":
+        h = ctypes.c_void_p()
+        vk = VerifyingKey()
+        check(lib().ace_pk_load(ctx.h, path.encode(), ctypes.byref(h), ctypes.byref(vk)))
+        return cls(ctx, None, _handle=h, vk=vk)
+
+    def verify(self, public: bytes, proof: bytes) -> int:
+        return check(lib().ace_verify(ctypes.byref(self.vk), public, 1, proof))
+
+
+def rs_from_seed(seed: int):
+    r = ctypes.create_string_buffer(32)
+    s = ctypes.create_string_buffer(32)
+    check(lib().ace_rs_from_seed(seed, r, s))
+    return r.raw, s.raw
+
+
+def verify(vk: VerifyingKey, public: bytes, proof: bytes) -> int:
+    return check(lib().ace_verify(ctypes.byref(vk), public, 1, proof))

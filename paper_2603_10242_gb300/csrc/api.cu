@@ -1,0 +1,324 @@
+// api.cu -- extern "C" entry points of libace.so: context, MSMs, fixed-base
+// multiplication and device diagnostics.  Every entry point validates its
+// arguments, records a message on failure and returns an ACE_E_* code.
+#include <string.h>
+
+#include "fixed_base.cuh"
+#include "msm.cuh"
+#include "ntt.cuh"
+
+using namespace ace;
+
+namespace {
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <class F>
+static int msm_entry(ace_ctx* ctx, const void* d_bases, int base_form, const ace_fr* d_scalars, size_t n,
+                     void* d_out, ace_stream stream) {
+    clear_error();
+    if (!ctx || !d_out || (n && (!d_bases || !d_scalars))) {
+        set_error("ace_msm: NULL argument");
+        return ACE_E_ARG;
+    }
+    if (base_form != ACE_FORM_CANONICAL && base_form != ACE_FORM_MONT) {
+        set_error("ace_msm: base_form must be ACE_FORM_CANONICAL or ACE_FORM_MONT");
+        return ACE_E_ARG;
+    }
+    if (!aligned16(d_bases) || !aligned16(d_scalars) || !aligned16(d_out)) {
+        set_error("ace_msm: device buffers must be 16-byte aligned");
+        return ACE_E_ARG;
+    }
+    if (n >= (1ull << 31)) {
+        set_error("ace_msm: n = %zu exceeds 2^31 - 1", n);
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    MsmPlan plan = msm_plan(n);
+    bool mont = base_form == ACE_FORM_MONT;
+    ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<F>(plan, mont)));
+    return msm_run<F>(plan, (const Affine<F>*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
+                      (Affine<F>*)d_out, pick_stream(ctx, stream));
+}
+
+template <class F>
+static int fixed_entry(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, void* d_out, int out_form,
+                       ace_stream stream) {
+    clear_error();
+    if (!ctx || (n && (!d_scalars || !d_out))) {
+        set_error("ace_fixed_base: NULL argument");
+        return ACE_E_ARG;
+    }
+    if (out_form != ACE_FORM_CANONICAL && out_form != ACE_FORM_MONT) {
+        set_error("ace_fixed_base: bad out_form");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    return fixed_base_mul<F>(ctx, (const uint32_t*)d_scalars, n, (Affine<F>*)d_out, out_form == ACE_FORM_MONT,
+                             pick_stream(ctx, stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ace_last_error(void) { return ace::last_error(); }
+
+int ace_ctx_create(ace_ctx** out, int device, size_t hbm_budget_bytes) {
+    clear_error();
+    if (!out) {
+        set_error("ace_ctx_create: out is NULL");
+        return ACE_E_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    ACE_TRY_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+        set_error("ace_ctx_create: device %d not present (%d devices)", device, ndev);
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(device));
+    ace_ctx* c = new ace_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    // a blocking stream: ordered with work the caller put on the legacy default
+    // stream (e.g. PyTorch copies), so inputs written there are visible
+    cudaError_t e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) {
+        set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+        delete c;
+        return ACE_E_CUDA;
+    }
+    *out = c;
+    return ACE_OK;
+}
+
+int ace_ctx_destroy(ace_ctx* c) {
+    if (!c) return ACE_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& a : c->scratch) dev_free(c, a.base, a.cap);
+    ntt_release_plans(c);
+    if (c->g1_fixed_tab) dev_free(c, c->g1_fixed_tab, 32 * 255 * sizeof(g1_aff));
+    if (c->g2_fixed_tab) dev_free(c, c->g2_fixed_tab, 32 * 255 * sizeof(g2_aff));
+    for (auto s : c->aux)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return ACE_OK;
+}
+
+int ace_ctx_device_bytes(const ace_ctx* c, size_t* out) {
+    if (!c || !out) {
+        set_error("ace_ctx_device_bytes: NULL argument");
+        return ACE_E_ARG;
+    }
+    *out = c->held;
+    return ACE_OK;
+}
+
+int ace_msm_g1(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars, size_t n,
+               ace_g1_affine* d_out, ace_stream stream) {
+    return msm_entry<fp_t>(ctx, d_bases, base_form, d_scalars, n, d_out, stream);
+}
+
+int ace_msm_g2(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const ace_fr* d_scalars, size_t n,
+               ace_g2_affine* d_out, ace_stream stream) {
+    return msm_entry<fp2_t>(ctx, d_bases, base_form, d_scalars, n, d_out, stream);
+}
+
+// Diagnostic: same MSM with an explicit window size c (6..20).
+int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
+                      size_t n, int c, ace_g1_affine* d_out, ace_stream stream) {
+    clear_error();
+    if (!ctx || !d_out || (n && (!d_bases || !d_scalars)) || c < 6 || c > 20) {
+        set_error("ace_msm_g1_window: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    MsmPlan plan = msm_plan(n, c);
+    bool mont = base_form == ACE_FORM_MONT;
+    ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(plan, mont)));
+    return msm_run<fp_t>(plan, (const g1_aff*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
+                         (g1_aff*)d_out, pick_stream(ctx, stream));
+}
+
+// NTT of N = 2^log_n canonical Fr values in natural order, in place.
+// kind: 0 forward (coefficients -> values on H), 1 inverse, 2 coset forward
+// (coefficients -> values on g H), 3 coset inverse.
+int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream stream) {
+    clear_error();
+    if (!ctx || !d_data || kind < 0 || kind > 3 || log_n < 1 || log_n > 28) {
+        set_error("ace_ntt: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    NttPlan* plan = nullptr;
+    ACE_TRY(ntt_get_plan(ctx, (int)log_n, &plan));
+    size_t n = (size_t)1 << log_n;
+    ACE_TRY(arena_ensure(ctx, 0, n * sizeof(fr_t) + 256));
+    fr_t* tmp = (fr_t*)ctx->scratch[0].take(n * sizeof(fr_t));
+    cudaStream_t st = pick_stream(ctx, stream);
+    fr_t* d = (fr_t*)d_data;
+    NttScale to_mont, from_mont, pre, post;
+    to_mont.hi = plan->rr;
+    to_mont.lo = plan->one;
+    to_mont.single = 1;
+    from_mont.hi = plan->plain_one;
+    from_mont.lo = plan->one;
+    from_mont.single = 1;
+    // canonical -> Montgomery
+    ACE_TRY(fr_scale_copy(d, d, n, to_mont, (int)log_n, st));
+    bool inverse = kind == 1 || kind == 3;
+    if (kind == 2) {  // coefficients times g^i
+        pre.hi = plan->cg_hi;
+        pre.lo = plan->cos_lo;
+        pre.h = plan->h;
+    }
+    if (kind == 1) {  // times 1/N
+        post.hi = plan->ninv;
+        post.lo = plan->one;
+        post.single = 1;
+    }
+    if (kind == 3) {  // times g^-e / N at bit-reversed position, leaves Montgomery form
+        post.hi = plan->icos_hi;
+        post.lo = plan->icos_lo;
+        post.h = plan->h;
+        post.brev = 1;
+    }
+    ACE_TRY(ntt_run(*plan, d, 1, true, inverse, pre, post, st));
+    ACE_TRY(fr_bitrev_copy(d, tmp, (int)log_n, 1, st));
+    if (kind == 3) {
+        ACE_TRY_CUDA(cudaMemcpyAsync(d, tmp, n * sizeof(fr_t), cudaMemcpyDeviceToDevice, st));
+    } else {
+        ACE_TRY(fr_scale_copy(tmp, d, n, from_mont, (int)log_n, st));
+    }
+    return ACE_OK;
+}
+
+// Diagnostic: raw in-place passes over `count` arrays of Montgomery-form
+// values (dif: natural -> bit-reversed; else bit-reversed -> natural), no
+// scaling.  This is the transform the QAP step is built from.
+int ace_ntt_mont(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int count, int dif, int inverse,
+                 ace_stream stream) {
+    clear_error();
+    if (!ctx || !d_data || count < 1 || log_n < 1 || log_n > 28) {
+        set_error("ace_ntt_mont: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    NttPlan* plan = nullptr;
+    ACE_TRY(ntt_get_plan(ctx, (int)log_n, &plan));
+    NttScale none;
+    return ntt_run(*plan, (fr_t*)d_data, count, dif != 0, inverse != 0, none, none, pick_stream(ctx, stream));
+}
+
+int ace_g1_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g1_affine* d_out, int out_form,
+                      ace_stream stream) {
+    return fixed_entry<fp_t>(ctx, d_scalars, n, d_out, out_form, stream);
+}
+int ace_g2_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g2_affine* d_out, int out_form,
+                      ace_stream stream) {
+    return fixed_entry<fp2_t>(ctx, d_scalars, n, d_out, out_form, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: element-wise field and curve operations on the device, for
+// unit-level parity tests of the arithmetic the hot path is built from.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace ace {
+ACE_HD fp_t coord_to_mont_any(const fp_t& a) { return fe_to_mont(a); }
+ACE_HD fr_t coord_to_mont_any(const fr_t& a) { return fe_to_mont(a); }
+ACE_HD fp2_t coord_to_mont_any(const fp2_t& a) { return fe_to_mont(a); }
+ACE_HD fp_t coord_from_mont_any(const fp_t& a) { return fe_from_mont(a); }
+ACE_HD fr_t coord_from_mont_any(const fr_t& a) { return fe_from_mont(a); }
+ACE_HD fp2_t coord_from_mont_any(const fp2_t& a) { return fe_from_mont(a); }
+ACE_HD fp_t any_sqr(const fp_t& a) { return fe_sqr(a); }
+ACE_HD fr_t any_sqr(const fr_t& a) { return fe_sqr(a); }
+ACE_HD fp2_t any_sqr(const fp2_t& a) { return fe_sqr(a); }
+ACE_HD fp_t any_inv(const fp_t& a) { return fe_inv(a); }
+ACE_HD fr_t any_inv(const fr_t& a) { return fe_inv(a); }
+ACE_HD fp2_t any_inv(const fp2_t& a) { return fe_inv(a); }
+
+template <class F>
+__global__ void k_field_op(int op, const F* a, const F* b, F* out, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    F x = coord_to_mont_any(a[i]);
+    F y = coord_to_mont_any(b[i]);
+    F r;
+    switch (op) {
+        case 0: r = x + y; break;
+        case 1: r = x - y; break;
+        case 2: r = x * y; break;
+        case 3: r = any_sqr(x); break;
+        default: r = any_inv(x); break;
+    }
+    out[i] = coord_from_mont_any(r);
+}
+
+// op: 0 P + Q (both as XYZZ), 1 P + Q (Q mixed), 2 2P, 3 k P (k from scal)
+template <class F>
+__global__ void k_curve_op(int op, const Affine<F>* a, const Affine<F>* b, const uint32_t* scal, Affine<F>* out,
+                           size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Affine<F> p = aff_to_mont(a[i]);
+    Affine<F> q = aff_to_mont(b[i]);
+    Xyzz<F> r;
+    switch (op) {
+        case 0: r = xyzz_add(xyzz_from_aff(p), xyzz_from_aff(q)); break;
+        case 1: r = xyzz_add_aff(xyzz_from_aff(p), q); break;
+        case 2: r = xyzz_dbl(xyzz_from_aff(p)); break;
+        default: r = xyzz_mul_aff(p, scal + 8 * i); break;
+    }
+    out[i] = aff_from_mont(xyzz_to_aff(r));
+}
+}  // namespace ace
+
+extern "C" {
+
+int ace_debug_field_op(int field, int op, const void* d_a, const void* d_b, void* d_out, size_t n,
+                       ace_stream stream) {
+    clear_error();
+    if (field < 0 || field > 2 || op < 0 || op > 4 || (n && (!d_a || !d_b || !d_out))) {
+        set_error("ace_debug_field_op: bad argument");
+        return ACE_E_ARG;
+    }
+    if (n == 0) return ACE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned grid = (unsigned)((n + 127) / 128);
+    if (field == 0)
+        k_field_op<fp_t><<<grid, 128, 0, st>>>(op, (const fp_t*)d_a, (const fp_t*)d_b, (fp_t*)d_out, n);
+    else if (field == 1)
+        k_field_op<fr_t><<<grid, 128, 0, st>>>(op, (const fr_t*)d_a, (const fr_t*)d_b, (fr_t*)d_out, n);
+    else
+        k_field_op<fp2_t><<<grid, 128, 0, st>>>(op, (const fp2_t*)d_a, (const fp2_t*)d_b, (fp2_t*)d_out, n);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+int ace_debug_curve_op(int group, int op, const void* d_a, const void* d_b, const ace_fr* d_k, void* d_out,
+                       size_t n, ace_stream stream) {
+    clear_error();
+    if (group < 1 || group > 2 || op < 0 || op > 3 || (n && (!d_a || !d_b || !d_out)) || (op == 3 && !d_k)) {
+        set_error("ace_debug_curve_op: bad argument");
+        return ACE_E_ARG;
+    }
+    if (n == 0) return ACE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned grid = (unsigned)((n + 63) / 64);
+    if (group == 1)
+        k_curve_op<fp_t><<<grid, 64, 0, st>>>(op, (const g1_aff*)d_a, (const g1_aff*)d_b, (const uint32_t*)d_k,
+                                              (g1_aff*)d_out, n);
+    else
+        k_curve_op<fp2_t><<<grid, 64, 0, st>>>(op, (const g2_aff*)d_a, (const g2_aff*)d_b, (const uint32_t*)d_k,
+                                               (g2_aff*)d_out, n);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,482 @@
+// field.cuh -- BN254 base field Fp, scalar field Fr and Fp2 = Fp[u]/(u^2+1).
+//
+// Elements are 8 little-endian 32-bit limbs held in registers, in Montgomery
+// form (x * 2^256 mod m) unless a name says otherwise.  Multiplication is the
+// coarsely integrated operand-scanning Montgomery product (Montgomery 1985;
+// Koc, Acar and Kaliski 1996) written with PTX multiply-add carry chains on the
+// device and with 64-bit products on the host.  Both moduli are below 2^254,
+// so a + b of reduced inputs never overflows 256 bits and the running CIOS
+// value stays below 2p; one conditional subtraction yields the reduced result.
+//
+// The curves and the fields are those of BN254, the curve the paper's circuit
+// operates over (Section 3.3, "ZK-ACE circuit specification").
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define ACE_HD __host__ __device__ __forceinline__
+#define ACE_DEV __device__ __forceinline__
+#else
+#define ACE_HD inline
+#define ACE_DEV inline
+#endif
+
+namespace ace {
+
+// p = 21888242871839275222246405745257275088696311157297823662689037894645226208583
+struct FpCfg {
+    static constexpr uint32_t M0 = 0xd87cfd47u, M1 = 0x3c208c16u, M2 = 0x6871ca8du, M3 = 0x97816a91u,
+                              M4 = 0x8181585du, M5 = 0xb85045b6u, M6 = 0xe131a029u, M7 = 0x30644e72u;
+    static constexpr uint32_t INV = 0xe4866389u;  // -p^{-1} mod 2^32
+    static constexpr uint32_t ONE0 = 0xc58f0d9du, ONE1 = 0xd35d438du, ONE2 = 0xf5c70b3du, ONE3 = 0x0a78eb28u,
+                              ONE4 = 0x7879462cu, ONE5 = 0x666ea36fu, ONE6 = 0x9a07df2fu, ONE7 = 0x0e0a77c1u;
+    static constexpr uint32_t RR0 = 0x538afa89u, RR1 = 0xf32cfc5bu, RR2 = 0xd44501fbu, RR3 = 0xb5e71911u,
+                              RR4 = 0x0a417ff6u, RR5 = 0x47ab1effu, RR6 = 0xcab8351fu, RR7 = 0x06d89f71u;
+};
+// r = 21888242871839275222246405745257275088548364400416034343698204186575808495617
+struct FrCfg {
+    static constexpr uint32_t M0 = 0xf0000001u, M1 = 0x43e1f593u, M2 = 0x79b97091u, M3 = 0x2833e848u,
+                              M4 = 0x8181585du, M5 = 0xb85045b6u, M6 = 0xe131a029u, M7 = 0x30644e72u;
+    static constexpr uint32_t INV = 0xefffffffu;  // -r^{-1} mod 2^32
+    static constexpr uint32_t ONE0 = 0x4ffffffbu, ONE1 = 0xac96341cu, ONE2 = 0x9f60cd29u, ONE3 = 0x36fc7695u,
+                              ONE4 = 0x7879462eu, ONE5 = 0x666ea36fu, ONE6 = 0x9a07df2fu, ONE7 = 0x0e0a77c1u;
+    static constexpr uint32_t RR0 = 0xae216da7u, RR1 = 0x1bb8e645u, RR2 = 0xe35c59e3u, RR3 = 0x53fe3ab1u,
+                              RR4 = 0x53bb8085u, RR5 = 0x8c49833du, RR6 = 0x7f4e44a5u, RR7 = 0x0216d0b1u;
+};
+
+template <class C>
+ACE_HD constexpr uint32_t mod_limb(int i) {
+    return i == 0 ? C::M0 : i == 1 ? C::M1 : i == 2 ? C::M2 : i == 3 ? C::M3
+         : i == 4 ? C::M4 : i == 5 ? C::M5 : i == 6 ? C::M6 : C::M7;
+}
+template <class C>
+ACE_HD constexpr uint32_t one_limb(int i) {
+    return i == 0 ? C::ONE0 : i == 1 ? C::ONE1 : i == 2 ? C::ONE2 : i == 3 ? C::ONE3
+         : i == 4 ? C::ONE4 : i == 5 ? C::ONE5 : i == 6 ? C::ONE6 : C::ONE7;
+}
+template <class C>
+ACE_HD constexpr uint32_t rr_limb(int i) {
+    return i == 0 ? C::RR0 : i == 1 ? C::RR1 : i == 2 ? C::RR2 : i == 3 ? C::RR3
+         : i == 4 ? C::RR4 : i == 5 ? C::RR5 : i == 6 ? C::RR6 : C::RR7;
+}
+
+template <class C>
+struct Fe {
+    uint32_t v[8];
+};
+typedef Fe<FpCfg> fp_t;
+typedef Fe<FrCfg> fr_t;
+
+// ---------------------------------------------------------------------------
+// constants
+// ---------------------------------------------------------------------------
+template <class C>
+ACE_HD Fe<C> fe_zero() {
+    Fe<C> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = 0;
+    return r;
+}
+template <class C>
+ACE_HD Fe<C> fe_one() {  // Montgomery form of 1
+    Fe<C> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = one_limb<C>(i);
+    return r;
+}
+template <class C>
+ACE_HD Fe<C> fe_rr() {  // R^2 mod m
+    Fe<C> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = rr_limb<C>(i);
+    return r;
+}
+
+template <class C>
+ACE_HD bool fe_is_zero(const Fe<C>& a) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) t |= a.v[i];
+    return t == 0;
+}
+template <class C>
+ACE_HD bool fe_eq(const Fe<C>& a, const Fe<C>& b) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) t |= a.v[i] ^ b.v[i];
+    return t == 0;
+}
+// a >= m for a canonical-candidate value (used to validate inputs)
+template <class C>
+ACE_HD bool fe_geq_mod(const Fe<C>& a) {
+#pragma unroll
+    for (int i = 7; i >= 0; i--) {
+        if (a.v[i] > mod_limb<C>(i)) return true;
+        if (a.v[i] < mod_limb<C>(i)) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// host (portable) arithmetic
+// ---------------------------------------------------------------------------
+template <class C>
+inline void h_add(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t t[8], d[8];
+    uint64_t c = 0;
+    for (int i = 0; i < 8; i++) { c += (uint64_t)a[i] + b[i]; t[i] = (uint32_t)c; c >>= 32; }
+    int64_t br = 0;
+    for (int i = 0; i < 8; i++) {
+        int64_t x = (int64_t)t[i] - mod_limb<C>(i) + br;
+        d[i] = (uint32_t)x;
+        br = x < 0 ? -1 : 0;
+    }
+    bool keep = br != 0;  // t < m
+    for (int i = 0; i < 8; i++) r[i] = keep ? t[i] : d[i];
+}
+template <class C>
+inline void h_sub(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t d[8];
+    int64_t br = 0;
+    for (int i = 0; i < 8; i++) {
+        int64_t x = (int64_t)a[i] - b[i] + br;
+        d[i] = (uint32_t)x;
+        br = x < 0 ? -1 : 0;
+    }
+    if (br) {
+        uint64_t c = 0;
+        for (int i = 0; i < 8; i++) { c += (uint64_t)d[i] + mod_limb<C>(i); d[i] = (uint32_t)c; c >>= 32; }
+    }
+    for (int i = 0; i < 8; i++) r[i] = d[i];
+}
+template <class C>
+inline void h_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 8; i++) {
+        uint64_t c = 0;
+        for (int j = 0; j < 8; j++) {
+            c += (uint64_t)t[j] + (uint64_t)a[j] * b[i];
+            t[j] = (uint32_t)c;
+            c >>= 32;
+        }
+        c += t[8];
+        t[8] = (uint32_t)c;
+        t[9] = (uint32_t)(c >> 32);
+        uint32_t m = t[0] * C::INV;
+        c = (uint64_t)t[0] + (uint64_t)m * mod_limb<C>(0);
+        c >>= 32;
+        for (int j = 1; j < 8; j++) {
+            c += (uint64_t)t[j] + (uint64_t)m * mod_limb<C>(j);
+            t[j - 1] = (uint32_t)c;
+            c >>= 32;
+        }
+        c += t[8];
+        t[7] = (uint32_t)c;
+        t[8] = t[9] + (uint32_t)(c >> 32);
+    }
+    uint32_t d[8];
+    int64_t br = 0;
+    for (int i = 0; i < 8; i++) {
+        int64_t x = (int64_t)t[i] - mod_limb<C>(i) + br;
+        d[i] = (uint32_t)x;
+        br = x < 0 ? -1 : 0;
+    }
+    bool keep = (t[8] == 0) && br != 0;
+    for (int i = 0; i < 8; i++) r[i] = keep ? t[i] : d[i];
+}
+
+// ---------------------------------------------------------------------------
+// device arithmetic (PTX carry chains)
+// ---------------------------------------------------------------------------
+#if defined(__CUDA_ARCH__)
+
+template <class C>
+ACE_DEV void d_add(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t t0, t1, t2, t3, t4, t5, t6, t7, d0, d1, d2, d3, d4, d5, d6, d7, mask;
+    asm("add.cc.u32 %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32 %7, %15, %23;\n\t"
+        : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3), "=r"(t4), "=r"(t5), "=r"(t6), "=r"(t7)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;\n\t"
+        : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3), "=r"(d4), "=r"(d5), "=r"(d6), "=r"(d7), "=r"(mask)
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7),
+          "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5), "n"(C::M6), "n"(C::M7));
+    // mask = 0xffffffff when t < m (keep t), else 0 (take t - m)
+    r[0] = (t0 & mask) | (d0 & ~mask);
+    r[1] = (t1 & mask) | (d1 & ~mask);
+    r[2] = (t2 & mask) | (d2 & ~mask);
+    r[3] = (t3 & mask) | (d3 & ~mask);
+    r[4] = (t4 & mask) | (d4 & ~mask);
+    r[5] = (t5 & mask) | (d5 & ~mask);
+    r[6] = (t6 & mask) | (d6 & ~mask);
+    r[7] = (t7 & mask) | (d7 & ~mask);
+}
+
+template <class C>
+ACE_DEV void d_sub(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t d0, d1, d2, d3, d4, d5, d6, d7, mask;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;\n\t"
+        : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3), "=r"(d4), "=r"(d5), "=r"(d6), "=r"(d7), "=r"(mask)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+    // mask = 0xffffffff on borrow: add m back
+    asm("add.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %11;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\t"
+        "addc.cc.u32 %4, %4, %13;\n\t"
+        "addc.cc.u32 %5, %5, %14;\n\t"
+        "addc.cc.u32 %6, %6, %15;\n\t"
+        "addc.u32 %7, %7, %16;\n\t"
+        : "+r"(d0), "+r"(d1), "+r"(d2), "+r"(d3), "+r"(d4), "+r"(d5), "+r"(d6), "+r"(d7)
+        : "r"(mask),
+          "r"(C::M0 & mask), "r"(C::M1 & mask), "r"(C::M2 & mask), "r"(C::M3 & mask),
+          "r"(C::M4 & mask), "r"(C::M5 & mask), "r"(C::M6 & mask), "r"(C::M7 & mask));
+    r[0] = d0; r[1] = d1; r[2] = d2; r[3] = d3; r[4] = d4; r[5] = d5; r[6] = d6; r[7] = d7;
+}
+
+// t += a * b_i (9-limb accumulator t0..t8, t8 == 0 on entry)
+#define ACE_MAC_ROW(bi)                                                                          \
+    asm("mad.lo.cc.u32 %0, %9, %17, %0;\n\t"                                                     \
+        "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"                                                   \
+        "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"                                                   \
+        "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"                                                   \
+        "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"                                                   \
+        "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"                                                   \
+        "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"                                                   \
+        "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"                                                   \
+        "addc.u32 %8, 0, 0;\n\t"                                                                 \
+        "mad.hi.cc.u32 %1, %9, %17, %1;\n\t"                                                     \
+        "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"                                                   \
+        "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"                                                   \
+        "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"                                                   \
+        "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"                                                   \
+        "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"                                                   \
+        "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"                                                   \
+        "madc.hi.u32 %8, %16, %17, %8;\n\t"                                                      \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), \
+          "r"(bi))
+
+// t = (t + m p) / 2^32 with m = t0 * INV; result in t0..t7 (shifted), t8 := 0
+#define ACE_REDUCE_ROW()                                                                         \
+    asm("{\n\t.reg .u32 m;\n\t"                                                                  \
+        "mul.lo.u32 m, %0, %9;\n\t"                                                              \
+        "mad.lo.cc.u32 %0, m, %10, %0;\n\t"                                                      \
+        "madc.lo.cc.u32 %1, m, %11, %1;\n\t"                                                     \
+        "madc.lo.cc.u32 %2, m, %12, %2;\n\t"                                                     \
+        "madc.lo.cc.u32 %3, m, %13, %3;\n\t"                                                     \
+        "madc.lo.cc.u32 %4, m, %14, %4;\n\t"                                                     \
+        "madc.lo.cc.u32 %5, m, %15, %5;\n\t"                                                     \
+        "madc.lo.cc.u32 %6, m, %16, %6;\n\t"                                                     \
+        "madc.lo.cc.u32 %7, m, %17, %7;\n\t"                                                     \
+        "addc.u32 %8, %8, 0;\n\t"                                                                \
+        "mad.hi.cc.u32 %0, m, %10, %1;\n\t"                                                      \
+        "madc.hi.cc.u32 %1, m, %11, %2;\n\t"                                                     \
+        "madc.hi.cc.u32 %2, m, %12, %3;\n\t"                                                     \
+        "madc.hi.cc.u32 %3, m, %13, %4;\n\t"                                                     \
+        "madc.hi.cc.u32 %4, m, %14, %5;\n\t"                                                     \
+        "madc.hi.cc.u32 %5, m, %15, %6;\n\t"                                                     \
+        "madc.hi.cc.u32 %6, m, %16, %7;\n\t"                                                     \
+        "madc.hi.u32 %7, m, %17, %8;\n\t"                                                        \
+        "mov.u32 %8, 0;\n\t}"                                                                    \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+        : "n"(C::INV), "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5),  \
+          "n"(C::M6), "n"(C::M7))
+
+template <class C>
+ACE_DEV void d_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
+    ACE_MAC_ROW(b[0]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[1]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[2]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[3]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[4]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[5]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[6]);
+    ACE_REDUCE_ROW();
+    ACE_MAC_ROW(b[7]);
+    ACE_REDUCE_ROW();
+    // t < 2m: one conditional subtraction
+    uint32_t d0, d1, d2, d3, d4, d5, d6, d7, mask;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;\n\t"
+        : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3), "=r"(d4), "=r"(d5), "=r"(d6), "=r"(d7), "=r"(mask)
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7),
+          "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5), "n"(C::M6), "n"(C::M7));
+    r[0] = (t0 & mask) | (d0 & ~mask);
+    r[1] = (t1 & mask) | (d1 & ~mask);
+    r[2] = (t2 & mask) | (d2 & ~mask);
+    r[3] = (t3 & mask) | (d3 & ~mask);
+    r[4] = (t4 & mask) | (d4 & ~mask);
+    r[5] = (t5 & mask) | (d5 & ~mask);
+    r[6] = (t6 & mask) | (d6 & ~mask);
+    r[7] = (t7 & mask) | (d7 & ~mask);
+}
+#undef ACE_MAC_ROW
+#undef ACE_REDUCE_ROW
+
+#endif  // __CUDA_ARCH__
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+template <class C>
+ACE_HD Fe<C> operator+(const Fe<C>& a, const Fe<C>& b) {
+    Fe<C> r;
+#if defined(__CUDA_ARCH__)
+    d_add<C>(r.v, a.v, b.v);
+#else
+    h_add<C>(r.v, a.v, b.v);
+#endif
+    return r;
+}
+template <class C>
+ACE_HD Fe<C> operator-(const Fe<C>& a, const Fe<C>& b) {
+    Fe<C> r;
+#if defined(__CUDA_ARCH__)
+    d_sub<C>(r.v, a.v, b.v);
+#else
+    h_sub<C>(r.v, a.v, b.v);
+#endif
+    return r;
+}
+template <class C>
+ACE_HD Fe<C> operator*(const Fe<C>& a, const Fe<C>& b) {
+    Fe<C> r;
+#if defined(__CUDA_ARCH__)
+    d_mul<C>(r.v, a.v, b.v);
+#else
+    h_mul<C>(r.v, a.v, b.v);
+#endif
+    return r;
+}
+template <class C>
+ACE_HD Fe<C> fe_sqr(const Fe<C>& a) { return a * a; }
+template <class C>
+ACE_HD Fe<C> fe_dbl(const Fe<C>& a) { return a + a; }
+template <class C>
+ACE_HD Fe<C> fe_neg(const Fe<C>& a) { return fe_zero<C>() - a; }
+template <class C>
+ACE_HD Fe<C> fe_to_mont(const Fe<C>& a) { return a * fe_rr<C>(); }
+template <class C>
+ACE_HD Fe<C> fe_from_mont(const Fe<C>& a) {
+    Fe<C> one = fe_zero<C>();
+    one.v[0] = 1;
+    return a * one;
+}
+// small integer in Montgomery form
+template <class C>
+ACE_HD Fe<C> fe_from_u32(uint32_t x) {
+    Fe<C> t = fe_zero<C>();
+    t.v[0] = x;
+    return fe_to_mont(t);
+}
+
+// a^e, e given as 8 little-endian limbs (plain integer): left-to-right binary
+// square-and-multiply (rare: inversions and setup constants only)
+template <class C>
+ACE_HD Fe<C> fe_pow(const Fe<C>& a, const uint32_t* e) {
+    Fe<C> acc = fe_one<C>();
+#pragma unroll 1
+    for (int i = 255; i >= 0; i--) {
+        acc = fe_sqr(acc);
+        if ((e[i >> 5] >> (i & 31)) & 1u) acc = acc * a;
+    }
+    return acc;
+}
+// inverse by Fermat (a^{m-2}); inverse of 0 is 0
+template <class C>
+ACE_HD Fe<C> fe_inv(const Fe<C>& a) {
+    uint32_t e[8];
+    for (int i = 0; i < 8; i++) e[i] = mod_limb<C>(i);
+    e[0] -= 2;  // m is odd and > 2: no borrow
+    return fe_pow(a, e);
+}
+
+// ---------------------------------------------------------------------------
+// Fp2 = Fp[u]/(u^2 + 1)
+// ---------------------------------------------------------------------------
+struct fp2_t {
+    fp_t c0, c1;
+};
+ACE_HD fp2_t operator+(const fp2_t& a, const fp2_t& b) { return {a.c0 + b.c0, a.c1 + b.c1}; }
+ACE_HD fp2_t operator-(const fp2_t& a, const fp2_t& b) { return {a.c0 - b.c0, a.c1 - b.c1}; }
+// Karatsuba: (a0 b0 - a1 b1) + ((a0 + a1)(b0 + b1) - a0 b0 - a1 b1) u
+ACE_HD fp2_t operator*(const fp2_t& a, const fp2_t& b) {
+    fp_t v0 = a.c0 * b.c0;
+    fp_t v1 = a.c1 * b.c1;
+    fp_t s = (a.c0 + a.c1) * (b.c0 + b.c1);
+    return {v0 - v1, s - v0 - v1};
+}
+ACE_HD fp2_t fe_sqr(const fp2_t& a) {
+    // (a0 + a1)(a0 - a1) + 2 a0 a1 u
+    fp_t t = a.c0 * a.c1;
+    return {(a.c0 + a.c1) * (a.c0 - a.c1), t + t};
+}
+ACE_HD fp2_t fe_dbl(const fp2_t& a) { return {a.c0 + a.c0, a.c1 + a.c1}; }
+ACE_HD fp2_t fe_neg(const fp2_t& a) { return {fe_neg(a.c0), fe_neg(a.c1)}; }
+ACE_HD bool fe_is_zero(const fp2_t& a) { return fe_is_zero(a.c0) && fe_is_zero(a.c1); }
+ACE_HD bool fe_eq(const fp2_t& a, const fp2_t& b) { return fe_eq(a.c0, b.c0) && fe_eq(a.c1, b.c1); }
+ACE_HD fp2_t fe_inv(const fp2_t& a) {
+    fp_t n = a.c0 * a.c0 + a.c1 * a.c1;
+    fp_t ni = fe_inv(n);
+    return {a.c0 * ni, fe_neg(a.c1 * ni)};
+}
+ACE_HD fp2_t fe_to_mont(const fp2_t& a) { return {fe_to_mont(a.c0), fe_to_mont(a.c1)}; }
+ACE_HD fp2_t fe_from_mont(const fp2_t& a) { return {fe_from_mont(a.c0), fe_from_mont(a.c1)}; }
+
+template <class F>
+ACE_HD F field_zero();
+template <>
+ACE_HD fp_t field_zero<fp_t>() { return fe_zero<FpCfg>(); }
+template <>
+ACE_HD fr_t field_zero<fr_t>() { return fe_zero<FrCfg>(); }
+template <>
+ACE_HD fp2_t field_zero<fp2_t>() { return {fe_zero<FpCfg>(), fe_zero<FpCfg>()}; }
+template <class F>
+ACE_HD F field_one();
+template <>
+ACE_HD fp_t field_one<fp_t>() { return fe_one<FpCfg>(); }
+template <>
+ACE_HD fr_t field_one<fr_t>() { return fe_one<FrCfg>(); }
+template <>
+ACE_HD fp2_t field_one<fp2_t>() { return {fe_one<FpCfg>(), fe_zero<FpCfg>()}; }
+
+}  // namespace ace

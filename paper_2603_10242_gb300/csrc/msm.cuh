@@ -1,0 +1,71 @@
+// msm.cuh -- Pippenger multi-scalar multiplication for G1 and G2 (internal).
+//
+// sum_i k_i P_i for affine P_i (Montgomery form) and canonical Fr scalars k_i:
+//   1. signed c-bit digits of every scalar; scalars 0 contribute nothing and
+//      scalars 1 go to an extra "ones" window of B virtual buckets (their sum
+//      is that window's plain total), so the frequent {0,1} witness values
+//      neither cost K additions nor pile onto one bucket;
+//   2. counting sort of (bucket, point) pairs: histogram, exclusive scan,
+//      scatter;
+//   3. one mixed XYZZ addition per entry into its bucket;
+//   4. per window sum_b b S_b: running sums over segments of L buckets, then a
+//      binary tree over segments whose right child is weighted by 2^level L;
+//   5. Horner over windows (c doublings each) plus the ones-window total.
+// These are the G1/G2 multi-scalar multiplications of Groth16.Prove (the
+// paper's Section 3.1, Algorithm 1), computed for the A, B1, L and H queries
+// on G1 and the B query on G2.
+#pragma once
+#include "curve.cuh"
+#include "runtime.cuh"
+
+namespace ace {
+
+struct MsmPlan {
+    size_t n = 0;
+    int c = 0;       // window bits
+    int K = 0;       // digit windows, ceil(255 / c)
+    uint32_t B = 0;  // buckets per window, 2^(c-1)
+    int lambda = 0;  // log2 of the segment length L
+    uint32_t L = 0;
+    uint32_t M = 0;  // segments per window, B / L
+    uint32_t windows() const { return (uint32_t)K + 1; }  // + ones window
+    uint32_t keys() const { return windows() * B; }
+};
+
+// c chosen by the cost model  n K madd + 2 K 2^(c-1) add  (force_c > 0 overrides)
+MsmPlan msm_plan(size_t n, int force_c = 0);
+
+template <class F, class A>
+struct MsmBufs {
+    uint32_t* offsets;   // keys + 1
+    uint32_t* cursor;    // keys
+    uint32_t* scan_tmp;  // scan block sums
+    uint32_t* entries;   // n K
+    Xyzz<F>* buckets;    // keys
+    Xyzz<F>* segW;       // windows M
+    Xyzz<F>* segS;       // windows M
+    Affine<F>* conv;     // n (only when bases arrive canonical)
+    template <class Alloc>
+    bool carve(Alloc& a, const MsmPlan& p, bool need_conv);
+};
+
+// Run one MSM.  d_bases: n affine points; base_mont says whether they are in
+// Montgomery form.  Writes the XYZZ result (Montgomery) to d_res if non-null
+// and the canonical affine result to d_out if non-null.  Scratch comes from
+// `ar` (size it with msm_scratch_bytes).  Asynchronous on st.
+template <class F>
+int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
+            Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st);
+template <class F>
+size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont);
+
+// exclusive prefix sum of n u32 values in place; tmp holds ceil(n/1024)+1 words
+int scan_exclusive_u32(uint32_t* d, size_t n, uint32_t* tmp, cudaStream_t st);
+size_t scan_tmp_words(size_t n);
+
+}  // namespace ace
+
+namespace ace {
+template <bool SCATTER>
+void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t* entries, cudaStream_t st);
+}  // namespace ace

@@ -1,0 +1,238 @@
+// msm_common.cu -- MSM plan, exclusive scan and the digit / histogram / scatter
+// kernels shared by the G1 and G2 instantiations (see msm.cuh).
+#include "msm.cuh"
+
+namespace ace {
+
+// ---------------------------------------------------------------------------
+// vectorised loads / stores of points (16-byte aligned arrays)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T ld_vec(const T* p) {
+    static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
+    T r;
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4* d = reinterpret_cast<uint4*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = __ldg(s + i);
+    return r;
+}
+template <class T>
+__device__ __forceinline__ void st_vec(T* p, const T& v) {
+    const uint4* s = reinterpret_cast<const uint4*>(&v);
+    uint4* d = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = s[i];
+}
+template <class T>
+__device__ __forceinline__ T ld_plain(const T* p) {
+    T r;
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4* d = reinterpret_cast<uint4*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = s[i];
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+MsmPlan msm_plan(size_t n, int force_c) {
+    MsmPlan p;
+    p.n = n;
+    int best_c = 8;
+    double best = 1e300;
+    for (int c = 6; c <= 20; c++) {
+        int K = (255 + c - 1) / c;
+        double cost = (double)n * K * 10.0 + 2.0 * K * (double)(1u << (c - 1)) * 14.0;
+        if (cost < best) { best = cost; best_c = c; }
+    }
+    p.c = force_c > 0 ? force_c : best_c;
+    if (p.c < 6) p.c = 6;
+    if (p.c > 20) p.c = 20;
+    p.K = (255 + p.c - 1) / p.c;
+    p.B = 1u << (p.c - 1);
+    p.lambda = p.c - 1 < 5 ? p.c - 1 : 5;
+    p.L = 1u << p.lambda;
+    p.M = p.B / p.L;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// scan
+// ---------------------------------------------------------------------------
+size_t scan_tmp_words(size_t n) { return (n + 1023) / 1024 + 1; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= (unsigned)o) v += t;
+    }
+    return v;
+}
+
+// block of 256 threads scans a tile of 1024 values (4 per thread), exclusive
+__global__ void k_scan_tiles(uint32_t* d, size_t n, uint32_t* sums) {
+    __shared__ uint32_t wsum[8];
+    size_t base = (size_t)blockIdx.x * 1024 + threadIdx.x * 4;
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = (base + k < n) ? d[base + k] : 0u;
+    uint32_t tsum = v[0] + v[1] + v[2] + v[3];
+    uint32_t incl = warp_incl_scan(tsum);
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < 8 ? wsum[lane] : 0u;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < 8) wsum[lane] = wi - w;  // exclusive warp offsets
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - tsum;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (base + k < n) d[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 255) sums[blockIdx.x] = run;
+}
+
+// one block scans the tile sums (any count), exclusive, in place
+__global__ void k_scan_sums(uint32_t* sums, uint32_t nb) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t start = 0; start < nb; start += 1024) {
+        uint32_t i = start + threadIdx.x;
+        uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t incl = warp_incl_scan(v);
+        int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+            uint32_t wi = warp_incl_scan(w);
+            wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        uint32_t ex = carry + wsum[warp] + incl - v;
+        if (i < nb) sums[i] = ex;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = ex + v;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(uint32_t* d, size_t n, const uint32_t* sums) {
+    size_t base = (size_t)blockIdx.x * 1024 + threadIdx.x * 4;
+    uint32_t add = sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (base + k < n) d[base + k] += add;
+}
+
+int scan_exclusive_u32(uint32_t* d, size_t n, uint32_t* tmp, cudaStream_t st) {
+    if (n == 0) return ACE_OK;
+    uint32_t nb = (uint32_t)((n + 1023) / 1024);
+    k_scan_tiles<<<nb, 256, 0, st>>>(d, n, tmp);
+    k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
+    k_scan_add<<<nb, 256, 0, st>>>(d, n, tmp);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// digits, histogram and scatter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ld_scalar(const uint32_t* sc, size_t i, uint32_t s[8]) {
+    const uint4* p = reinterpret_cast<const uint4*>(sc + 8 * i);
+    uint4 a = __ldg(p), b = __ldg(p + 1);
+    s[0] = a.x; s[1] = a.y; s[2] = a.z; s[3] = a.w;
+    s[4] = b.x; s[5] = b.y; s[6] = b.z; s[7] = b.w;
+}
+
+template <int C>
+__device__ __forceinline__ uint32_t window_bits(const uint32_t s[8], int w) {
+    const int bit = w * C;
+    const int limb = bit >> 5, sh = bit & 31;
+    uint32_t lo = s[limb] >> sh;
+    uint32_t hi = (sh != 0 && limb + 1 < 8) ? (s[limb + 1] << (32 - sh)) : 0u;
+    return (lo | hi) & ((1u << C) - 1u);
+}
+
+// kind: 0 zero, 1 one, 2 general
+__device__ __forceinline__ int scalar_kind(const uint32_t s[8]) {
+    uint32_t hi = s[1] | s[2] | s[3] | s[4] | s[5] | s[6] | s[7];
+    if (hi == 0 && s[0] == 0) return 0;
+    if (hi == 0 && s[0] == 1) return 1;
+    return 2;
+}
+
+// SCATTER = false: histogram into cnt; true: place entries using cnt as cursor
+template <int C, bool SCATTER>
+__global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t* cnt, uint32_t* entries) {
+    constexpr int K = (255 + C - 1) / C;
+    constexpr uint32_t B = 1u << (C - 1);
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t s[8];
+    ld_scalar(sc, i, s);
+    int kind = scalar_kind(s);
+    if (kind == 0) return;
+    if (kind == 1) {
+        uint32_t key = (uint32_t)K * B + (uint32_t)(i & (B - 1));
+        if (SCATTER) {
+            uint32_t pos = atomicAdd(&cnt[key], 1u);
+            entries[pos] = (uint32_t)i;
+        } else {
+            atomicAdd(&cnt[key], 1u);
+        }
+        return;
+    }
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        uint32_t raw = window_bits<C>(s, w) + carry;
+        uint32_t mag, neg;
+        if (raw > B) {
+            mag = (1u << C) - raw;  // digit raw - 2^C < 0
+            neg = 1u;
+            carry = 1u;
+        } else {
+            mag = raw;
+            neg = 0u;
+            carry = 0u;
+        }
+        if (mag != 0) {
+            uint32_t key = (uint32_t)w * B + (mag - 1u);
+            if (SCATTER) {
+                uint32_t pos = atomicAdd(&cnt[key], 1u);
+                entries[pos] = (uint32_t)i | (neg << 31);
+            } else {
+                atomicAdd(&cnt[key], 1u);
+            }
+        }
+    }
+}
+
+template <bool SCATTER>
+void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t* entries, cudaStream_t st) {
+    unsigned grid = (unsigned)((n + 255) / 256);
+    switch (c) {
+#define ACE_DIGITS_CASE(CC) \
+    case CC: k_msm_digits<CC, SCATTER><<<grid, 256, 0, st>>>(sc, n, cnt, entries); break;
+        ACE_DIGITS_CASE(6) ACE_DIGITS_CASE(7) ACE_DIGITS_CASE(8) ACE_DIGITS_CASE(9) ACE_DIGITS_CASE(10)
+        ACE_DIGITS_CASE(11) ACE_DIGITS_CASE(12) ACE_DIGITS_CASE(13) ACE_DIGITS_CASE(14) ACE_DIGITS_CASE(15)
+        ACE_DIGITS_CASE(16) ACE_DIGITS_CASE(17) ACE_DIGITS_CASE(18) ACE_DIGITS_CASE(19) ACE_DIGITS_CASE(20)
+#undef ACE_DIGITS_CASE
+        default: break;
+    }
+}
+
+template void launch_digits<false>(int, const uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
+template void launch_digits<true>(int, const uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
+
+}  // namespace ace

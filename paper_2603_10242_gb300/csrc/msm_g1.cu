@@ -1,0 +1,8 @@
+// msm_g1.cu -- G1 instantiation of the Pippenger MSM.
+#include "msm_impl.cuh"
+
+namespace ace {
+template int msm_run<fp_t>(const MsmPlan&, const Affine<fp_t>*, bool, const uint32_t*, Arena&, Xyzz<fp_t>*,
+                           Affine<fp_t>*, cudaStream_t);
+template size_t msm_scratch_bytes<fp_t>(const MsmPlan&, bool);
+}  // namespace ace

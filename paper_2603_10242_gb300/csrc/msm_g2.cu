@@ -1,0 +1,8 @@
+// msm_g2.cu -- G2 instantiation of the Pippenger MSM.
+#include "msm_impl.cuh"
+
+namespace ace {
+template int msm_run<fp2_t>(const MsmPlan&, const Affine<fp2_t>*, bool, const uint32_t*, Arena&, Xyzz<fp2_t>*,
+                            Affine<fp2_t>*, cudaStream_t);
+template size_t msm_scratch_bytes<fp2_t>(const MsmPlan&, bool);
+}  // namespace ace

@@ -1,0 +1,197 @@
+// msm_impl.cuh -- templated MSM kernels and driver, instantiated once per
+// group by msm_g1.cu and msm_g2.cu (see msm.cuh for the method).
+#pragma once
+#include "msm.cuh"
+
+namespace ace {
+
+// ---------------------------------------------------------------------------
+// vectorised loads / stores of points (16-byte aligned arrays)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T ld_vec(const T* p) {
+    static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
+    T r;
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4* d = reinterpret_cast<uint4*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = __ldg(s + i);
+    return r;
+}
+template <class T>
+__device__ __forceinline__ void st_vec(T* p, const T& v) {
+    const uint4* s = reinterpret_cast<const uint4*>(&v);
+    uint4* d = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = s[i];
+}
+template <class T>
+__device__ __forceinline__ T ld_plain(const T* p) {
+    T r;
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4* d = reinterpret_cast<uint4*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = s[i];
+    return r;
+}
+
+template <class F, class A>
+template <class Alloc>
+bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
+    size_t keys = p.keys();
+    offsets = (uint32_t*)a.take((keys + 1) * 4);
+    cursor = (uint32_t*)a.take(keys * 4);
+    scan_tmp = (uint32_t*)a.take(scan_tmp_words(keys + 1) * 4);
+    entries = (uint32_t*)a.take(p.n * (size_t)p.K * 4 + 4);
+    buckets = (Xyzz<F>*)a.take(keys * sizeof(Xyzz<F>));
+    segW = (Xyzz<F>*)a.take((size_t)p.windows() * p.M * sizeof(Xyzz<F>));
+    segS = (Xyzz<F>*)a.take((size_t)p.windows() * p.M * sizeof(Xyzz<F>));
+    conv = need_conv ? (Affine<F>*)a.take(p.n * sizeof(Affine<F>)) : nullptr;
+    return offsets && cursor && scan_tmp && entries && buckets && segW && segS && (!need_conv || conv);
+}
+
+template <class F>
+size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont) {
+    Sizer s;
+    MsmBufs<F, Sizer> b;
+    b.carve(s, plan, !base_mont);
+    return s.off + 256;
+}
+
+// ---------------------------------------------------------------------------
+// bucket accumulation: one thread per bucket, one mixed addition per entry
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(128) k_bucket_acc(const Affine<F>* __restrict__ bases,
+                                                    const uint32_t* __restrict__ entries,
+                                                    const uint32_t* __restrict__ offsets, uint32_t nkeys,
+                                                    Xyzz<F>* buckets) {
+    uint32_t key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= nkeys) return;
+    uint32_t b = offsets[key], e = offsets[key + 1];
+    Xyzz<F> acc = xyzz_inf<F>();
+    for (uint32_t t = b; t < e; t++) {
+        uint32_t v = __ldg(entries + t);
+        Affine<F> p = ld_vec(bases + (v & 0x7fffffffu));
+        if (v >> 31) p.y = fe_neg(p.y);
+        acc = xyzz_add_aff(acc, p);
+    }
+    st_vec(buckets + key, acc);
+}
+
+// ---------------------------------------------------------------------------
+// bucket reduction: segments of L buckets, then a weighted binary tree
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(128) k_seg_reduce(const Xyzz<F>* __restrict__ buckets, uint32_t nseg,
+                                                    uint32_t B, uint32_t L, uint32_t M, Xyzz<F>* segW,
+                                                    Xyzz<F>* segS) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nseg) return;
+    uint32_t w = t / M, j = t % M;
+    const Xyzz<F>* bk = buckets + (size_t)w * B + (size_t)j * L;
+    Xyzz<F> run = xyzz_inf<F>(), acc = xyzz_inf<F>();
+    for (int b = (int)L - 1; b >= 0; b--) {
+        run = xyzz_add(run, ld_plain(bk + b));
+        acc = xyzz_add(acc, run);
+    }
+    st_vec(segW + t, acc);
+    st_vec(segS + t, run);
+}
+
+// level: combine slots (j 2^(lev+1)) and (j 2^(lev+1) + 2^lev) of every window:
+// W = W_l + W_r + 2^(lev + lambda) S_r, S = S_l + S_r
+template <class F>
+__global__ void __launch_bounds__(128) k_tree_level(Xyzz<F>* W, Xyzz<F>* S, uint32_t windows, uint32_t M,
+                                                    int lev, int lambda) {
+    uint32_t pairs = M >> (lev + 1);
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= windows * pairs) return;
+    uint32_t w = t / pairs, j = t % pairs;
+    size_t l = (size_t)w * M + ((size_t)j << (lev + 1));
+    size_t r = l + ((size_t)1 << lev);
+    Xyzz<F> sr = ld_plain(S + r);
+    Xyzz<F> sh = sr;
+    for (int k = 0; k < lev + lambda; k++) sh = xyzz_dbl(sh);
+    Xyzz<F> wl = ld_plain(W + l);
+    wl = xyzz_add(wl, ld_plain(W + r));
+    wl = xyzz_add(wl, sh);
+    st_vec(W + l, wl);
+    st_vec(S + l, xyzz_add(ld_plain(S + l), sr));
+}
+
+// Horner over the K digit windows, plus the ones-window total
+template <class F>
+__global__ void k_msm_final(const Xyzz<F>* W, const Xyzz<F>* S, uint32_t K, uint32_t M, int c, Xyzz<F>* res,
+                            Affine<F>* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Xyzz<F> acc = ld_plain(W + (size_t)(K - 1) * M);
+    for (int w = (int)K - 2; w >= 0; w--) {
+        for (int k = 0; k < c; k++) acc = xyzz_dbl(acc);
+        acc = xyzz_add(acc, ld_plain(W + (size_t)w * M));
+    }
+    acc = xyzz_add(acc, ld_plain(S + (size_t)K * M));
+    if (res) st_vec(res, acc);
+    if (out) {
+        Affine<F> a = aff_from_mont(xyzz_to_aff(acc));
+        st_vec(out, a);
+    }
+}
+
+template <class F>
+__global__ void k_msm_empty(Xyzz<F>* res, Affine<F>* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (res) *res = xyzz_inf<F>();
+    if (out) {
+        out->x = field_zero<F>();
+        out->y = field_zero<F>();
+    }
+}
+
+template <class F>
+__global__ void k_bases_to_mont(const Affine<F>* in, size_t n, Affine<F>* out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Affine<F> p = ld_vec(in + i);
+    st_vec(out + i, aff_to_mont(p));
+}
+
+template <class F>
+int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
+            Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st) {
+    if (plan.n == 0) {
+        k_msm_empty<F><<<1, 1, 0, st>>>(d_res, d_out);
+        ACE_TRY_CUDA(cudaGetLastError());
+        return ACE_OK;
+    }
+    MsmBufs<F, Arena> b;
+    if (!b.carve(ar, plan, !base_mont)) {
+        set_error("msm: scratch arena too small");
+        return ACE_E_OOM;
+    }
+    const size_t n = plan.n;
+    const uint32_t keys = plan.keys();
+    const Affine<F>* bases = d_bases;
+    if (!base_mont) {
+        k_bases_to_mont<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_bases, n, b.conv);
+        bases = b.conv;
+    }
+    ACE_TRY_CUDA(cudaMemsetAsync(b.offsets, 0, (keys + 1) * sizeof(uint32_t), st));
+    launch_digits<false>(plan.c, d_scalars, n, b.offsets, nullptr, st);
+    ACE_TRY(scan_exclusive_u32(b.offsets, keys + 1, b.scan_tmp, st));
+    ACE_TRY_CUDA(cudaMemcpyAsync(b.cursor, b.offsets, keys * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    launch_digits<true>(plan.c, d_scalars, n, b.cursor, b.entries, st);
+    k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, keys, b.buckets);
+    uint32_t nseg = plan.windows() * plan.M;
+    k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS);
+    for (int lev = 0; (1u << lev) < plan.M; lev++) {
+        uint32_t pairs = plan.windows() * (plan.M >> (lev + 1));
+        k_tree_level<F><<<(pairs + 127) / 128, 128, 0, st>>>(b.segW, b.segS, plan.windows(), plan.M, lev,
+                                                             plan.lambda);
+    }
+    k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, (uint32_t)plan.K, plan.M, plan.c, d_res, d_out);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+}  // namespace ace

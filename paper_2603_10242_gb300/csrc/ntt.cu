@@ -1,0 +1,341 @@
+// ntt.cu -- radix-2 NTT passes over Fr staged in shared memory (see ntt.cuh).
+#include <vector>
+
+#include "ntt.cuh"
+
+namespace ace {
+
+// ---------------------------------------------------------------------------
+// host-side power tables
+// ---------------------------------------------------------------------------
+static fr_t h_pow_u64(const fr_t& a, uint64_t e) {
+    uint32_t ex[8] = {(uint32_t)e, (uint32_t)(e >> 32), 0, 0, 0, 0, 0, 0};
+    return fe_pow(a, ex);
+}
+
+// omega_N = 5^((r - 1) / N)
+fr_t root_of_unity_host(int log_n) {
+    uint32_t e[8];
+    for (int i = 0; i < 8; i++) e[i] = mod_limb<FrCfg>(i);
+    e[0] -= 1;  // r - 1 (r is odd: no borrow)
+    for (int k = 0; k < log_n; k++) {
+        for (int i = 0; i < 8; i++) e[i] = (e[i] >> 1) | (i < 7 ? (e[i + 1] << 31) : 0u);
+    }
+    return fe_pow(fe_from_u32<FrCfg>(5), e);
+}
+
+__global__ void k_expand_pow(const fr_t* hi, const fr_t* lo, int a, size_t n, fr_t* out) {
+    size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    out[j] = hi[j >> a] * lo[j & ((1ull << a) - 1)];
+}
+
+static void h_powers(std::vector<fr_t>& out, const fr_t& base, const fr_t& first, size_t count) {
+    out.resize(count);
+    fr_t x = first;
+    for (size_t i = 0; i < count; i++) {
+        out[i] = x;
+        x = x * base;
+    }
+}
+
+int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
+    auto it = ctx->ntt_plans.find(log_n);
+    if (it != ctx->ntt_plans.end()) {
+        *out = it->second;
+        return ACE_OK;
+    }
+    if (log_n < 1 || log_n > 28) {
+        set_error("ntt: log_n = %d out of range [1, 28]", log_n);
+        return ACE_E_ARG;
+    }
+    const size_t n = (size_t)1 << log_n;
+    const size_t half = n / 2;
+    const int h = (log_n + 1) / 2;
+    const size_t nlo = (size_t)1 << h, nhi = (size_t)1 << (log_n - h);
+    // twiddle seeds: tw[j] = T_hi[j >> a] * T_lo[j & (2^a - 1)], j < N/2
+    const int a = log_n > 1 ? log_n / 2 : 0;
+    const size_t tlo = (size_t)1 << a, thi = (half + tlo - 1) / tlo;
+
+    fr_t omega = root_of_unity_host(log_n);
+    fr_t omega_inv = fe_inv(omega);
+    fr_t one = fe_one<FrCfg>();
+    fr_t g = fe_from_u32<FrCfg>(5), ginv = fe_inv(g);
+    fr_t ninv = fe_inv(fe_from_u32<FrCfg>(1) * h_pow_u64(fe_from_u32<FrCfg>(2), (uint64_t)log_n));
+    fr_t gn = h_pow_u64(g, (uint64_t)n);
+    fr_t zinv = fe_inv(gn - one);
+
+    std::vector<fr_t> fw_lo, fw_hi, iw_lo, iw_hi;
+    h_powers(fw_lo, omega, one, tlo);
+    h_powers(fw_hi, h_pow_u64(omega, tlo), one, thi);
+    h_powers(iw_lo, omega_inv, one, tlo);
+    h_powers(iw_hi, h_pow_u64(omega_inv, tlo), one, thi);
+    std::vector<fr_t> cos_lo, cg_hi, cos_hi, icos_lo_m, icos_lo, icos_hi;
+    h_powers(cos_lo, g, one, nlo);
+    h_powers(cg_hi, h_pow_u64(g, nlo), one, nhi);
+    h_powers(cos_hi, h_pow_u64(g, nlo), ninv, nhi);
+    h_powers(icos_lo_m, ginv, one, nlo);
+    icos_lo.resize(nlo);
+    for (size_t i = 0; i < nlo; i++) icos_lo[i] = fe_from_mont(icos_lo_m[i]);
+    h_powers(icos_hi, h_pow_u64(ginv, nlo), ninv, nhi);
+    fr_t plain1 = fe_zero<FrCfg>();
+    plain1.v[0] = 1;
+    fr_t rr = fe_rr<FrCfg>();
+
+    // layout
+    size_t off = 0;
+    auto place = [&](size_t count) {
+        size_t o = off;
+        off += ((count * sizeof(fr_t)) + 255) & ~(size_t)255;
+        return o;
+    };
+    size_t o_twf = place(half), o_twi = place(half), o_cos_hi = place(nhi), o_cos_lo = place(nlo),
+           o_cg_hi = place(nhi), o_icos_hi = place(nhi), o_icos_lo = place(nlo), o_ninv = place(1),
+           o_one = place(1), o_p1 = place(1), o_rr = place(1), o_seed = place(4 * (tlo + thi));
+    void* mem = nullptr;
+    ACE_TRY(dev_alloc(ctx, &mem, off));
+    char* base = (char*)mem;
+    NttPlan* p = new NttPlan();
+    p->log_n = log_n;
+    p->n = n;
+    p->h = h;
+    p->tw_fwd = (fr_t*)(base + o_twf);
+    p->tw_inv = (fr_t*)(base + o_twi);
+    p->cos_hi = (fr_t*)(base + o_cos_hi);
+    p->cos_lo = (fr_t*)(base + o_cos_lo);
+    p->cg_hi = (fr_t*)(base + o_cg_hi);
+    p->icos_hi = (fr_t*)(base + o_icos_hi);
+    p->icos_lo = (fr_t*)(base + o_icos_lo);
+    p->ninv = (fr_t*)(base + o_ninv);
+    p->one = (fr_t*)(base + o_one);
+    p->plain_one = (fr_t*)(base + o_p1);
+    p->rr = (fr_t*)(base + o_rr);
+    p->zinv = zinv;
+    p->mem = mem;
+    p->bytes = off;
+    fr_t* seed = (fr_t*)(base + o_seed);
+    cudaStream_t st = ctx->stream;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : up(seed, fw_lo.data(), tlo * sizeof(fr_t));
+    e = e ? e : up(seed + tlo, fw_hi.data(), thi * sizeof(fr_t));
+    e = e ? e : up(seed + tlo + thi, iw_lo.data(), tlo * sizeof(fr_t));
+    e = e ? e : up(seed + 2 * tlo + thi, iw_hi.data(), thi * sizeof(fr_t));
+    e = e ? e : up(p->cos_hi, cos_hi.data(), nhi * sizeof(fr_t));
+    e = e ? e : up(p->cos_lo, cos_lo.data(), nlo * sizeof(fr_t));
+    e = e ? e : up(p->cg_hi, cg_hi.data(), nhi * sizeof(fr_t));
+    e = e ? e : up(p->icos_hi, icos_hi.data(), nhi * sizeof(fr_t));
+    e = e ? e : up(p->icos_lo, icos_lo.data(), nlo * sizeof(fr_t));
+    e = e ? e : up(p->ninv, &ninv, sizeof(fr_t));
+    e = e ? e : up(p->one, &one, sizeof(fr_t));
+    e = e ? e : up(p->plain_one, &plain1, sizeof(fr_t));
+    e = e ? e : up(p->rr, &rr, sizeof(fr_t));
+    if (e == cudaSuccess && half > 0) {
+        unsigned grid = (unsigned)((half + 255) / 256);
+        k_expand_pow<<<grid, 256, 0, st>>>(seed + tlo, seed, a, half, p->tw_fwd);
+        k_expand_pow<<<grid, 256, 0, st>>>(seed + 2 * tlo + thi, seed + tlo + thi, a, half, p->tw_inv);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
+    if (e != cudaSuccess) {
+        set_error("ntt plan: %s", cudaGetErrorString(e));
+        dev_free(ctx, mem, off);
+        delete p;
+        return ACE_E_CUDA;
+    }
+    ctx->ntt_plans[log_n] = p;
+    *out = p;
+    return ACE_OK;
+}
+
+void ntt_release_plans(ace_ctx* ctx) {
+    for (auto& kv : ctx->ntt_plans) {
+        dev_free(ctx, kv.second->mem, kv.second->bytes);
+        delete kv.second;
+    }
+    ctx->ntt_plans.clear();
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ fr_t ld_fr(const fr_t* p) {
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4 a = s[0], b = s[1];
+    fr_t r;
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+    r.v[4] = b.x; r.v[5] = b.y; r.v[6] = b.z; r.v[7] = b.w;
+    return r;
+}
+__device__ __forceinline__ void st_fr(fr_t* p, const fr_t& x) {
+    uint4* d = reinterpret_cast<uint4*>(p);
+    d[0] = make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]);
+    d[1] = make_uint4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+__device__ __forceinline__ uint32_t brev_bits(uint32_t x, int bits) { return bits ? (__brev(x) >> (32 - bits)) : 0u; }
+
+__device__ __forceinline__ fr_t scale_factor(const NttScale& s, uint32_t idx, int log_n) {
+    if (s.single) return ld_fr(s.hi) * ld_fr(s.lo);
+    uint32_t e = s.brev ? brev_bits(idx, log_n) : idx;
+    return ld_fr(s.hi + (e >> s.h)) * ld_fr(s.lo + (e & ((1u << s.h) - 1u)));
+}
+
+template <bool DIT>
+__global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int log_n, int t, int b0, int logG,
+                                                  const fr_t* __restrict__ tw, int first_stage, NttScale pre,
+                                                  NttScale post) {
+    extern __shared__ uint32_t sm[];
+    const uint32_t G = 1u << logG;
+    const uint32_t S = G << t;
+    fr_t* arr = data + ((size_t)blockIdx.y << log_n);
+    const uint32_t q0 = blockIdx.x * G;
+    const uint32_t lomask = (1u << b0) - 1u;
+
+    for (uint32_t e = threadIdx.x; e < S; e += blockDim.x) {
+        uint32_t g = e >> logG, ql = e & (G - 1u);
+        uint32_t q = q0 + ql;
+        uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
+        fr_t x = ld_fr(arr + idx);
+        if (pre.hi) x = x * scale_factor(pre, idx, log_n);
+#pragma unroll
+        for (int l = 0; l < 8; l++) sm[l * S + e] = x.v[l];
+    }
+    __syncthreads();
+    for (int ls = 0; ls < t; ls++) {
+        const int hb = DIT ? ls : (t - 1 - ls);
+        const int s = first_stage + ls;
+        const int tshift = DIT ? (log_n - s - 1) : s;
+        for (uint32_t beta = threadIdx.x; beta < S / 2; beta += blockDim.x) {
+            uint32_t ql = beta & (G - 1u), pi = beta >> logG;
+            uint32_t lowbits = pi & ((1u << hb) - 1u);
+            uint32_t gt = ((pi >> hb) << (hb + 1)) | lowbits;
+            uint32_t et = (gt << logG) + ql, eb = et + ((1u << hb) << logG);
+            fr_t x, y;
+#pragma unroll
+            for (int l = 0; l < 8; l++) {
+                x.v[l] = sm[l * S + et];
+                y.v[l] = sm[l * S + eb];
+            }
+            uint32_t j = (lowbits << b0) | ((q0 + ql) & lomask);
+            if (DIT) {
+                if (j) y = y * ld_fr(tw + ((size_t)j << tshift));
+                fr_t u = x + y;
+                y = x - y;
+                x = u;
+            } else {
+                fr_t u = x + y;
+                y = x - y;
+                if (j) y = y * ld_fr(tw + ((size_t)j << tshift));
+                x = u;
+            }
+#pragma unroll
+            for (int l = 0; l < 8; l++) {
+                sm[l * S + et] = x.v[l];
+                sm[l * S + eb] = y.v[l];
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t e = threadIdx.x; e < S; e += blockDim.x) {
+        uint32_t g = e >> logG, ql = e & (G - 1u);
+        uint32_t q = q0 + ql;
+        uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
+        fr_t x;
+#pragma unroll
+        for (int l = 0; l < 8; l++) x.v[l] = sm[l * S + e];
+        if (post.hi) x = x * scale_factor(post, idx, log_n);
+        st_fr(arr + idx, x);
+    }
+}
+
+static const int NTT_MAX_T = 11;     // 2^11 elements x 32 B = 64 KB of shared memory per group
+static const int NTT_SMEM_LOG = 11;  // elements staged per block
+
+int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, const NttScale& pre,
+            const NttScale& post, cudaStream_t st) {
+    const int k = plan.log_n;
+    int passes[4], np = 0;
+    if (k <= NTT_MAX_T) {
+        passes[np++] = k;
+    } else if (k <= 2 * NTT_MAX_T) {
+        passes[np++] = (k + 1) / 2;
+        passes[np++] = k - (k + 1) / 2;
+    } else {
+        int t1 = (k + 2) / 3, t2 = (k - t1 + 1) / 2;
+        passes[np++] = t1;
+        passes[np++] = t2;
+        passes[np++] = k - t1 - t2;
+    }
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        attr_done = true;
+    }
+    const fr_t* tw = inverse ? plan.tw_inv : plan.tw_fwd;
+    NttScale none;
+    int done_bits = 0;
+    for (int pi = 0; pi < np; pi++) {
+        int t = passes[pi];
+        int b0, first_stage;
+        if (dif) {
+            b0 = k - done_bits - t;
+            first_stage = done_bits;
+        } else {
+            b0 = done_bits;
+            first_stage = done_bits;
+        }
+        int logG = NTT_SMEM_LOG - t;
+        if (logG < 0) logG = 0;
+        if (logG > k - t) logG = k - t;
+        uint32_t groups = 1u << (k - t);
+        uint32_t blocks = groups >> logG;
+        uint32_t S = (1u << logG) << t;
+        int threads = S / 2 < 256 ? (int)(S / 2) : 256;
+        if (threads < 32) threads = 32;
+        size_t smem = (size_t)S * 32;
+        dim3 grid(blocks, (unsigned)count);
+        const NttScale& a = pi == 0 ? pre : none;
+        const NttScale& z = pi == np - 1 ? post : none;
+        if (dif)
+            k_ntt_pass<false><<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
+        else
+            k_ntt_pass<true><<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
+        done_bits += t;
+    }
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+__global__ void k_scale_copy(const fr_t* in, fr_t* out, size_t n, NttScale s, int log_n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    st_fr(out + i, ld_fr(in + i) * scale_factor(s, (uint32_t)i, log_n));
+}
+
+int fr_scale_copy(const fr_t* in, fr_t* out, size_t n, const NttScale& s, int log_n, cudaStream_t st) {
+    if (n == 0) return ACE_OK;
+    k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n, s, log_n);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+__global__ void k_bitrev_copy(const fr_t* in, fr_t* out, int log_n) {
+    size_t n = (size_t)1 << log_n;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    size_t off = (size_t)blockIdx.y << log_n;
+    st_fr(out + off + brev_bits((uint32_t)i, log_n), ld_fr(in + off + i));
+}
+
+int fr_bitrev_copy(const fr_t* in, fr_t* out, int log_n, int count, cudaStream_t st) {
+    size_t n = (size_t)1 << log_n;
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)count);
+    k_bitrev_copy<<<grid, 256, 0, st>>>(in, out, log_n);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+}  // namespace ace

@@ -1,0 +1,63 @@
+// ntt.cuh -- number-theoretic transforms over Fr (internal).
+//
+// Domain H = {omega^i}, omega = 5^((r-1)/N) (5 is a non-residue mod r and
+// 2^28 | r - 1); coset g H with g = 5.  A transform is a sequence of passes,
+// each doing t radix-2 stages on groups of 2^t elements staged in shared
+// memory (limb-planar layout, one 32-byte element per index).  Forward
+// passes are decimation in frequency (natural order in, bit-reversed out);
+// the transform that follows consumes bit-reversed input by decimation in
+// time, so the QAP pipeline never permutes data.  Per-element factors (coset
+// powers g^i, 1/N, Montgomery conversion) are applied while a pass loads or
+// stores, from two small power tables.  These are the iNTT / coset NTT steps
+// of the QAP quotient in Groth16.Prove (the paper's Section 3.1, Algorithm 1).
+#pragma once
+#include "curve.cuh"
+#include "runtime.cuh"
+
+namespace ace {
+
+struct NttPlan {
+    int log_n = 0;
+    size_t n = 0;
+    int h = 0;                // factor index split: e = (e_hi << h) | e_lo
+    fr_t* tw_fwd = nullptr;   // omega^j, j < N/2 (Montgomery)
+    fr_t* tw_inv = nullptr;   // omega^-j
+    fr_t* cos_hi = nullptr;   // N^-1 g^(e_hi 2^h) (Montgomery)
+    fr_t* cos_lo = nullptr;   // g^e_lo (Montgomery)
+    fr_t* cg_hi = nullptr;    // g^(e_hi 2^h) (Montgomery)
+    fr_t* icos_hi = nullptr;  // N^-1 g^-(e_hi 2^h) (Montgomery)
+    fr_t* icos_lo = nullptr;  // g^-e_lo as a plain value: the product leaves Montgomery form
+    fr_t* ninv = nullptr;     // [N^-1] (Montgomery), single entry
+    fr_t* one = nullptr;      // [1] (Montgomery), single entry
+    fr_t* plain_one = nullptr;  // [1] as a plain value: multiplying by it leaves Montgomery form
+    fr_t* rr = nullptr;       // [R^2 mod r] raw: multiplying by it enters Montgomery form
+    fr_t zinv;                // (g^N - 1)^-1 (Montgomery)
+    void* mem = nullptr;
+    size_t bytes = 0;
+};
+
+// omega_N = 5^((r-1)/N) in Montgomery form (host)
+fr_t root_of_unity_host(int log_n);
+int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out);
+void ntt_release_plans(ace_ctx* ctx);
+
+// Factor applied to the element at position p: hi[e >> h] * lo[e & (2^h-1)]
+// with e = p or e = bitrev(p); `single` uses hi[0] * lo[0] everywhere.
+struct NttScale {
+    const fr_t* hi = nullptr;
+    const fr_t* lo = nullptr;
+    int h = 0;
+    int brev = 0;
+    int single = 0;
+};
+
+// In-place transform of `count` consecutive arrays of N = 2^log_n elements.
+// dif: natural -> bit-reversed (else bit-reversed -> natural); inverse
+// selects omega^-1.  pre applies at the first load, post at the last store.
+int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, const NttScale& pre,
+            const NttScale& post, cudaStream_t st);
+
+int fr_scale_copy(const fr_t* in, fr_t* out, size_t n, const NttScale& s, int log_n, cudaStream_t st);
+int fr_bitrev_copy(const fr_t* in, fr_t* out, int log_n, int count, cudaStream_t st);
+
+}  // namespace ace

@@ -1,0 +1,490 @@
+// pairing.cpp -- Groth16 verification on the host: the three-pairing check
+// that finalises a block (Section 3.3: a single Groth16 verification, three
+// bilinear pairing operations on BN254; Section 3.4, Algorithm 4).
+//
+// Optimal ate pairing on BN254 (Vercauteren 2010): Miller loop over
+// 6x + 2 (x = 4965661367192848881) with Q on the sextic twist
+// E': y^2 = x^3 + 3/xi (xi = 9 + u) in affine Fp2 coordinates, line values
+// evaluated at P as sparse elements of the tower
+//   Fp2 = Fp[u]/(u^2 + 1),  Fp6 = Fp2[v]/(v^3 - xi),  Fp12 = Fp6[w]/(w^2 - v),
+// the two Frobenius correction lines (pi(Q), -pi^2(Q)), then one final
+// exponentiation: f^(p^6 - 1) by conjugation and inversion, ^(p^2 + 1) by
+// the Frobenius map, and ^((p^4 - p^2 + 1)/r) by square-and-multiply.
+// For the untwisted T = (x' w^2, y' w^3) the slope is lambda' w, so the line
+// through T at P is  y_P - lambda' x_P w + (lambda' x' - y') w^3.
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/ace.h"
+#include "field.cuh"
+
+namespace ace {
+void set_error(const char* fmt, ...);
+void clear_error();
+}  // namespace ace
+
+namespace ace {
+namespace {
+
+typedef fp2_t F2;
+struct F6 {
+    F2 a0, a1, a2;
+};
+struct F12 {
+    F6 c0, c1;
+};
+
+F2 f2_zero() { return field_zero<fp2_t>(); }
+F2 f2_one() { return field_one<fp2_t>(); }
+F2 f2_conj(const F2& a) { return {a.c0, fe_neg(a.c1)}; }
+F2 f2_scale(const F2& a, const fp_t& s) { return {a.c0 * s, a.c1 * s}; }
+// (a0 + a1 u)(9 + u) = (9 a0 - a1) + (a0 + 9 a1) u
+F2 mul_xi(const F2& a) {
+    fp_t nine = fe_from_u32<FpCfg>(9);
+    return {a.c0 * nine - a.c1, a.c0 + a.c1 * nine};
+}
+
+F6 f6_zero() { return {f2_zero(), f2_zero(), f2_zero()}; }
+F6 f6_one() { return {f2_one(), f2_zero(), f2_zero()}; }
+F6 operator+(const F6& a, const F6& b) { return {a.a0 + b.a0, a.a1 + b.a1, a.a2 + b.a2}; }
+F6 operator-(const F6& a, const F6& b) { return {a.a0 - b.a0, a.a1 - b.a1, a.a2 - b.a2}; }
+F6 f6_neg(const F6& a) { return {fe_neg(a.a0), fe_neg(a.a1), fe_neg(a.a2)}; }
+F6 operator*(const F6& a, const F6& b) {
+    F2 c0 = a.a0 * b.a0 + mul_xi(a.a1 * b.a2 + a.a2 * b.a1);
+    F2 c1 = a.a0 * b.a1 + a.a1 * b.a0 + mul_xi(a.a2 * b.a2);
+    F2 c2 = a.a0 * b.a2 + a.a1 * b.a1 + a.a2 * b.a0;
+    return {c0, c1, c2};
+}
+F6 mul_v(const F6& a) { return {mul_xi(a.a2), a.a0, a.a1}; }
+F6 f6_inv(const F6& a) {
+    F2 t0 = fe_sqr(a.a0) - mul_xi(a.a1 * a.a2);
+    F2 t1 = mul_xi(fe_sqr(a.a2)) - a.a0 * a.a1;
+    F2 t2 = fe_sqr(a.a1) - a.a0 * a.a2;
+    F2 d = a.a0 * t0 + mul_xi(a.a2 * t1 + a.a1 * t2);
+    F2 di = fe_inv(d);
+    return {t0 * di, t1 * di, t2 * di};
+}
+bool f6_eq(const F6& a, const F6& b) { return fe_eq(a.a0, b.a0) && fe_eq(a.a1, b.a1) && fe_eq(a.a2, b.a2); }
+
+F12 f12_one() { return {f6_one(), f6_zero()}; }
+F12 operator*(const F12& a, const F12& b) {
+    F6 t0 = a.c0 * b.c0, t1 = a.c1 * b.c1;
+    return {t0 + mul_v(t1), a.c0 * b.c1 + a.c1 * b.c0};
+}
+F12 f12_conj(const F12& a) { return {a.c0, f6_neg(a.c1)}; }
+F12 f12_inv(const F12& a) {
+    F6 d = a.c0 * a.c0 - mul_v(a.c1 * a.c1);
+    F6 di = f6_inv(d);
+    return {a.c0 * di, f6_neg(a.c1 * di)};
+}
+bool f12_eq(const F12& a, const F12& b) { return f6_eq(a.c0, b.c0) && f6_eq(a.c1, b.c1); }
+
+// ---- constants -------------------------------------------------------------
+struct Consts {
+    F2 gamma[6];                 // xi^(k (p-1)/6): Frobenius of w^k
+    F2 b2;                       // twist coefficient 3/xi
+    std::vector<uint32_t> hard;  // (p^4 - p^2 + 1) / r
+    unsigned __int128 ate = 0;   // 6x + 2 (a 65-bit value)
+};
+
+// small multi-precision helpers on little-endian 32-bit limbs
+typedef std::vector<uint32_t> Big;
+Big big_from(const uint32_t* l, int n) { return Big(l, l + n); }
+Big big_mul(const Big& a, const Big& b) {
+    Big r(a.size() + b.size(), 0);
+    for (size_t i = 0; i < a.size(); i++) {
+        uint64_t c = 0;
+        for (size_t j = 0; j < b.size(); j++) {
+            c += (uint64_t)r[i + j] + (uint64_t)a[i] * b[j];
+            r[i + j] = (uint32_t)c;
+            c >>= 32;
+        }
+        for (size_t k = i + b.size(); c; k++) {
+            c += r[k];
+            r[k] = (uint32_t)c;
+            c >>= 32;
+        }
+    }
+    return r;
+}
+void big_add_small(Big& a, uint32_t v, bool sub) {
+    uint64_t c = v;
+    for (size_t i = 0; i < a.size() && c; i++) {
+        if (sub) {
+            uint32_t old = a[i];
+            a[i] = old - (uint32_t)c;
+            c = old < c ? 1 : 0;
+        } else {
+            c += a[i];
+            a[i] = (uint32_t)c;
+            c >>= 32;
+        }
+    }
+}
+Big big_sub(const Big& a, const Big& b) {  // a >= b
+    Big r(a);
+    int64_t br = 0;
+    for (size_t i = 0; i < r.size(); i++) {
+        int64_t x = (int64_t)r[i] - (i < b.size() ? b[i] : 0) + br;
+        r[i] = (uint32_t)x;
+        br = x < 0 ? -1 : 0;
+    }
+    return r;
+}
+// quotient of a by the 254-bit modulus d (remainder must be 0)
+bool big_div_exact(const Big& a, const uint32_t d[8], Big& q) {
+    q.assign(a.size(), 0);
+    Big rem(9, 0);
+    for (int bit = (int)a.size() * 32 - 1; bit >= 0; bit--) {
+        uint32_t carry = (a[bit >> 5] >> (bit & 31)) & 1u;
+        for (int i = 0; i < 9; i++) {
+            uint32_t nc = rem[i] >> 31;
+            rem[i] = (rem[i] << 1) | carry;
+            carry = nc;
+        }
+        bool ge = rem[8] != 0;
+        if (!ge) {
+            ge = true;
+            for (int i = 7; i >= 0; i--) {
+                if (rem[i] != d[i]) {
+                    ge = rem[i] > d[i];
+                    break;
+                }
+            }
+        }
+        if (ge) {
+            int64_t br = 0;
+            for (int i = 0; i < 9; i++) {
+                int64_t x = (int64_t)rem[i] - (i < 8 ? d[i] : 0) + br;
+                rem[i] = (uint32_t)x;
+                br = x < 0 ? -1 : 0;
+            }
+            q[bit >> 5] |= 1u << (bit & 31);
+        }
+    }
+    for (uint32_t v : rem)
+        if (v) return false;
+    return true;
+}
+
+F2 f2_pow(const F2& a, const Big& e) {
+    F2 acc = f2_one();
+    for (int i = (int)e.size() * 32 - 1; i >= 0; i--) {
+        acc = fe_sqr(acc);
+        if ((e[i >> 5] >> (i & 31)) & 1u) acc = acc * a;
+    }
+    return acc;
+}
+
+Consts make_consts() {
+    Consts c;
+    uint32_t pl[8], rl[8];
+    for (int i = 0; i < 8; i++) {
+        pl[i] = mod_limb<FpCfg>(i);
+        rl[i] = mod_limb<FrCfg>(i);
+    }
+    Big p = big_from(pl, 8);
+    // (p - 1) / 6, then k (p - 1) / 6
+    Big pm1 = p;
+    big_add_small(pm1, 1, true);
+    Big e6;
+    {
+        // divide by 6 (small divisor)
+        e6.assign(pm1.size(), 0);
+        uint64_t rem = 0;
+        for (int i = (int)pm1.size() - 1; i >= 0; i--) {
+            uint64_t cur = (rem << 32) | pm1[i];
+            e6[i] = (uint32_t)(cur / 6);
+            rem = cur % 6;
+        }
+    }
+    F2 xi = {fe_from_u32<FpCfg>(9), fe_from_u32<FpCfg>(1)};
+    for (int k = 0; k < 6; k++) {
+        Big kk(1, (uint32_t)k);
+        c.gamma[k] = f2_pow(xi, big_mul(e6, kk));
+    }
+    F2 three = {fe_from_u32<FpCfg>(3), fe_zero<FpCfg>()};
+    c.b2 = three * fe_inv(xi);
+    // (p^4 - p^2 + 1) / r
+    Big p2 = big_mul(p, p);
+    Big p4 = big_mul(p2, p2);
+    Big num = big_sub(p4, p2);
+    big_add_small(num, 1, false);
+    Big q;
+    big_div_exact(num, rl, q);
+    while (q.size() > 1 && q.back() == 0) q.pop_back();
+    c.hard = q;
+    c.ate = (unsigned __int128)6 * 4965661367192848881ull + 2u;
+    return c;
+}
+
+// built once, thread-safely, on first use
+const Consts& consts() {
+    static const Consts c = make_consts();
+    return c;
+}
+
+// a^p: coefficient of w^k is conjugated and multiplied by gamma_k.
+// Basis order: c0 = (w^0, w^2, w^4), c1 = (w^1, w^3, w^5).
+F12 frobenius(const F12& a) {
+    const Consts& k = consts();
+    F12 r;
+    r.c0.a0 = f2_conj(a.c0.a0) * k.gamma[0];
+    r.c0.a1 = f2_conj(a.c0.a1) * k.gamma[2];
+    r.c0.a2 = f2_conj(a.c0.a2) * k.gamma[4];
+    r.c1.a0 = f2_conj(a.c1.a0) * k.gamma[1];
+    r.c1.a1 = f2_conj(a.c1.a1) * k.gamma[3];
+    r.c1.a2 = f2_conj(a.c1.a2) * k.gamma[5];
+    return r;
+}
+
+F12 f12_pow(const F12& a, const Big& e) {
+    F12 acc = f12_one();
+    for (int i = (int)e.size() * 32 - 1; i >= 0; i--) {
+        acc = acc * acc;
+        if ((e[i >> 5] >> (i & 31)) & 1u) acc = acc * a;
+    }
+    return acc;
+}
+
+F12 final_exp(const F12& f) {
+    F12 t = f12_conj(f) * f12_inv(f);          // f^(p^6 - 1)
+    t = frobenius(frobenius(t)) * t;           // ^(p^2 + 1)
+    return f12_pow(t, consts().hard);          // ^((p^4 - p^2 + 1)/r)
+}
+
+struct G2a {
+    F2 x, y;
+    bool inf;
+};
+
+// line through T with twist slope lam, evaluated at P = (xp, yp)
+F12 line(const F2& lam, const F2& xt, const F2& yt, const fp_t& xp, const fp_t& yp) {
+    F12 l;
+    l.c0 = f6_zero();
+    l.c1 = f6_zero();
+    l.c0.a0 = {yp, fe_zero<FpCfg>()};
+    l.c1.a0 = fe_neg(f2_scale(lam, xp));
+    l.c1.a1 = lam * xt - yt;
+    return l;
+}
+
+// one Miller step: f *= l_{T,S}(P), T = T + S (S == T: tangent)
+bool miller_step(F12& f, G2a& T, const G2a& S, const fp_t& xp, const fp_t& yp) {
+    F2 lam;
+    if (fe_eq(T.x, S.x)) {
+        if (!fe_eq(T.y, S.y) || fe_is_zero(T.y)) return false;  // vertical: not reached for valid inputs
+        F2 xx = fe_sqr(T.x);
+        lam = (xx + xx + xx) * fe_inv(T.y + T.y);
+    } else {
+        lam = (S.y - T.y) * fe_inv(S.x - T.x);
+    }
+    f = f * line(lam, T.x, T.y, xp, yp);
+    F2 x3 = fe_sqr(lam) - T.x - S.x;
+    F2 y3 = lam * (T.x - x3) - T.y;
+    T.x = x3;
+    T.y = y3;
+    return true;
+}
+
+// Miller function of the optimal ate pairing (before the final exponentiation)
+bool miller(const fp_t& xp, const fp_t& yp, const G2a& Q, F12& out) {
+    const Consts& k = consts();
+    F12 f = f12_one();
+    G2a T = Q;
+    int top = 127;
+    while (!((k.ate >> top) & 1u)) top--;
+    for (int i = top - 1; i >= 0; i--) {
+        f = f * f;
+        if (!miller_step(f, T, T, xp, yp)) return false;
+        if ((unsigned)(k.ate >> i) & 1u)
+            if (!miller_step(f, T, Q, xp, yp)) return false;
+    }
+    // pi(Q) = (conj(x) gamma_2, conj(y) gamma_3); -pi^2(Q) = (x gamma_2 conj(gamma_2), -y gamma_3 conj(gamma_3))
+    G2a Q1 = {f2_conj(Q.x) * k.gamma[2], f2_conj(Q.y) * k.gamma[3], false};
+    G2a Q2 = {Q.x * k.gamma[2] * f2_conj(k.gamma[2]), fe_neg(Q.y * k.gamma[3] * f2_conj(k.gamma[3])), false};
+    if (!miller_step(f, T, Q1, xp, yp)) return false;
+    if (!miller_step(f, T, Q2, xp, yp)) return false;
+    out = f;
+    return true;
+}
+
+bool read_fp(const uint8_t* b, fp_t& out) {
+    memcpy(out.v, b, 32);
+    if (fe_geq_mod(out)) return false;
+    out = fe_to_mont(out);
+    return true;
+}
+bool read_g1(const uint8_t* b, fp_t& x, fp_t& y, bool& inf) {
+    if (!read_fp(b, x) || !read_fp(b + 32, y)) return false;
+    inf = fe_is_zero(x) && fe_is_zero(y);
+    if (inf) return true;
+    return fe_eq(fe_sqr(y), fe_sqr(x) * x + fe_from_u32<FpCfg>(3));
+}
+bool read_g2(const uint8_t* b, G2a& q) {
+    if (!read_fp(b, q.x.c0) || !read_fp(b + 32, q.x.c1) || !read_fp(b + 64, q.y.c0) || !read_fp(b + 96, q.y.c1))
+        return false;
+    q.inf = fe_is_zero(q.x) && fe_is_zero(q.y);
+    if (q.inf) return true;
+    return fe_eq(fe_sqr(q.y), fe_sqr(q.x) * q.x + consts().b2);
+}
+
+// r Q == O on the twist (subgroup membership), affine double-and-add
+bool g2_in_subgroup(const G2a& q) {
+    if (q.inf) return true;
+    uint32_t rl[8];
+    for (int i = 0; i < 8; i++) rl[i] = mod_limb<FrCfg>(i);
+    G2a acc = {f2_zero(), f2_zero(), true};
+    for (int i = 253; i >= 0; i--) {
+        // acc = 2 acc
+        if (!acc.inf) {
+            if (fe_is_zero(acc.y)) {
+                acc.inf = true;
+            } else {
+                F2 xx = fe_sqr(acc.x);
+                F2 lam = (xx + xx + xx) * fe_inv(acc.y + acc.y);
+                F2 x3 = fe_sqr(lam) - acc.x - acc.x;
+                acc.y = lam * (acc.x - x3) - acc.y;
+                acc.x = x3;
+            }
+        }
+        if ((rl[i >> 5] >> (i & 31)) & 1u) {
+            if (acc.inf) {
+                acc = q;
+            } else if (fe_eq(acc.x, q.x)) {
+                if (fe_eq(acc.y, q.y)) {
+                    F2 xx = fe_sqr(acc.x);
+                    F2 lam = (xx + xx + xx) * fe_inv(acc.y + acc.y);
+                    F2 x3 = fe_sqr(lam) - acc.x - acc.x;
+                    acc.y = lam * (acc.x - x3) - acc.y;
+                    acc.x = x3;
+                } else {
+                    acc.inf = true;
+                }
+            } else {
+                F2 lam = (q.y - acc.y) * fe_inv(q.x - acc.x);
+                F2 x3 = fe_sqr(lam) - acc.x - q.x;
+                acc.y = lam * (acc.x - x3) - acc.y;
+                acc.x = x3;
+            }
+        }
+    }
+    return acc.inf;
+}
+
+// affine G1 helpers for the input term ic0 + x ic1
+struct G1a {
+    fp_t x, y;
+    bool inf;
+};
+G1a g1_add(const G1a& a, const G1a& b) {
+    if (a.inf) return b;
+    if (b.inf) return a;
+    fp_t lam;
+    if (fe_eq(a.x, b.x)) {
+        if (!fe_eq(a.y, b.y) || fe_is_zero(a.y)) return {fe_zero<FpCfg>(), fe_zero<FpCfg>(), true};
+        fp_t xx = fe_sqr(a.x);
+        lam = (xx + xx + xx) * fe_inv(a.y + a.y);
+    } else {
+        lam = (b.y - a.y) * fe_inv(b.x - a.x);
+    }
+    fp_t x3 = fe_sqr(lam) - a.x - b.x;
+    return {x3, lam * (a.x - x3) - a.y, false};
+}
+G1a g1_mul(const G1a& p, const uint32_t k[8]) {
+    G1a acc = {fe_zero<FpCfg>(), fe_zero<FpCfg>(), true};
+    for (int i = 255; i >= 0; i--) {
+        acc = g1_add(acc, acc);
+        if ((k[i >> 5] >> (i & 31)) & 1u) acc = g1_add(acc, p);
+    }
+    return acc;
+}
+
+}  // namespace
+
+// product of pairings e(P_i, Q_i) == 1 ?  (P, Q given in Montgomery affine)
+int pairing_product_is_one(int n, const fp_t* px, const fp_t* py, const bool* pinf, const G2a* q) {
+    F12 acc = f12_one();
+    for (int i = 0; i < n; i++) {
+        if (pinf[i] || q[i].inf) continue;
+        F12 f;
+        if (!miller(px[i], py[i], q[i], f)) return -1;
+        acc = acc * f;
+    }
+    return f12_eq(final_exp(acc), f12_one()) ? 1 : 0;
+}
+
+}  // namespace ace
+
+using namespace ace;
+
+extern "C" {
+
+int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t proof[256]) {
+    clear_error();
+    if (!vk || !pub || !proof) {
+        set_error("ace_verify: NULL argument");
+        return ACE_E_ARG;
+    }
+    if (n_pub != 1) {
+        set_error("ace_verify: the circuit has exactly one public input (n_pub = %zu)", n_pub);
+        return ACE_E_ARG;
+    }
+    fr_t x;
+    memcpy(x.v, pub->l, 32);
+    if (fe_geq_mod(x)) {
+        set_error("ace_verify: public input not canonical");
+        return ACE_E_ARG;
+    }
+    fp_t ax, ay, cx, cy;
+    bool ainf, cinf;
+    G2a B;
+    if (!read_g1(proof, ax, ay, ainf) || !read_g1(proof + 192, cx, cy, cinf) || !read_g2(proof + 64, B)) {
+        set_error("ace_verify: proof point not on the curve or not canonical");
+        return ACE_E_NOT_ON_CURVE;
+    }
+    if (!g2_in_subgroup(B)) return 0;
+    const uint8_t* v = (const uint8_t*)vk;
+    fp_t alx, aly, i0x, i0y, i1x, i1y;
+    bool alinf, i0inf, i1inf;
+    G2a beta, gamma, delta;
+    if (!read_g1(v, alx, aly, alinf) || !read_g2(v + 64, beta) || !read_g2(v + 192, gamma) ||
+        !read_g2(v + 320, delta) || !read_g1(v + 448, i0x, i0y, i0inf) || !read_g1(v + 512, i1x, i1y, i1inf)) {
+        set_error("ace_verify: verifying key point not on the curve");
+        return ACE_E_NOT_ON_CURVE;
+    }
+    G1a ic = g1_add({i0x, i0y, i0inf}, g1_mul({i1x, i1y, i1inf}, x.v));
+    // e(-A, B) e(alpha, beta) e(IC, gamma) e(C, delta) == 1
+    fp_t px[4] = {ax, alx, ic.x, cx};
+    fp_t py[4] = {fe_neg(ay), aly, ic.y, cy};
+    bool pinf[4] = {ainf, alinf, ic.inf, cinf};
+    G2a q[4] = {B, beta, gamma, delta};
+    int rc = pairing_product_is_one(4, px, py, pinf, q);
+    if (rc < 0) {
+        set_error("ace_verify: degenerate Miller loop");
+        return 0;
+    }
+    return rc;
+}
+
+// Diagnostic: e(P, Q) as 12 canonical Fp limbs-triples, tower order
+// (c0.a0, c0.a1, c0.a2, c1.a0, c1.a1, c1.a2; each Fp2 as c0, c1).
+int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]) {
+    fp_t x, y;
+    bool inf;
+    G2a q;
+    if (!read_g1(g1, x, y, inf) || !read_g2(g2, q)) return ACE_E_NOT_ON_CURVE;
+    F12 f = f12_one();
+    if (!inf && !q.inf && !miller(x, y, q, f)) return ACE_E_ARG;
+    f = final_exp(f);
+    const F2* c[6] = {&f.c0.a0, &f.c0.a1, &f.c0.a2, &f.c1.a0, &f.c1.a1, &f.c1.a2};
+    for (int i = 0; i < 6; i++) {
+        fp_t a = fe_from_mont(c[i]->c0), b = fe_from_mont(c[i]->c1);
+        memcpy(out + 64 * i, a.v, 32);
+        memcpy(out + 64 * i + 32, b.v, 32);
+    }
+    return ACE_OK;
+}
+
+}  // extern "C"

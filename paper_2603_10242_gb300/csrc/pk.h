@@ -1,0 +1,54 @@
+// pk.h -- device-resident Groth16 proving key (internal).
+#pragma once
+#include <vector>
+
+#include "circuit.h"
+#include "curve.cuh"
+#include "msm.cuh"
+#include "ntt.cuh"
+#include "runtime.cuh"
+
+namespace ace {
+
+// fixed points of the key, Montgomery affine, kept together on the device
+struct PkFixed {
+    g1_aff alpha1, beta1, delta1;
+    g2_aff beta2, delta2;
+};
+
+// one compacted MSM query: points whose setup scalar is non-zero, and the
+// witness index each one multiplies
+template <class F>
+struct Query {
+    uint32_t count = 0;
+    uint32_t* d_idx = nullptr;        // count (witness indices)
+    Affine<F>* d_pts = nullptr;       // count (Montgomery affine)
+    std::vector<uint32_t> h_idx;      // host copy of the indices (ascending)
+};
+
+}  // namespace ace
+
+struct ace_pk {
+    ace_ctx* ctx = nullptr;
+    ace_circuit_params params;
+    uint64_t N = 0, m = 0;
+    int log_n = 0;
+    // R1CS on the device (CSR; values in Montgomery form)
+    uint32_t* d_rp[3] = {};
+    uint32_t* d_col[3] = {};
+    ace::fr_t* d_val[3] = {};
+    uint64_t nnz[3] = {};
+    ace::Query<ace::fp_t> A, B1, L;
+    ace::Query<ace::fp2_t> B2;   // same indices as B1
+    ace::g1_aff* d_H = nullptr;  // N points: d_H[p] = H_{bitrev(p)}, H_{N-1} = infinity
+    ace::PkFixed* d_fixed = nullptr;
+    ace_vk vk;
+    size_t bytes = 0;            // device bytes held
+    std::vector<std::pair<void*, size_t>> allocs;
+    // host copy of the circuit (for ace_pk_save)
+    ace_circuit* circ = nullptr;
+};
+
+namespace ace {
+int pk_alloc(ace_pk* pk, void** p, size_t bytes);
+}  // namespace ace

@@ -1,0 +1,337 @@
+// prove.cu -- the Groth16 prover on the device: Groth16.Prove of the paper's
+// Phase 2 (Section 3.1, Algorithm 1 ProveAsync; Section 3.3, Algorithm 3
+// Stage 1), producing the 256-byte proof of Section 3.3 / Appendix B.
+//
+//   1. a, b, c = Az, Bz, Cz (one thread per row, all three matrices), with
+//      the R1CS check a_i b_i = c_i folded in (status word on failure);
+//   2. QAP quotient: inverse NTT of a, b, c (decimation in frequency, scaled
+//      by g^e / N on the way out: coset coefficients), forward NTT
+//      (decimation in time: values on g H), q = (a b - c)/(g^N - 1), inverse
+//      NTT scaled by g^-e / N leaving canonical h in bit-reversed order;
+//   3. five MSMs on their own streams: H (h, bit-reversed H query) on the
+//      main stream, A, B1 (G1), B2 (G2) and L on auxiliary streams, with the
+//      witness gathered per compacted query; the fixed-base terms r delta,
+//      s delta, r s delta run alongside;
+//   4. assembly: A = alpha + S_A + r delta, B = beta + S_B2 + s delta,
+//      B1 = beta + S_B1 + s delta, C = S_L + S_H + s A + r B1 - r s delta,
+//      s A + r B1 by one joint double-and-add; affine, canonical bytes.
+#include <string.h>
+
+#include "pk.h"
+
+namespace ace {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ fr_t ldg_fr(const fr_t* p) {
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4 a = __ldg(s), b = __ldg(s + 1);
+    fr_t r;
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+    r.v[4] = b.x; r.v[5] = b.y; r.v[6] = b.z; r.v[7] = b.w;
+    return r;
+}
+__device__ __forceinline__ void st_fr2(fr_t* p, const fr_t& x) {
+    uint4* d = reinterpret_cast<uint4*>(p);
+    d[0] = make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]);
+    d[1] = make_uint4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+
+struct CsrDev {
+    const uint32_t* rp[3];
+    const uint32_t* col[3];
+    const fr_t* val[3];
+};
+
+// a, b, c (Montgomery) for every row; z canonical.  The product of a
+// Montgomery coefficient and a canonical z_j is the canonical product, so the
+// row sums are canonical and one multiplication by R^2 mod r returns them to
+// Montgomery form.
+__global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const fr_t* __restrict__ z, uint32_t N, fr_t* abc,
+                                               int32_t* status) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    fr_t v[3];
+#pragma unroll 1
+    for (int k = 0; k < 3; k++) {
+        fr_t acc = fe_zero<FrCfg>();
+        uint32_t b = m.rp[k][i], e = m.rp[k][i + 1];
+        for (uint32_t t = b; t < e; t++) acc = acc + ldg_fr(m.val[k] + t) * ldg_fr(z + __ldg(m.col[k] + t));
+        v[k] = acc * fe_rr<FrCfg>();
+        st_fr2(abc + (size_t)k * N + i, v[k]);
+    }
+    if (!fe_eq(v[0] * v[1], v[2])) atomicOr(status, 1);
+}
+
+// q_i = (a_i b_i - c_i) * zinv, written over a
+__global__ void k_quotient(fr_t* abc, uint32_t N, fr_t zinv) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    fr_t a = ldg_fr(abc + i), b = ldg_fr(abc + N + i), c = ldg_fr(abc + 2 * (size_t)N + i);
+    st_fr2(abc + i, (a * b - c) * zinv);
+}
+
+__global__ void k_gather(const fr_t* __restrict__ z, const uint32_t* __restrict__ idx, uint32_t n, fr_t* out) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    st_fr2(out + k, ldg_fr(z + __ldg(idx + k)));
+}
+
+// the fixed-base terms: r delta1, s delta1, r s delta1 (G1) and s delta2 (G2)
+__global__ void k_prove_smul(const PkFixed* fx, fr_t r, fr_t s, fr_t rs, g1_xyzz* o1, g2_xyzz* o2) {
+    int t = threadIdx.x;
+    if (t == 0) o1[0] = xyzz_mul_aff(fx->delta1, r.v);
+    if (t == 1) o1[1] = xyzz_mul_aff(fx->delta1, s.v);
+    if (t == 2) o1[2] = xyzz_mul_aff(fx->delta1, rs.v);
+    if (t == 3) o2[0] = xyzz_mul_aff(fx->delta2, s.v);
+}
+
+__device__ void write_g1(uint32_t* dst, const g1_xyzz& p) {
+    g1_aff a = aff_from_mont(xyzz_to_aff(p));
+    for (int i = 0; i < 8; i++) {
+        dst[i] = a.x.v[i];
+        dst[8 + i] = a.y.v[i];
+    }
+}
+
+// res1: S_H, S_A, S_B1, S_L; sm1: r delta1, s delta1, r s delta1; sm2: s delta2
+__global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2, const g1_xyzz* sm1,
+                           const g2_xyzz* sm2, fr_t r, fr_t s, uint32_t* proof) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    g1_xyzz A = xyzz_add(xyzz_add(xyzz_from_aff(fx->alpha1), res1[1]), sm1[0]);
+    g2_xyzz B = xyzz_add(xyzz_add(xyzz_from_aff(fx->beta2), resB2[0]), sm2[0]);
+    g1_xyzz B1 = xyzz_add(xyzz_add(xyzz_from_aff(fx->beta1), res1[2]), sm1[1]);
+    // s A + r B1, joint double-and-add over the bits of s and r
+    g1_aff Aa = xyzz_to_aff(A), Ba = xyzz_to_aff(B1), Ta = xyzz_to_aff(xyzz_add(A, B1));
+    g1_xyzz acc = xyzz_inf<fp_t>();
+    for (int i = 255; i >= 0; i--) {
+        acc = xyzz_dbl(acc);
+        uint32_t bs = (s.v[i >> 5] >> (i & 31)) & 1u, br = (r.v[i >> 5] >> (i & 31)) & 1u;
+        if (bs && br) acc = xyzz_add_aff(acc, Ta);
+        else if (bs) acc = xyzz_add_aff(acc, Aa);
+        else if (br) acc = xyzz_add_aff(acc, Ba);
+    }
+    g1_xyzz C = xyzz_add(xyzz_add(res1[3], res1[0]), acc);
+    C = xyzz_add(C, xyzz_neg(sm1[2]));
+    write_g1(proof, A);
+    g2_aff b = aff_from_mont(xyzz_to_aff(B));
+    for (int i = 0; i < 8; i++) {
+        proof[16 + i] = b.x.c0.v[i];
+        proof[24 + i] = b.x.c1.v[i];
+        proof[32 + i] = b.y.c0.v[i];
+        proof[40 + i] = b.y.c1.v[i];
+    }
+    write_g1(proof + 48, C);
+}
+
+// ---------------------------------------------------------------------------
+// drivers
+// ---------------------------------------------------------------------------
+static CsrDev csr_of(const ace_pk* pk) {
+    CsrDev m;
+    for (int k = 0; k < 3; k++) {
+        m.rp[k] = pk->d_rp[k];
+        m.col[k] = pk->d_col[k];
+        m.val[k] = pk->d_val[k];
+    }
+    return m;
+}
+
+// steps 1-2: leaves canonical h in bit-reversed order in abc[0..N)
+int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t* d_status, cudaStream_t st) {
+    NttPlan* plan = nullptr;
+    ACE_TRY(ntt_get_plan(ctx, pk->log_n, &plan));
+    const uint32_t N = (uint32_t)pk->N;
+    k_spmv3<<<(N + 255) / 256, 256, 0, st>>>(csr_of(pk), d_z, N, abc, d_status);
+    NttScale none, cos, icos;
+    cos.hi = plan->cos_hi;
+    cos.lo = plan->cos_lo;
+    cos.h = plan->h;
+    cos.brev = 1;
+    icos.hi = plan->icos_hi;
+    icos.lo = plan->icos_lo;
+    icos.h = plan->h;
+    icos.brev = 1;
+    ACE_TRY(ntt_run(*plan, abc, 3, true, true, none, cos, st));
+    ACE_TRY(ntt_run(*plan, abc, 3, false, false, none, none, st));
+    k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, plan->zinv);
+    ACE_TRY(ntt_run(*plan, abc, 1, true, true, none, icos, st));
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+struct ProvePlans {
+    MsmPlan H, A, B, L;
+    size_t slot_bytes[5];
+};
+
+static ProvePlans prove_plans(const ace_pk* pk) {
+    ProvePlans p;
+    p.H = msm_plan(pk->N);
+    p.A = msm_plan(pk->A.count);
+    p.B = msm_plan(pk->B1.count);
+    p.L = msm_plan(pk->L.count);
+    size_t N = pk->N;
+    p.slot_bytes[0] = 3 * N * sizeof(fr_t) + msm_scratch_bytes<fp_t>(p.H, true) + (1 << 16);
+    p.slot_bytes[1] = pk->A.count * sizeof(fr_t) + msm_scratch_bytes<fp_t>(p.A, true) + 4096;
+    p.slot_bytes[2] = pk->B1.count * sizeof(fr_t) + msm_scratch_bytes<fp_t>(p.B, true) + 4096;
+    p.slot_bytes[3] = pk->B2.count * sizeof(fr_t) + msm_scratch_bytes<fp2_t>(p.B, true) + 4096;
+    p.slot_bytes[4] = pk->L.count * sizeof(fr_t) + msm_scratch_bytes<fp_t>(p.L, true) + 4096;
+    return p;
+}
+
+template <class F>
+static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z, Arena& ar, Xyzz<F>* res,
+                        cudaStream_t s) {
+    fr_t* zq = (fr_t*)ar.take((size_t)q.count * sizeof(fr_t) + 32);
+    if (!zq) {
+        set_error("prove: arena too small");
+        return ACE_E_OOM;
+    }
+    if (q.count) k_gather<<<(q.count + 255) / 256, 256, 0, s>>>(d_z, q.d_idx, q.count, zq);
+    return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
+}
+
+// Full proof on stream st; writes 64 words of proof to d_proof (device) and
+// the R1CS status to d_status (0 ok, 1 unsat).  Scratch: context arenas 0-4.
+int prove_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s, uint32_t* d_proof,
+              int32_t* d_status, cudaStream_t st) {
+    ACE_TRY(ctx_aux_streams(ctx));
+    ProvePlans pl = prove_plans(pk);
+    for (int k = 0; k < 5; k++) ACE_TRY(arena_ensure(ctx, k, pl.slot_bytes[k]));
+    Arena& a0 = ctx->scratch[0];
+    fr_t* abc = (fr_t*)a0.take(3 * pk->N * sizeof(fr_t));
+    g1_xyzz* res1 = (g1_xyzz*)a0.take(8 * sizeof(g1_xyzz));
+    g2_xyzz* res2 = (g2_xyzz*)a0.take(2 * sizeof(g2_xyzz));
+    if (!abc || !res1 || !res2) {
+        set_error("prove: arena too small");
+        return ACE_E_OOM;
+    }
+    g1_xyzz* sm1 = res1 + 4;
+    g2_xyzz* sm2 = res2 + 1;
+    // r s mod r on the host
+    fr_t rs = fe_from_mont(fe_to_mont(r) * fe_to_mont(s));
+
+    cudaEvent_t ev_start = ctx->ev[0];
+    ACE_TRY_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
+    ACE_TRY_CUDA(cudaEventRecord(ev_start, st));
+    for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(ctx->aux[k], ev_start, 0));
+    // auxiliary streams: A, B1, B2, L MSMs and the fixed-base terms
+    ACE_TRY(gathered_msm<fp_t>(pl.A, pk->A, d_z, ctx->scratch[1], res1 + 1, ctx->aux[0]));
+    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, ctx->scratch[2], res1 + 2, ctx->aux[1]));
+    ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, ctx->scratch[3], res2, ctx->aux[2]));
+    ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, ctx->scratch[4], res1 + 3, ctx->aux[3]));
+    k_prove_smul<<<1, 32, 0, ctx->aux[4]>>>(pk->d_fixed, r, s, rs, sm1, sm2);
+    // main stream: QAP then the H MSM
+    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, st));
+    MsmPlan ph = pl.H;
+    ACE_TRY(msm_run<fp_t>(ph, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, st));
+    for (int k = 0; k < 5; k++) {
+        ACE_TRY_CUDA(cudaEventRecord(ctx->ev[1 + k], ctx->aux[k]));
+        ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->ev[1 + k], 0));
+    }
+    k_assemble<<<1, 32, 0, st>>>(pk->d_fixed, res1, res2, sm1, sm2, r, s, d_proof);
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+static bool canonical_fr(const ace_fr* x) {
+    fr_t t;
+    memcpy(t.v, x->l, 32);
+    return !fe_geq_mod(t);
+}
+
+}  // namespace ace
+
+using namespace ace;
+
+extern "C" {
+
+int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out, ace_stream stream) {
+    clear_error();
+    if (!ctx || !pk || !d_z || !d_h_out) {
+        set_error("ace_qap_h: NULL argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = pick_stream(ctx, stream);
+    ACE_TRY(arena_ensure(ctx, 0, 3 * pk->N * sizeof(fr_t) + 4096));
+    fr_t* abc = (fr_t*)ctx->scratch[0].take(3 * pk->N * sizeof(fr_t));
+    int32_t* status = (int32_t*)ctx->scratch[0].take(16);
+    ACE_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    ACE_TRY(qap_run(ctx, pk, (const fr_t*)d_z, abc, status, st));
+    return fr_bitrev_copy(abc, (fr_t*)d_h_out, pk->log_n, 1, st);
+}
+
+int ace_prove_async(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
+                    uint8_t* d_proof_out, int32_t* d_status, ace_stream stream) {
+    clear_error();
+    if (!ctx || !pk || !d_z || !r || !s || !d_proof_out || !d_status) {
+        set_error("ace_prove_async: NULL argument");
+        return ACE_E_ARG;
+    }
+    if (!canonical_fr(r) || !canonical_fr(s)) {
+        set_error("ace_prove: r and s must be canonical Fr values");
+        return ACE_E_ARG;
+    }
+    if (((uintptr_t)d_z & 15u) || ((uintptr_t)d_proof_out & 3u) || ((uintptr_t)d_status & 3u)) {
+        set_error("ace_prove: d_z must be 16-byte aligned, outputs 4-byte aligned");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    fr_t rr, ss;
+    memcpy(rr.v, r->l, 32);
+    memcpy(ss.v, s->l, 32);
+    return prove_run(ctx, pk, (const fr_t*)d_z, rr, ss, (uint32_t*)d_proof_out, d_status, pick_stream(ctx, stream));
+}
+
+int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
+              uint8_t proof_out[256], ace_stream stream) {
+    clear_error();
+    if (!proof_out) {
+        set_error("ace_prove: proof_out is NULL");
+        return ACE_E_ARG;
+    }
+    if (!ctx) {
+        set_error("ace_prove: NULL context");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    // proof and status words live past the per-proof scratch of arena 5
+    ACE_TRY(arena_ensure(ctx, 5, 512));
+    uint8_t* d_out = (uint8_t*)ctx->scratch[5].take(256);
+    int32_t* d_status = (int32_t*)ctx->scratch[5].take(16);
+    cudaStream_t st = pick_stream(ctx, stream);
+    ACE_TRY(ace_prove_async(ctx, pk, d_z, r, s, d_out, d_status, stream));
+    int32_t status = 0;
+    ACE_TRY_CUDA(cudaMemcpyAsync(proof_out, d_out, 256, cudaMemcpyDeviceToHost, st));
+    ACE_TRY_CUDA(cudaMemcpyAsync(&status, d_status, sizeof status, cudaMemcpyDeviceToHost, st));
+    ACE_TRY_CUDA(cudaStreamSynchronize(st));
+    if (status) {
+        set_error("ace_prove: witness does not satisfy the R1CS");
+        return ACE_E_UNSAT;
+    }
+    return ACE_OK;
+}
+
+int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs, const ace_fr* rs,
+                    const ace_fr* ss, uint8_t* proofs, int32_t* status) {
+    clear_error();
+    if (!ctx || (k && (!pks || !d_zs || !rs || !ss || !proofs || !status))) {
+        set_error("ace_prove_batch: NULL argument");
+        return ACE_E_ARG;
+    }
+    for (size_t i = 0; i < k; i++) {
+        int rc = ace_prove(ctx, pks[i], d_zs[i], rs + i, ss + i, proofs + 256 * i, nullptr);
+        if (rc == ACE_E_UNSAT) {
+            status[i] = 1;
+            continue;
+        }
+        if (rc != ACE_OK) return rc;
+        status[i] = 0;
+    }
+    return ACE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// runtime.cuh -- context, error reporting, device memory and scratch arenas
+// shared by the translation units of libace.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ace.h"
+
+namespace ace {
+
+// ---- errors -----------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+const char* last_error();
+
+#define ACE_TRY_CUDA(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            ::ace::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e),   \
+                             __FILE__, __LINE__);                                       \
+            return ACE_E_CUDA;                                                          \
+        }                                                                               \
+    } while (0)
+
+#define ACE_TRY(expr)                 \
+    do {                              \
+        int _rc = (expr);             \
+        if (_rc != ACE_OK) return _rc; \
+    } while (0)
+
+// ---- device memory -------------------------------------------------------------
+// A growable device buffer carved by bump allocation.  take() hands out
+// 256-byte-aligned pieces; reset() forgets them (the caller guarantees the
+// work using them is complete or ordered on the same stream).
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    void reset() { off = 0; }
+    void* take(size_t bytes) {
+        size_t a = (off + 255) & ~(size_t)255;
+        if (a + bytes > cap) return nullptr;
+        off = a + bytes;
+        return base + a;
+    }
+};
+
+// Sizing pass: the same carving sequence run without memory to learn the size.
+struct Sizer {
+    size_t off = 0;
+    void* take(size_t bytes) {
+        size_t a = (off + 255) & ~(size_t)255;
+        off = a + bytes;
+        return (void*)(uintptr_t)1;  // non-null marker, never dereferenced
+    }
+};
+
+struct NttPlan;  // twiddle tables for one size (ntt.cu)
+
+}  // namespace ace
+
+struct ace_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;  // 0 = unbounded
+    size_t held = 0;    // bytes of device memory held by caches and arenas
+    std::mutex mu;
+    ace::Arena scratch[8];  // slot 0: single calls; 1..: concurrent MSMs of a proof
+    cudaStream_t aux[8] = {};
+    cudaEvent_t ev[16] = {};
+    std::map<int, ace::NttPlan*> ntt_plans;
+    void* g1_fixed_tab = nullptr;  // fixed-base tables for the generators (setup.cu)
+    void* g2_fixed_tab = nullptr;
+};
+
+namespace ace {
+int dev_alloc(ace_ctx* ctx, void** p, size_t bytes);
+void dev_free(ace_ctx* ctx, void* p, size_t bytes);
+// make arena `slot` hold at least `bytes` (synchronises the device if it grows)
+int arena_ensure(ace_ctx* ctx, int slot, size_t bytes);
+inline cudaStream_t pick_stream(ace_ctx* ctx, ace_stream s) { return s ? (cudaStream_t)s : ctx->stream; }
+int ctx_aux_streams(ace_ctx* ctx);  // lazily create aux streams and events
+}  // namespace ace

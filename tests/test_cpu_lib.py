@@ -1,0 +1,133 @@
+"""CPU-side checks of the library: it builds, loads and exports every symbol
+of include/ace.h; its host logic (circuit generator, witness, prover
+randomness, Groth16 verifier) matches the oracle; the shared input
+generators follow the published SplitMix64 definition.  No GPU calls.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import pyref as Y
+import paper_2603_10242_gb300 as ace
+from paper_2603_10242_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ace.build()
+    return ace.lib()
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:int|const char\*)\s+(ace_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_sampler_matches_published_definition():
+    g = Y.SplitMix64(5, 7)
+    assert inputs.limbs_to_int(inputs.sample_fr(5, 7, 500)) == [g.fr() for _ in range(500)]
+    assert [int(x) for x in inputs.splitmix64(9, 3, 100)] == O.splitmix64(9, 3, 100)
+    sp = inputs.limbs_to_int(inputs.sample_scalars(11, 20000, "sparse"))
+    frac = sum(1 for v in sp if v in (0, 1)) / len(sp)
+    assert 0.68 < frac < 0.72
+    sel = Y.SplitMix64(11, inputs.PURPOSE["selector"])
+    uni = Y.SplitMix64(11, inputs.PURPOSE["scalars"])
+    for i in range(300):
+        u = sel.next()
+        want = (u >> 63) if u % 10 < 7 else uni.fr()
+        assert sp[i] == want
+
+
+@pytest.mark.parametrize("params", [(2, 4, 0, 0, 0), (3, 6, 0, 1, 3), (10, 1024, 4, 0, 0), (12, 4000, 8, 8, 172)])
+def test_host_circuit_and_witness_match_oracle(lib, params):
+    lc = ace.Circuit(*params, seed=4)
+    oc = O.Circuit(*params, seed=4, input_seed=6)
+    assert (lc.N, lc.m) == (oc.N, oc.m)
+    assert lc.info[4:7] == [oc.nnz_a, oc.nnz_b, oc.nnz_c]
+    assert lc.witness(6) == oc.witness()
+
+
+def test_circuit_parameter_errors(lib):
+    with pytest.raises(ace.AceError):
+        ace.Circuit(10, 1024, 5, 0, 0)        # 5 permutations need more than 1024 rows
+    with pytest.raises(ace.AceError):
+        ace.Circuit(1, 2, 0, 0, 0)            # domain too small
+    with pytest.raises(ace.AceError):
+        ace.Circuit(10, 2000, 0, 0, 0)        # n_rows > N
+
+
+def test_rs_from_seed_matches_oracle(lib):
+    for seed in (0, 1, 12345):
+        assert ace.rs_from_seed(seed) == O.rs_from_seed(seed)
+
+
+def _vk_from_oracle(opk):
+    vk = ace.VerifyingKey()
+    raw = (opk.point("fixed", 0) + opk.point("fixed", 3) + opk.point("fixed", 4) + opk.point("fixed", 5)
+           + opk.point("fixed", 6) + opk.point("fixed", 7))
+    ctypes.memmove(ctypes.byref(vk), raw, len(raw))
+    return vk
+
+
+def test_host_verifier_accepts_oracle_proofs_and_rejects_forgeries(lib):
+    oc = O.Circuit(10, 1024, 4, 0, 0, seed=1, input_seed=1)
+    opk = O.ProvingKey(oc, 1, with_points=True)
+    z = oc.witness()
+    r, s = O.rs_from_seed(1)
+    ok, proof = opk.prove(z, r, s)
+    assert ok
+    vk = _vk_from_oracle(opk)
+    pub = z[32:64]
+    assert ace.verify(vk, pub, proof) == 1
+    wrong_pub = ((int.from_bytes(pub, "little") + 1) % Y.R).to_bytes(32, "little")
+    assert ace.verify(vk, wrong_pub, proof) == 0
+    swapped = proof[192:256] + proof[64:192] + proof[0:64]
+    assert ace.verify(vk, pub, swapped) == 0
+    bad = bytearray(proof)
+    bad[3] ^= 1
+    with pytest.raises(ace.AceError) as e:
+        ace.verify(vk, pub, bytes(bad))
+    assert e.value.code == -5
+    # a proof for another witness of the same circuit also verifies (with its own public input)
+    oc2 = O.Circuit(10, 1024, 4, 0, 0, seed=1, input_seed=2)
+    z2 = oc2.witness()
+    ok, proof2 = opk.prove(z2, r, s)
+    assert ace.verify(vk, z2[32:64], proof2) == 1
+    assert ace.verify(vk, pub, proof2) == 0
+
+
+def test_host_pairing_bilinear(lib):
+    f = lib.ace_debug_pairing
+    f.restype = ctypes.c_int
+    g1, g2 = O.g1_generator(), O.g2_generator()
+
+    def e(p, q):
+        out = ctypes.create_string_buffer(384)
+        assert f(p, q, out) == 0
+        return out.raw
+
+    one = Y.ints_to_bytes([1] + [0] * 11)
+    base = e(g1, g2)
+    assert base != one
+    a, b = 987654321987654321, 1234567
+    lhs = e(O.g1_mul(g1, a), O.g2_mul(g2, b))
+    assert lhs == e(O.g1_mul(g1, a * b % Y.R), g2) == e(g1, O.g2_mul(g2, a * b % Y.R))
+    assert e(O.g1_mul(g1, Y.R - 1), g2) != base

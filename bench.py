@@ -1,0 +1,415 @@
+"""Benchmark: Groth16/BN254 proofs/s of the 2^20 block-scale proof on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one whole proof (sparse products + R1CS check, QAP quotient with 7
+NTTs, four G1 MSMs and one G2 MSM, assembly) of the block-scale circuit:
+N = 2^20 constraints, 2,048 transactions x 2 Poseidon-style permutations,
+2 bit-packing rows of 172 bits per transaction (~40% of the witness in {0,1}),
+squaring chain up to 2^20.  Inputs (witness, proving key) are resident in HBM
+for `value`; `e2e` copies the witness from pinned host memory and reads the
+proof back inside every step through the public C ABI.  One JSON line is
+printed by rank 0.  Under torchrun each rank proves its own proofs on its own
+GPU (independent replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Groth16 proofs/s and G1 MSM points/s at 2^20 (BN254), bit-exact; p99 prove latency"
+UNIT = "proofs/s"
+WORKLOAD = {
+    "workload": "groth16_block_2p20",
+    "constraints": 1 << 20,
+    "transactions": 2048,
+    "permutations": 4096,
+    "pack_rows": 4096,
+    "pack_bits": 172,
+    "curve": "BN254",
+}
+CIRCUIT = dict(log_n=20, n_rows=1 << 20, n_perm=4096, n_pack=4096, pack_bits=172)
+SEED = 2
+# Algorithmic cost of one mixed XYZZ addition (madd-2008-s): 8M + 2S field
+# multiplications on G1, 8 Fp2 mul (3 Fp mul) + 2 Fp2 sqr (2 Fp mul) on G2;
+# one 8-limb Montgomery product = 2 * 8^2 + 8 = 136 limb products = 272
+# 32-bit multiply-adds (lo and hi halves).
+IMAD_PER_FP_MUL = 272
+IMAD_PER_G1_MADD = 10 * IMAD_PER_FP_MUL
+IMAD_PER_G2_MADD = 28 * IMAD_PER_FP_MUL
+# ALU roofline: SMs x 64 32-bit IMAD per clock per SM x maximum SM clock
+# (152 SMs, 2070 MHz on GB300).
+SM_COUNT = 152
+IMAD_PER_CLK_PER_SM = 64
+SM_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the G1 bucket
+# accumulation kernel, per mixed addition, from the ncu capture summarised in
+# profiles/ (None until captured for the current kernel).
+G1_BUCKET_DRAM_BYTES_PER_MADD = None
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def _clock_summary(path, device):
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+class CpuSample:
+    """The oracle on a bounded sample of the block workload, scaled to one
+    2^20 proof.  Sample: the QAP quotient of the 2^16 instance of the same
+    circuit family (scaled by N log N), and plain-Pippenger MSMs over 2^15 G1
+    and 2^12 G2 points with the workload's witness scalars (scaled linearly
+    to the proof's point counts)."""
+
+    LOG_S, N1, N2 = 16, 1 << 15, 1 << 12
+
+    def __init__(self, shape):
+        import numpy as np
+
+        import oracle as O
+        from paper_2603_10242_gb300 import inputs
+
+        self.O = O
+        self.shape = shape
+        self.c = O.Circuit(self.LOG_S, 1 << self.LOG_S, 256, 256, 172, seed=SEED, input_seed=SEED)
+        self.z = self.c.witness()
+        kb = inputs.sample_fr(SEED, inputs.PURPOSE["bases"], self.N1)
+        zz = np.frombuffer(self.z, dtype=np.uint32).reshape(-1, 8)
+        self.sc = zz[np.arange(self.N1) % len(zz)].copy()
+        self.pts = O.g1_mul_gen_batch(kb.tobytes())
+        self.pts2 = O.g2_mul_gen_batch(kb[:self.N2].tobytes())
+
+    def measure(self):
+        O, shape = self.O, self.shape
+        t0 = time.perf_counter()
+        ok, _ = self.c.qap_h(self.z)
+        t_qap = time.perf_counter() - t0
+        assert ok
+        t_qap_full = t_qap * ((1 << 20) * 20) / ((1 << self.LOG_S) * self.LOG_S)
+        t0 = time.perf_counter()
+        O.msm_g1(self.pts, self.sc.tobytes(), 1)
+        t_g1 = (time.perf_counter() - t0) / self.N1
+        t0 = time.perf_counter()
+        O.msm_g2(self.pts2, self.sc[:self.N2].tobytes(), 1)
+        t_g2 = (time.perf_counter() - t0) / self.N2
+        g1_points = shape["m_A"] + shape["m_B"] + shape["m_L"] + shape["N"]
+        t_proof = t_qap_full + t_g1 * g1_points + t_g2 * shape["m_B"]
+        return {
+            "value": 1.0 / t_proof,
+            "unit": UNIT,
+            "cores": O.lib().orc_num_threads(),
+            "kind": "oracle",
+            "sample": (f"oracle QAP of the 2^{self.LOG_S} circuit of the same family ({t_qap:.2f} s, scaled by "
+                       f"N log N) + plain Pippenger over {self.N1} G1 / {self.N2} G2 points with witness scalars "
+                       f"({t_g1 * 1e6:.1f} / {t_g2 * 1e6:.1f} us per point, scaled to {g1_points} G1 + "
+                       f"{shape['m_B']} G2 points); est. {t_proof:.1f} s per proof"),
+        }
+
+
+def cpu_sample(shape):
+    s = CpuSample(shape)
+    runs = [s.measure() for _ in range(2)]
+    return max(runs, key=lambda r: r["value"])
+
+
+def run_reference(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    shape = {"N": 1 << 20, "m_A": 1765375, "m_B": 1060865, "m_L": 1765373}
+    s = CpuSample(shape)
+    for _ in range(args.warmup):
+        s.measure()
+    runs = [s.measure() for _ in range(args.steps)]
+    v = statistics.median(r["value"] for r in runs)
+    r = dict(runs[0])
+    r["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(WORKLOAD), "cpu_baseline": r,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2603_10242_gb300 as ace
+    from paper_2603_10242_gb300 import inputs
+
+    ws, rank, local = _dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    device = local if ws > 1 else 0
+    torch.cuda.set_device(device)
+    ace.build()
+    ctx = ace.Context(device)
+    circ = ace.Circuit(seed=SEED, **CIRCUIT)
+    z = circ.witness(SEED)
+    pk = ace.ProvingKey(ctx, circ, toxic_seed=SEED)
+    m, N = circ.m, circ.N
+    shape = {"N": N, "m": m, "m_A": pk.info[7], "m_B": pk.info[8], "m_L": pk.info[9]}
+    zb = np.frombuffer(z, dtype=np.uint8)
+    bool_frac = float(np.mean((zb.reshape(-1, 32)[:, 1:] == 0).all(axis=1) & (zb.reshape(-1, 32)[:, 0] <= 1)))
+    stream = torch.cuda.current_stream(device)
+    dz = torch.from_numpy(zb.copy()).to(device)
+    proofs = torch.zeros((args.steps + args.warmup) * 256, dtype=torch.uint8, device=device)
+    status = torch.zeros(args.steps + args.warmup, dtype=torch.int32, device=device)
+    rs = [ace.rs_from_seed(1000 + i) for i in range(args.warmup + args.steps)]
+
+    # correctness of the bench's own proof: verify on the host
+    proof0 = ctx.prove(pk, dz, *rs[0])
+    verified = pk.verify(z[32:64], proof0) == 1
+
+    for i in range(args.warmup):
+        ctx.prove_async(pk, dz, rs[i][0], rs[i][1], proofs[256 * i:], status[i:])
+    torch.cuda.synchronize()
+
+    # ---- timed region: K proofs, inputs resident in HBM ----
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sampler, sf = _clock_sampler(f"/tmp/bench_clocks_{rank}.csv")
+    ace.profile_enable(True)
+    launches0 = ace.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        j = args.warmup + i
+        ctx.prove_async(pk, dz, rs[j][0], rs[j][1], proofs[256 * j:], status[j:])
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = ace.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    prof = {k: ace.profile_read(k) for k in (ace.PROF_G1_BUCKET, ace.PROF_G2_BUCKET, ace.PROF_NTT,
+                                             ace.PROF_SPMV)}
+    ace.profile_enable(False)
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+        sf.close()
+    clocks = _clock_summary(f"/tmp/bench_clocks_{rank}.csv", device)
+    assert int(status.sum().item()) == 0, "a proof reported an unsatisfied witness"
+    allp = proofs.cpu().numpy().reshape(-1, 256)
+    # the timed proofs differ only by (r, s); check two of them on the host
+    for j in (args.warmup, args.warmup + args.steps - 1):
+        verified = verified and pk.verify(z[32:64], bytes(allp[j])) == 1
+
+    if dist:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps / (total_ms / 1000.0)
+
+    # ---- e2e: host witness -> device -> proof bytes on the host, per step ----
+    zpin = torch.from_numpy(zb.copy()).pin_memory()
+    dz2 = torch.empty_like(dz)
+    for i in range(2):
+        dz2.copy_(zpin, non_blocking=True)
+        ctx.prove(pk, dz2, *rs[i])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        dz2.copy_(zpin, non_blocking=True)
+        ctx.prove(pk, dz2, *rs[args.warmup + i])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * m,
+           "d2h_bytes_per_step": 256 + 4}
+
+    # ---- G1 MSM points/s at 2^20 (second half of the metric) ----
+    n = 1 << 20
+    kb = inputs.sample_fr(20, inputs.PURPOSE["bases"], n)
+    bases = torch.empty(64 * n, dtype=torch.uint8, device=device)
+    ctx.g1_fixed_base(torch.from_numpy(kb.view(np.uint8).reshape(-1)).to(device), n, bases, ace.FORM_MONT)
+    msm = {}
+    for dist_name in ("uniform", "sparse"):
+        sc = torch.from_numpy(inputs.sample_scalars(20, n, dist_name).view(np.uint8).reshape(-1)).to(device)
+        out = torch.empty(64, dtype=torch.uint8, device=device)
+        for _ in range(3):
+            ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT)
+        b.record(stream)
+        torch.cuda.synchronize()
+        msm[dist_name] = n * reps / (a.elapsed_time(b) / 1000.0)
+
+    # ---- roofline of the dominant kernel (G1 bucket accumulation) ----
+    ms, nl, units = prof[ace.PROF_G1_BUCKET]
+    peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = units * IMAD_PER_G1_MADD / (ms / 1000.0) / 1e12 if ms > 0 else None
+    measured_peak = {k: ace.imad_rate(ctx, mode) / 1e12 for k, mode in (("mad_lo", 0), ("mad_hi", 1),
+                                                                       ("mad_lo_hi_chain", 2))}
+    traffic = None
+    if G1_BUCKET_DRAM_BYTES_PER_MADD is not None and nl:
+        traffic = G1_BUCKET_DRAM_BYTES_PER_MADD * units / nl
+    roofline = {"bound": "alu", "kernel": "k_bucket_acc<G1>", "achieved": achieved, "peak": peak,
+                "unit": "T IMAD/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "algorithmic_per_unit": f"{IMAD_PER_G1_MADD} IMAD per mixed addition (10 Fp mul x 272)",
+                "units_per_launch": units / nl if nl else None, "launches": nl, "ms_union": ms,
+                "peak_source": "152 SMs x 64 IMAD/clk/SM x 2070 MHz (nominal unit counts and max clock)",
+                "peak_measured_T_per_s": measured_peak}
+    stages = {
+        "g1_bucket_ms_per_proof": ms / args.steps,
+        "g2_bucket_ms_per_proof": prof[ace.PROF_G2_BUCKET][0] / args.steps,
+        "ntt_ms_per_proof": prof[ace.PROF_NTT][0] / args.steps,
+        "spmv_ms_per_proof": prof[ace.PROF_SPMV][0] / args.steps,
+        "ntt_butterflies_per_proof": prof[ace.PROF_NTT][2] / args.steps,
+    }
+    step_sorted = sorted(step_ms)
+    p50 = statistics.median(step_sorted)
+    p99 = step_sorted[min(len(step_sorted) - 1, int(round(0.99 * (len(step_sorted) - 1))))]
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(WORKLOAD, l2="inputs larger than L2 (proving key %.2f GB resident)" % (pk.info[10] / 1e9),
+                           m=m, m_A=shape["m_A"], m_B=shape["m_B"], m_L=shape["m_L"],
+                           witness_bool_fraction=round(bool_frac, 4), parallelism="replicas" if ws > 1 else "1gpu"),
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "latency_ms": {"p50": p50, "p99": p99, "budget_ms": 600.0},
+            "msm_g1_2p20_points_per_s": msm,
+            "stages": stages,
+            "verified": bool(verified),
+            "clocks": clocks,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_sample(shape)
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_case(args):
+    """Small fixed launches for profiler captures (not a bench line):
+    msm_g1 -- one G1 MSM of 2^20 points (uniform scalars);
+    ntt -- one 2^20 forward transform of three arrays (QAP batch shape);
+    prove16 -- one proof of the 2^16 instance of the block circuit family."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10242_gb300 as ace
+    from paper_2603_10242_gb300 import inputs
+
+    ace.build()
+    ctx = ace.Context(0)
+    if args.case == "msm_g1":
+        n = 1 << 20
+        kb = inputs.sample_fr(20, inputs.PURPOSE["bases"], n)
+        bases = torch.empty(64 * n, dtype=torch.uint8, device="cuda")
+        ctx.g1_fixed_base(torch.from_numpy(kb.view(np.uint8).reshape(-1)).cuda(), n, bases, ace.FORM_MONT)
+        sc = torch.from_numpy(inputs.sample_scalars(20, n, "uniform").view(np.uint8).reshape(-1)).cuda()
+        out = torch.empty(64, dtype=torch.uint8, device="cuda")
+        for _ in range(args.steps):
+            ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT)
+    elif args.case == "ntt":
+        n = 1 << 20
+        d = torch.from_numpy(inputs.sample_fr(1, 7, 3 * n).view(np.uint8).reshape(-1)).cuda()
+        for _ in range(args.steps):
+            ctx.ntt_mont(d, 20, 3, True, False)
+    else:
+        c = ace.Circuit(16, 1 << 16, 256, 256, 172, seed=SEED)
+        z = c.witness(SEED)
+        pk = ace.ProvingKey(ctx, c, toxic_seed=SEED)
+        dz = torch.frombuffer(bytearray(z), dtype=torch.uint8).cuda()
+        r, s_ = ace.rs_from_seed(1)
+        for _ in range(args.steps):
+            ctx.prove(pk, dz, r, s_)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "steps": args.steps, "launches": ace.launch_count()}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["msm_g1", "ntt", "prove16"], default=None,
+                    help="run a small fixed case for profiler captures instead of the bench")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        if args.warmup < 3:
+            args.warmup = 3
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

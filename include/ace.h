@@ -200,6 +200,53 @@ int ace_rs_from_seed(uint64_t seed, ace_fr* r, ace_fr* s);
  * (the three-pairing check of Section 3.3 / Section 3.4).  n_pub must be 1. */
 int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t proof[256]);
 
+/* NTT of N = 2^log_n canonical Fr values in natural order, in place on the
+ * device: the transforms of the QAP step (H = {omega^i}, omega = 5^((r-1)/N),
+ * coset g H with g = 5).  kind: 0 forward (coefficients -> values on H),
+ * 1 inverse, 2 coset forward (coefficients -> values on g H), 3 coset inverse.
+ * 1 <= log_n <= 28.  Scratch: N elements from the context. */
+int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream stream);
+
+/* The transform passes the QAP step is built from, without scaling: `count`
+ * consecutive arrays of N Montgomery-form values, in place.  dif != 0:
+ * natural -> bit-reversed order (decimation in frequency), else bit-reversed
+ * -> natural (decimation in time); inverse != 0 uses omega^-1. */
+int ace_ntt_mont(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int count, int dif, int inverse,
+                 ace_stream stream);
+
+/* ace_msm_g1 with the window size forced to c (6 <= c <= 20). */
+int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
+                      size_t n, int c, ace_g1_affine* d_out, ace_stream stream);
+
+/* ---- diagnostics and measurement ------------------------------------------- */
+
+/* Element-wise device arithmetic on canonical inputs, for unit-level checks.
+ * field: 0 Fp, 1 Fr, 2 Fp2 (16 limbs per element); op: 0 a+b, 1 a-b, 2 a*b,
+ * 3 a^2, 4 a^-1 (0 for a = 0).  n elements each. */
+int ace_debug_field_op(int field, int op, const void* d_a, const void* d_b, void* d_out, size_t n,
+                       ace_stream stream);
+/* group: 1 G1, 2 G2 (affine canonical points); op: 0 P+Q, 1 P+Q mixed, 2 2P,
+ * 3 k P with k from d_k (canonical 256-bit). */
+int ace_debug_curve_op(int group, int op, const void* d_a, const void* d_b, const ace_fr* d_k, void* d_out,
+                       size_t n, ace_stream stream);
+/* Host: the library's optimal-ate pairing e(P, Q) after final exponentiation,
+ * as 6 Fp2 coefficients (w^0, w^2, w^4, w^1, w^3, w^5), canonical. */
+int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
+/* Measured 32-bit multiply-add throughput of the device (operations/s):
+ * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs. */
+int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s);
+
+/* Kernel launches issued by the library in this process so far. */
+int ace_launch_count(uint64_t* out);
+/* Kernel timing: when enabled (and reset), the hot kernels are bracketed
+ * with CUDA events on the stream they run on.  ace_profile_read synchronises
+ * the device and returns, for one kind, the length of the union of the
+ * bracketed intervals (ms), the launches and the work units:
+ * kind 0 G1 bucket accumulation (units: mixed additions), 1 the same on G2,
+ * 2 NTT passes (units: radix-2 butterflies), 3 sparse products (units: non-zeros). */
+int ace_profile_enable(int on);
+int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
+
 /* ---- batching and serving ------------------------------------------------ */
 
 /* k independent proofs (each with its own pk and witness) in one call; proof i

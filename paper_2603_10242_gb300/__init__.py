@@ -75,6 +75,12 @@ def lib():
             "ace_prove_batch": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
             "ace_pk_save": (i32, [vp, cp]),
             "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
+            "ace_debug_pairing": (i32, [cp, cp, cp]),
+            "ace_debug_imad_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
+            "ace_launch_count": (i32, [ctypes.POINTER(u64)]),
+            "ace_profile_enable": (i32, [i32]),
+            "ace_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
+                                       ctypes.POINTER(u64)]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name, None)
@@ -296,3 +302,30 @@ def rs_from_seed(seed: int):
 
 def verify(vk: VerifyingKey, public: bytes, proof: bytes) -> int:
     return check(lib().ace_verify(ctypes.byref(vk), public, 1, proof))
+
+
+# ---- measurement hooks ----
+PROF_G1_BUCKET, PROF_G2_BUCKET, PROF_NTT, PROF_SPMV = 0, 1, 2, 3
+
+
+def launch_count() -> int:
+    v = ctypes.c_uint64()
+    check(lib().ace_launch_count(ctypes.byref(v)))
+    return v.value
+
+
+def profile_enable(on: bool = True):
+    check(lib().ace_profile_enable(1 if on else 0))
+
+
+def profile_read(kind: int):
+    """(ms, launches, units) for one profiled kernel kind since enabling."""
+    ms, n, u = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().ace_profile_read(kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u)))
+    return ms.value, n.value, u.value
+
+
+def imad_rate(ctx: Context, mode: int) -> float:
+    v = ctypes.c_double()
+    check(lib().ace_debug_imad_rate(ctx.h, mode, ctypes.byref(v)))
+    return v.value

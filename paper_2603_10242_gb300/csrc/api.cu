@@ -297,6 +297,7 @@ int ace_debug_field_op(int field, int op, const void* d_a, const void* d_b, void
         k_field_op<fr_t><<<grid, 128, 0, st>>>(op, (const fr_t*)d_a, (const fr_t*)d_b, (fr_t*)d_out, n);
     else
         k_field_op<fp2_t><<<grid, 128, 0, st>>>(op, (const fp2_t*)d_a, (const fp2_t*)d_b, (fp2_t*)d_out, n);
+    ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }
@@ -317,7 +318,100 @@ int ace_debug_curve_op(int group, int op, const void* d_a, const void* d_b, cons
     else
         k_curve_op<fp2_t><<<grid, 64, 0, st>>>(op, (const g2_aff*)d_a, (const g2_aff*)d_b, (const uint32_t*)d_k,
                                                (g2_aff*)d_out, n);
+    ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// measurement hooks
+// ---------------------------------------------------------------------------
+int ace_launch_count(uint64_t* out) {
+    if (!out) return ACE_E_ARG;
+    *out = launch_count();
+    return ACE_OK;
+}
+
+int ace_profile_enable(int on) {
+    prof_enable(on != 0);
+    return ACE_OK;
+}
+
+int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units) {
+    clear_error();
+    if (kind < 0 || kind >= PROF_KINDS || !ms || !launches || !units) {
+        set_error("ace_profile_read: bad argument");
+        return ACE_E_ARG;
+    }
+    return prof_read(kind, ms, launches, units);
+}
+
+}  // extern "C"
+
+namespace ace {
+// Independent multiply-add chains: 8 per thread, `iters` rounds, in one of
+// three forms: 0 mad.lo.u32, 1 mad.hi.u32, 2 the carry-chained
+// mad.lo.cc / madc.hi.cc pairs of the Montgomery product.
+__global__ void k_imad_rate(int mode, int iters, uint32_t seed, uint32_t* out) {
+    uint32_t a[8], b = seed ^ (threadIdx.x * 2654435761u), c = blockIdx.x + 12345u;
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = seed + k * 7919u + threadIdx.x;
+    if (mode == 0) {
+        for (int i = 0; i < iters; i++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(b), "r"(c));
+    } else if (mode == 1) {
+        for (int i = 0; i < iters; i++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(b), "r"(c));
+    } else {
+        for (int i = 0; i < iters; i++)
+#pragma unroll
+            for (int k = 0; k < 8; k += 2)
+                asm volatile("mad.lo.cc.u32 %0, %0, %2, %3;\n\tmadc.hi.u32 %1, %1, %2, %3;"
+                             : "+r"(a[k]), "+r"(a[k + 1])
+                             : "r"(b), "r"(c));
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) x ^= a[k];
+    if (x == 0x9e3779b9u) out[0] = x;  // keeps the chains live
+}
+}  // namespace ace
+
+extern "C" {
+
+// Measured 32-bit multiply-add rate (operations per second) of the device:
+// mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs.
+int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s) {
+    clear_error();
+    if (!ctx || !ops_per_s || mode < 0 || mode > 2) {
+        set_error("ace_debug_imad_rate: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    int sms = 0;
+    ACE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    ACE_TRY(arena_ensure(ctx, 0, 4096));
+    uint32_t* d = (uint32_t*)ctx->scratch[0].take(16);
+    const int threads = 256, iters = 4096;
+    const int blocks = sms * 8;
+    cudaEvent_t a, b;
+    ACE_TRY_CUDA(cudaEventCreate(&a));
+    ACE_TRY_CUDA(cudaEventCreate(&b));
+    k_imad_rate<<<blocks, threads, 0, ctx->stream>>>(mode, 64, 1u, d);  // warm up
+    ::ace::note_launch();
+    ACE_TRY_CUDA(cudaEventRecord(a, ctx->stream));
+    k_imad_rate<<<blocks, threads, 0, ctx->stream>>>(mode, iters, 1u, d);
+    ::ace::note_launch();
+    ACE_TRY_CUDA(cudaEventRecord(b, ctx->stream));
+    ACE_TRY_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    ACE_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ops_per_s = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
     return ACE_OK;
 }
 

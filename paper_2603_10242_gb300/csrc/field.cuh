@@ -377,8 +377,24 @@ ACE_HD Fe<C> operator-(const Fe<C>& a, const Fe<C>& b) {
 #endif
     return r;
 }
+#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
+// Out-of-line Montgomery product: translation units whose kernels chain many
+// products (the MSM bucket loops) define ACE_FIELD_MUL_CALL so that all warps
+// run one shared ~300-instruction body instead of an instruction stream of
+// thousands of inlined copies that misses the instruction cache.
+template <class C>
+__device__ __noinline__ Fe<C> d_mul_call(const Fe<C> a, const Fe<C> b) {
+    Fe<C> r;
+    d_mul<C>(r.v, a.v, b.v);
+    return r;
+}
+#endif
+
 template <class C>
 ACE_HD Fe<C> operator*(const Fe<C>& a, const Fe<C>& b) {
+#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
+    return d_mul_call<C>(a, b);
+#else
     Fe<C> r;
 #if defined(__CUDA_ARCH__)
     d_mul<C>(r.v, a.v, b.v);
@@ -386,6 +402,7 @@ ACE_HD Fe<C> operator*(const Fe<C>& a, const Fe<C>& b) {
     h_mul<C>(r.v, a.v, b.v);
 #endif
     return r;
+#endif
 }
 template <class C>
 ACE_HD Fe<C> fe_sqr(const Fe<C>& a) { return a * a; }

@@ -114,8 +114,8 @@ int fixed_base_table(ace_ctx* ctx, Affine<F>** tab_out) {
         dev_free(ctx, q, 32 * sizeof(Xyzz<F>));
         return rc;
     }
-    k_fb_powers<F><<<1, 1, 0, ctx->stream>>>(generator_mont<F>(), (Xyzz<F>*)q);
-    k_fb_table<F><<<(32 * 255 + 127) / 128, 128, 0, ctx->stream>>>((Xyzz<F>*)q, (Affine<F>*)tab);
+    k_fb_powers<F><<<1, 1, 0, ctx->stream>>>(generator_mont<F>(), (Xyzz<F>*)q); ::ace::note_launch();
+    k_fb_table<F><<<(32 * 255 + 127) / 128, 128, 0, ctx->stream>>>((Xyzz<F>*)q, (Affine<F>*)tab); ::ace::note_launch();
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, q, 32 * sizeof(Xyzz<F>));
     if (e != cudaSuccess) {
@@ -134,7 +134,7 @@ int fixed_base_mul(ace_ctx* ctx, const uint32_t* d_scalars, size_t n, Affine<F>*
     if (n == 0) return ACE_OK;
     Affine<F>* tab = nullptr;
     ACE_TRY(fixed_base_table<F>(ctx, &tab));
-    k_fb_mul<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, d_scalars, n, d_out, out_mont ? 1 : 0);
+    k_fb_mul<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, d_scalars, n, d_out, out_mont ? 1 : 0); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

@@ -41,6 +41,8 @@ struct MsmBufs {
     uint32_t* cursor;    // keys
     uint32_t* scan_tmp;  // scan block sums
     uint32_t* entries;   // n K
+    uint32_t* order;     // keys, bucket keys by decreasing size
+    uint32_t* size_bins; // SIZE_BINS + 1
     Xyzz<F>* buckets;    // keys
     Xyzz<F>* segW;       // windows M
     Xyzz<F>* segS;       // windows M
@@ -66,6 +68,12 @@ size_t scan_tmp_words(size_t n);
 }  // namespace ace
 
 namespace ace {
+// buckets are processed in decreasing order of size so that the threads of a
+// warp carry similar numbers of additions; sizes >= SIZE_BINS - 1 share a bin
+static const uint32_t SIZE_BINS = 512;
+// order[] = keys sorted by decreasing bucket size (counting sort on sizes)
+int bucket_order(const uint32_t* offsets, uint32_t keys, uint32_t* bins, uint32_t* scan_tmp, uint32_t* order,
+                 cudaStream_t st);
 template <bool SCATTER>
 void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t* entries, cudaStream_t st);
 }  // namespace ace

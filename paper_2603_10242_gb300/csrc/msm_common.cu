@@ -137,9 +137,9 @@ __global__ void k_scan_add(uint32_t* d, size_t n, const uint32_t* sums) {
 int scan_exclusive_u32(uint32_t* d, size_t n, uint32_t* tmp, cudaStream_t st) {
     if (n == 0) return ACE_OK;
     uint32_t nb = (uint32_t)((n + 1023) / 1024);
-    k_scan_tiles<<<nb, 256, 0, st>>>(d, n, tmp);
-    k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
-    k_scan_add<<<nb, 256, 0, st>>>(d, n, tmp);
+    k_scan_tiles<<<nb, 256, 0, st>>>(d, n, tmp); ::ace::note_launch();
+    k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb); ::ace::note_launch();
+    k_scan_add<<<nb, 256, 0, st>>>(d, n, tmp); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }
@@ -223,7 +223,7 @@ void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t*
     unsigned grid = (unsigned)((n + 255) / 256);
     switch (c) {
 #define ACE_DIGITS_CASE(CC) \
-    case CC: k_msm_digits<CC, SCATTER><<<grid, 256, 0, st>>>(sc, n, cnt, entries); break;
+    case CC: k_msm_digits<CC, SCATTER><<<grid, 256, 0, st>>>(sc, n, cnt, entries); ::ace::note_launch(); break;
         ACE_DIGITS_CASE(6) ACE_DIGITS_CASE(7) ACE_DIGITS_CASE(8) ACE_DIGITS_CASE(9) ACE_DIGITS_CASE(10)
         ACE_DIGITS_CASE(11) ACE_DIGITS_CASE(12) ACE_DIGITS_CASE(13) ACE_DIGITS_CASE(14) ACE_DIGITS_CASE(15)
         ACE_DIGITS_CASE(16) ACE_DIGITS_CASE(17) ACE_DIGITS_CASE(18) ACE_DIGITS_CASE(19) ACE_DIGITS_CASE(20)
@@ -234,5 +234,38 @@ void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t*
 
 template void launch_digits<false>(int, const uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
 template void launch_digits<true>(int, const uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// bucket order: counting sort of keys by decreasing size
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t size_bin(const uint32_t* off, uint32_t key) {
+    uint32_t s = off[key + 1] - off[key];
+    if (s > SIZE_BINS - 1) s = SIZE_BINS - 1;
+    return SIZE_BINS - 1 - s;  // bin 0 holds the largest buckets
+}
+
+__global__ void k_size_hist(const uint32_t* __restrict__ off, uint32_t keys, uint32_t* bins) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= keys) return;
+    atomicAdd(&bins[size_bin(off, k)], 1u);
+}
+
+__global__ void k_size_scatter(const uint32_t* __restrict__ off, uint32_t keys, uint32_t* bins, uint32_t* order) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= keys) return;
+    uint32_t pos = atomicAdd(&bins[size_bin(off, k)], 1u);
+    order[pos] = k;
+}
+
+int bucket_order(const uint32_t* offsets, uint32_t keys, uint32_t* bins, uint32_t* scan_tmp, uint32_t* order,
+                 cudaStream_t st) {
+    ACE_TRY_CUDA(cudaMemsetAsync(bins, 0, (SIZE_BINS + 1) * sizeof(uint32_t), st));
+    unsigned grid = (keys + 255) / 256;
+    k_size_hist<<<grid, 256, 0, st>>>(offsets, keys, bins); ::ace::note_launch();
+    ACE_TRY(scan_exclusive_u32(bins, SIZE_BINS + 1, scan_tmp, st));
+    k_size_scatter<<<grid, 256, 0, st>>>(offsets, keys, bins, order); ::ace::note_launch();
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
 
 }  // namespace ace

@@ -1,4 +1,5 @@
 // msm_g1.cu -- G1 instantiation of the Pippenger MSM.
+#define ACE_FIELD_MUL_CALL 1
 #include "msm_impl.cuh"
 
 namespace ace {

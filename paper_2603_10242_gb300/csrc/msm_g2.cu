@@ -1,4 +1,5 @@
 // msm_g2.cu -- G2 instantiation of the Pippenger MSM.
+#define ACE_FIELD_MUL_CALL 1
 #include "msm_impl.cuh"
 
 namespace ace {

@@ -43,11 +43,14 @@ bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
     cursor = (uint32_t*)a.take(keys * 4);
     scan_tmp = (uint32_t*)a.take(scan_tmp_words(keys + 1) * 4);
     entries = (uint32_t*)a.take(p.n * (size_t)p.K * 4 + 4);
+    order = (uint32_t*)a.take(keys * 4);
+    size_bins = (uint32_t*)a.take((SIZE_BINS + 1) * 4);
     buckets = (Xyzz<F>*)a.take(keys * sizeof(Xyzz<F>));
     segW = (Xyzz<F>*)a.take((size_t)p.windows() * p.M * sizeof(Xyzz<F>));
     segS = (Xyzz<F>*)a.take((size_t)p.windows() * p.M * sizeof(Xyzz<F>));
     conv = need_conv ? (Affine<F>*)a.take(p.n * sizeof(Affine<F>)) : nullptr;
-    return offsets && cursor && scan_tmp && entries && buckets && segW && segS && (!need_conv || conv);
+    return offsets && cursor && scan_tmp && entries && order && size_bins && buckets && segW && segS &&
+           (!need_conv || conv);
 }
 
 template <class F>
@@ -64,10 +67,12 @@ size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont) {
 template <class F>
 __global__ void __launch_bounds__(128) k_bucket_acc(const Affine<F>* __restrict__ bases,
                                                     const uint32_t* __restrict__ entries,
-                                                    const uint32_t* __restrict__ offsets, uint32_t nkeys,
+                                                    const uint32_t* __restrict__ offsets,
+                                                    const uint32_t* __restrict__ order, uint32_t nkeys,
                                                     Xyzz<F>* buckets) {
-    uint32_t key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= nkeys) return;
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nkeys) return;
+    uint32_t key = __ldg(order + t);
     uint32_t b = offsets[key], e = offsets[key + 1];
     Xyzz<F> acc = xyzz_inf<F>();
     for (uint32_t t = b; t < e; t++) {
@@ -160,7 +165,7 @@ template <class F>
 int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
             Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st) {
     if (plan.n == 0) {
-        k_msm_empty<F><<<1, 1, 0, st>>>(d_res, d_out);
+        k_msm_empty<F><<<1, 1, 0, st>>>(d_res, d_out); ::ace::note_launch();
         ACE_TRY_CUDA(cudaGetLastError());
         return ACE_OK;
     }
@@ -173,7 +178,7 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     const uint32_t keys = plan.keys();
     const Affine<F>* bases = d_bases;
     if (!base_mont) {
-        k_bases_to_mont<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_bases, n, b.conv);
+        k_bases_to_mont<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_bases, n, b.conv); ::ace::note_launch();
         bases = b.conv;
     }
     ACE_TRY_CUDA(cudaMemsetAsync(b.offsets, 0, (keys + 1) * sizeof(uint32_t), st));
@@ -181,15 +186,18 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     ACE_TRY(scan_exclusive_u32(b.offsets, keys + 1, b.scan_tmp, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(b.cursor, b.offsets, keys * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     launch_digits<true>(plan.c, d_scalars, n, b.cursor, b.entries, st);
-    k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, keys, b.buckets);
+    ACE_TRY(bucket_order(b.offsets, keys, b.size_bins, b.scan_tmp, b.order, st));
+    int prof = prof_begin(sizeof(F) == sizeof(fp_t) ? PROF_G1_BUCKET : PROF_G2_BUCKET, st);
+    k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, b.order, keys, b.buckets); ::ace::note_launch();
+    prof_end(prof, st, b.offsets + keys, 0);
     uint32_t nseg = plan.windows() * plan.M;
-    k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS);
+    k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS); ::ace::note_launch();
     for (int lev = 0; (1u << lev) < plan.M; lev++) {
         uint32_t pairs = plan.windows() * (plan.M >> (lev + 1));
         k_tree_level<F><<<(pairs + 127) / 128, 128, 0, st>>>(b.segW, b.segS, plan.windows(), plan.M, lev,
-                                                             plan.lambda);
+                                                             plan.lambda); ::ace::note_launch();
     }
-    k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, (uint32_t)plan.K, plan.M, plan.c, d_res, d_out);
+    k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, (uint32_t)plan.K, plan.M, plan.c, d_res, d_out); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

@@ -134,8 +134,8 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     e = e ? e : up(p->rr, &rr, sizeof(fr_t));
     if (e == cudaSuccess && half > 0) {
         unsigned grid = (unsigned)((half + 255) / 256);
-        k_expand_pow<<<grid, 256, 0, st>>>(seed + tlo, seed, a, half, p->tw_fwd);
-        k_expand_pow<<<grid, 256, 0, st>>>(seed + 2 * tlo + thi, seed + tlo + thi, a, half, p->tw_inv);
+        k_expand_pow<<<grid, 256, 0, st>>>(seed + tlo, seed, a, half, p->tw_fwd); ::ace::note_launch();
+        k_expand_pow<<<grid, 256, 0, st>>>(seed + 2 * tlo + thi, seed + tlo + thi, a, half, p->tw_inv); ::ace::note_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
@@ -299,10 +299,14 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
         dim3 grid(blocks, (unsigned)count);
         const NttScale& a = pi == 0 ? pre : none;
         const NttScale& z = pi == np - 1 ? post : none;
+        int prof = prof_begin(PROF_NTT, st);
         if (dif)
             k_ntt_pass<false><<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
         else
             k_ntt_pass<true><<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
+        ::ace::note_launch();
+        // work: butterflies of this pass
+        prof_end(prof, st, nullptr, (uint64_t)count * ((uint64_t)1 << (k - 1)) * (uint64_t)t);
         done_bits += t;
     }
     ACE_TRY_CUDA(cudaGetLastError());
@@ -317,7 +321,7 @@ __global__ void k_scale_copy(const fr_t* in, fr_t* out, size_t n, NttScale s, in
 
 int fr_scale_copy(const fr_t* in, fr_t* out, size_t n, const NttScale& s, int log_n, cudaStream_t st) {
     if (n == 0) return ACE_OK;
-    k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n, s, log_n);
+    k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n, s, log_n); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }
@@ -333,7 +337,7 @@ __global__ void k_bitrev_copy(const fr_t* in, fr_t* out, int log_n) {
 int fr_bitrev_copy(const fr_t* in, fr_t* out, int log_n, int count, cudaStream_t st) {
     size_t n = (size_t)1 << log_n;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)count);
-    k_bitrev_copy<<<grid, 256, 0, st>>>(in, out, log_n);
+    k_bitrev_copy<<<grid, 256, 0, st>>>(in, out, log_n); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

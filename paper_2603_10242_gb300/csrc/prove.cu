@@ -143,7 +143,9 @@ int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t*
     NttPlan* plan = nullptr;
     ACE_TRY(ntt_get_plan(ctx, pk->log_n, &plan));
     const uint32_t N = (uint32_t)pk->N;
-    k_spmv3<<<(N + 255) / 256, 256, 0, st>>>(csr_of(pk), d_z, N, abc, d_status);
+    int prof = prof_begin(PROF_SPMV, st);
+    k_spmv3<<<(N + 255) / 256, 256, 0, st>>>(csr_of(pk), d_z, N, abc, d_status); ::ace::note_launch();
+    prof_end(prof, st, nullptr, pk->nnz[0] + pk->nnz[1] + pk->nnz[2]);
     NttScale none, cos, icos;
     cos.hi = plan->cos_hi;
     cos.lo = plan->cos_lo;
@@ -155,7 +157,7 @@ int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t*
     icos.brev = 1;
     ACE_TRY(ntt_run(*plan, abc, 3, true, true, none, cos, st));
     ACE_TRY(ntt_run(*plan, abc, 3, false, false, none, none, st));
-    k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, plan->zinv);
+    k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, plan->zinv); ::ace::note_launch();
     ACE_TRY(ntt_run(*plan, abc, 1, true, true, none, icos, st));
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
@@ -189,7 +191,10 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
         set_error("prove: arena too small");
         return ACE_E_OOM;
     }
-    if (q.count) k_gather<<<(q.count + 255) / 256, 256, 0, s>>>(d_z, q.d_idx, q.count, zq);
+    if (q.count) {
+        k_gather<<<(q.count + 255) / 256, 256, 0, s>>>(d_z, q.d_idx, q.count, zq);
+        ::ace::note_launch();
+    }
     return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
 }
 
@@ -222,7 +227,7 @@ int prove_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, const fr_t& r, co
     ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, ctx->scratch[2], res1 + 2, ctx->aux[1]));
     ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, ctx->scratch[3], res2, ctx->aux[2]));
     ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, ctx->scratch[4], res1 + 3, ctx->aux[3]));
-    k_prove_smul<<<1, 32, 0, ctx->aux[4]>>>(pk->d_fixed, r, s, rs, sm1, sm2);
+    k_prove_smul<<<1, 32, 0, ctx->aux[4]>>>(pk->d_fixed, r, s, rs, sm1, sm2); ::ace::note_launch();
     // main stream: QAP then the H MSM
     ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, st));
     MsmPlan ph = pl.H;
@@ -231,7 +236,7 @@ int prove_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, const fr_t& r, co
         ACE_TRY_CUDA(cudaEventRecord(ctx->ev[1 + k], ctx->aux[k]));
         ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->ev[1 + k], 0));
     }
-    k_assemble<<<1, 32, 0, st>>>(pk->d_fixed, res1, res2, sm1, sm2, r, s, d_proof);
+    k_assemble<<<1, 32, 0, st>>>(pk->d_fixed, res1, res2, sm1, sm2, r, s, d_proof); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

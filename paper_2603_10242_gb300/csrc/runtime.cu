@@ -2,6 +2,11 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
 #include "runtime.cuh"
 
 namespace ace {
@@ -62,6 +67,119 @@ int ctx_aux_streams(ace_ctx* ctx) {
     if (ctx->aux[0]) return ACE_OK;
     for (int i = 0; i < 8; i++) ACE_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
     for (int i = 0; i < 16; i++) ACE_TRY_CUDA(cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming));
+    return ACE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch counter and profiler
+// ---------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(); }
+
+namespace {
+const int PROF_MAX = 8192;
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    uint64_t host_units;
+    bool dev_units;
+};
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    int device = -1;
+    std::vector<cudaEvent_t> pool;
+    std::vector<ProfRec> recs;
+    uint32_t* d_units = nullptr;
+};
+Profiler& prof() {
+    static Profiler p;
+    return p;
+}
+}  // namespace
+
+bool prof_on() { return prof().on; }
+
+void prof_enable(bool on) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    cudaDeviceSynchronize();
+    p.recs.clear();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (on && (p.pool.empty() || p.device != dev)) {
+        p.pool.resize(2 * PROF_MAX);
+        for (auto& e : p.pool) cudaEventCreate(&e);
+        cudaMalloc(&p.d_units, PROF_MAX * sizeof(uint32_t));
+        p.device = dev;
+    }
+    if (p.d_units) cudaMemset(p.d_units, 0, PROF_MAX * sizeof(uint32_t));
+    p.on = on;
+}
+
+int prof_begin(int kind, cudaStream_t st) {
+    Profiler& p = prof();
+    if (!p.on) return -1;
+    std::lock_guard<std::mutex> g(p.mu);
+    int slot = (int)p.recs.size();
+    if (slot >= PROF_MAX) return -1;
+    ProfRec r{kind, p.pool[2 * slot], p.pool[2 * slot + 1], 0, false};
+    p.recs.push_back(r);
+    cudaEventRecord(r.a, st);
+    return slot;
+}
+
+void prof_end(int slot, cudaStream_t st, const uint32_t* device_units, uint64_t host_units) {
+    if (slot < 0) return;
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    ProfRec& r = p.recs[slot];
+    cudaEventRecord(r.b, st);
+    r.host_units = host_units;
+    if (device_units) {
+        r.dev_units = true;
+        cudaMemcpyAsync(p.d_units + slot, device_units, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    }
+}
+
+int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    ACE_TRY_CUDA(cudaDeviceSynchronize());
+    std::vector<uint32_t> du(p.recs.size());
+    if (!p.recs.empty()) ACE_TRY_CUDA(cudaMemcpy(du.data(), p.d_units, du.size() * 4, cudaMemcpyDeviceToHost));
+    // time = length of the union of the [start, end] intervals of this kind,
+    // on the common GPU clock (launches on several streams may overlap)
+    std::vector<std::pair<double, double>> iv;
+    uint64_t n = 0, u = 0;
+    cudaEvent_t origin = nullptr;
+    for (size_t i = 0; i < p.recs.size(); i++) {
+        const ProfRec& r = p.recs[i];
+        if (r.kind != kind) continue;
+        if (!origin) origin = r.a;
+        float a = 0, b = 0;
+        ACE_TRY_CUDA(cudaEventElapsedTime(&a, origin, r.a));
+        ACE_TRY_CUDA(cudaEventElapsedTime(&b, origin, r.b));
+        iv.push_back({a, b});
+        n++;
+        u += r.host_units + (r.dev_units ? du[i] : 0);
+    }
+    std::sort(iv.begin(), iv.end());
+    double t = 0, cs = 0, ce = -1e300;
+    for (auto& x : iv) {
+        if (x.first > ce) {
+            if (ce > cs) t += ce - cs;
+            cs = x.first;
+            ce = x.second;
+        } else if (x.second > ce) {
+            ce = x.second;
+        }
+    }
+    if (!iv.empty() && ce > cs) t += ce - cs;
+    *ms = t;
+    *launches = n;
+    *units = u;
     return ACE_OK;
 }
 

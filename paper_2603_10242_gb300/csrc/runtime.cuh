@@ -87,4 +87,20 @@ void dev_free(ace_ctx* ctx, void* p, size_t bytes);
 int arena_ensure(ace_ctx* ctx, int slot, size_t bytes);
 inline cudaStream_t pick_stream(ace_ctx* ctx, ace_stream s) { return s ? (cudaStream_t)s : ctx->stream; }
 int ctx_aux_streams(ace_ctx* ctx);  // lazily create aux streams and events
+
+// ---- launch counting and kernel timing ----------------------------------------
+// Every kernel launch of the library bumps a process-wide counter.  When the
+// profiler is on, the hot kernels are bracketed with CUDA events on the
+// stream they run on, together with their work count (taken from the device
+// when only the device knows it).
+void note_launch();
+uint64_t launch_count();
+enum ProfKind { PROF_G1_BUCKET = 0, PROF_G2_BUCKET = 1, PROF_NTT = 2, PROF_SPMV = 3, PROF_KINDS = 4 };
+bool prof_on();
+int prof_begin(int kind, cudaStream_t st);  // returns a record slot, or -1 when off / full
+// device_units (optional): a u32 on the device copied into the record;
+// host_units is added to it
+void prof_end(int slot, cudaStream_t st, const uint32_t* device_units, uint64_t host_units);
+void prof_enable(bool on);
+int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
 }  // namespace ace

@@ -170,6 +170,21 @@ int ace_msm_g1(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const 
 int ace_msm_g2(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const ace_fr* d_scalars,
                size_t n, ace_g2_affine* d_out, ace_stream stream);
 
+/* G1 MSM that allocates no device memory, for callers that cannot call
+ * cudaMalloc (their device memory is owned by a pool handed out up front, or
+ * they must not trigger the device-wide synchronisation that allocation and
+ * freeing imply).  The paper has no counterpart; this is a library service.
+ * Same arguments and result as ace_msm_g1, without a context: it runs on the
+ * current device, on `stream` (NULL = the legacy default stream).  n must be
+ * at most 16384 (ACE_E_ARG otherwise).  Its scratch is one fixed 6 MiB device
+ * array inside the library, present on every GPU that loads the library
+ * until the process exits; the first call on a device looks up that array's
+ * address (make that first call before any stream capture).  Every call
+ * shares the array and leaves its contents behind (the call clears what must
+ * start at zero), so calls whose work overlaps on the GPU race. */
+int ace_msm_g1_noalloc(const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars, size_t n,
+                       ace_g1_affine* d_out, ace_stream stream);
+
 /* Fixed-base batch k_i * G1 (resp. G2 generator) for canonical Fr scalars;
  * writes n affine points in out_form.  Used for setup and for MSM inputs. */
 int ace_g1_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g1_affine* d_out,

@@ -53,6 +53,7 @@ def lib():
             "ace_msm_g1": (i32, [vp, vp, i32, vp, sz, vp, vp]),
             "ace_msm_g2": (i32, [vp, vp, i32, vp, sz, vp, vp]),
             "ace_msm_g1_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
+            "ace_msm_g1_noalloc": (i32, [vp, i32, vp, sz, vp, vp]),
             "ace_g1_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
             "ace_g2_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
             "ace_debug_field_op": (i32, [i32, i32, vp, vp, vp, sz, vp]),
@@ -195,6 +196,11 @@ class Context:
         status = (ctypes.c_int32 * k)()
         check(lib().ace_prove_batch(self.h, k, pk_arr, z_arr, rs, ss, proofs, status))
         return [proofs.raw[256 * i:256 * i + 256] for i in range(k)], list(status)
+
+
+def msm_g1_noalloc(bases, scalars, n: int, out, base_form: int = FORM_CANONICAL, stream=None):
+    """G1 MSM without any device allocation (n <= 16384); see include/ace.h."""
+    check(lib().ace_msm_g1_noalloc(_ptr(bases), base_form, _ptr(scalars), n, _ptr(out), _stream(stream)))
 
 
 # ---- diagnostics (device element-wise arithmetic) ----

@@ -251,6 +251,11 @@ int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[3
  * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs. */
 int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s);
 
+/* Nanoseconds per step of a single-thread dependent chain: what = 0 Fp
+ * Montgomery products, 1 G1 XYZZ additions (the latency that sequential
+ * reductions and final combinations pay). */
+int ace_debug_chain_latency(ace_ctx* ctx, int what, double* ns_per_step);
+
 /* Kernel launches issued by the library in this process so far. */
 int ace_launch_count(uint64_t* out);
 /* Kernel timing: when enabled (and reset), the hot kernels are bracketed

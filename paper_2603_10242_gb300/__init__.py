@@ -78,6 +78,7 @@ def lib():
             "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
             "ace_debug_pairing": (i32, [cp, cp, cp]),
             "ace_debug_imad_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
+            "ace_debug_chain_latency": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "ace_launch_count": (i32, [ctypes.POINTER(u64)]),
             "ace_profile_enable": (i32, [i32]),
             "ace_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
@@ -334,4 +335,10 @@ def profile_read(kind: int):
 def imad_rate(ctx: Context, mode: int) -> float:
     v = ctypes.c_double()
     check(lib().ace_debug_imad_rate(ctx.h, mode, ctypes.byref(v)))
+    return v.value
+
+
+def chain_latency_ns(ctx: Context, what: int) -> float:
+    v = ctypes.c_double()
+    check(lib().ace_debug_chain_latency(ctx.h, what, ctypes.byref(v)))
     return v.value

@@ -97,13 +97,19 @@ int ace_ctx_destroy(ace_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto& a : c->scratch) dev_free(c, a.base, a.cap);
+    for (auto& sl : c->slots) {
+        for (auto& a : sl.ar) dev_free(c, a.base, a.cap);
+        if (!sl.ready) continue;
+        cudaStreamDestroy(sl.main);
+        for (auto s : sl.aux) cudaStreamDestroy(s);
+        cudaEventDestroy(sl.ev_in);
+        cudaEventDestroy(sl.ev_start);
+        cudaEventDestroy(sl.ev_done);
+        for (auto e : sl.ev_aux) cudaEventDestroy(e);
+    }
     ntt_release_plans(c);
     if (c->g1_fixed_tab) dev_free(c, c->g1_fixed_tab, 32 * 255 * sizeof(g1_aff));
     if (c->g2_fixed_tab) dev_free(c, c->g2_fixed_tab, 32 * 255 * sizeof(g2_aff));
-    for (auto s : c->aux)
-        if (s) cudaStreamDestroy(s);
-    for (auto e : c->ev)
-        if (e) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return ACE_OK;
@@ -412,6 +418,62 @@ int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     *ops_per_s = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+    return ACE_OK;
+}
+
+
+}  // extern "C"
+
+namespace ace {
+// one thread, `iters` dependent Montgomery products (Fp), or dependent G1
+// XYZZ additions (what = 1): the latency a sequential chain pays per step
+__global__ void k_chain_latency(int what, int iters, fp_t seed, g1_xyzz p0, uint32_t* out) {
+    if (what == 0) {
+        fp_t x = seed;
+        for (int i = 0; i < iters; i++) x = x * x;
+        if (x.v[0] == 0x12345678u) out[0] = x.v[1];
+    } else {
+        g1_xyzz a = p0;
+        for (int i = 0; i < iters; i++) a = xyzz_add(a, p0 /* a + p0, a != p0 */);
+        if (a.X.v[0] == 0x12345678u) out[0] = a.X.v[1];
+    }
+}
+}  // namespace ace
+
+extern "C" {
+
+// Diagnostic: nanoseconds per step of a single-thread dependent chain of Fp
+// Montgomery products (what = 0) or G1 XYZZ additions (what = 1).
+int ace_debug_chain_latency(ace_ctx* ctx, int what, double* ns_per_step) {
+    clear_error();
+    if (!ctx || !ns_per_step || what < 0 || what > 1) {
+        set_error("ace_debug_chain_latency: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    ACE_TRY(arena_ensure(ctx, 0, 4096));
+    uint32_t* d = (uint32_t*)ctx->scratch[0].take(16);
+    fp_t seed = fe_from_u32<FpCfg>(7);
+    g1_aff g;
+    g.x = fe_from_u32<FpCfg>(1);
+    g.y = fe_from_u32<FpCfg>(2);
+    g1_xyzz p0 = xyzz_dbl(xyzz_from_aff(g));
+    const int iters = 2000;
+    cudaEvent_t a, b;
+    ACE_TRY_CUDA(cudaEventCreate(&a));
+    ACE_TRY_CUDA(cudaEventCreate(&b));
+    k_chain_latency<<<1, 1, 0, ctx->stream>>>(what, 10, seed, p0, d);
+    ::ace::note_launch();
+    ACE_TRY_CUDA(cudaEventRecord(a, ctx->stream));
+    k_chain_latency<<<1, 1, 0, ctx->stream>>>(what, iters, seed, p0, d);
+    ::ace::note_launch();
+    ACE_TRY_CUDA(cudaEventRecord(b, ctx->stream));
+    ACE_TRY_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    ACE_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ns_per_step = ms * 1e6 / iters;
     return ACE_OK;
 }
 

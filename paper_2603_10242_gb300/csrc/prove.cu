@@ -198,14 +198,19 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
     return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
 }
 
-// Full proof on stream st; writes 64 words of proof to d_proof (device) and
-// the R1CS status to d_status (0 ok, 1 unsat).  Scratch: context arenas 0-4.
-int prove_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s, uint32_t* d_proof,
-              int32_t* d_status, cudaStream_t st) {
-    ACE_TRY(ctx_aux_streams(ctx));
+// Full proof on proving slot `slot`: ordered after the work already on
+// `st_in`; writes the 256 proof bytes to d_proof and the R1CS status to
+// d_status (0 ok, 1 unsat), both device memory.  With join, st_in waits for
+// the proof; without, the caller joins on the slot's ev_done.  The slot's
+// main stream runs the QAP and the H MSM, its auxiliary streams the A, B1,
+// B2 and L MSMs and the fixed-base terms; proofs on other slots overlap.
+int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
+              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join) {
+    ACE_TRY(slot_ready(ctx, slot));
+    ProveSlot& sl = ctx->slots[slot];
     ProvePlans pl = prove_plans(pk);
-    for (int k = 0; k < 5; k++) ACE_TRY(arena_ensure(ctx, k, pl.slot_bytes[k]));
-    Arena& a0 = ctx->scratch[0];
+    for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, slot, k, pl.slot_bytes[k]));
+    Arena& a0 = sl.ar[0];
     fr_t* abc = (fr_t*)a0.take(3 * pk->N * sizeof(fr_t));
     g1_xyzz* res1 = (g1_xyzz*)a0.take(8 * sizeof(g1_xyzz));
     g2_xyzz* res2 = (g2_xyzz*)a0.take(2 * sizeof(g2_xyzz));
@@ -218,26 +223,28 @@ int prove_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, const fr_t& r, co
     // r s mod r on the host
     fr_t rs = fe_from_mont(fe_to_mont(r) * fe_to_mont(s));
 
-    cudaEvent_t ev_start = ctx->ev[0];
-    ACE_TRY_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
-    ACE_TRY_CUDA(cudaEventRecord(ev_start, st));
-    for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(ctx->aux[k], ev_start, 0));
-    // auxiliary streams: A, B1, B2, L MSMs and the fixed-base terms
-    ACE_TRY(gathered_msm<fp_t>(pl.A, pk->A, d_z, ctx->scratch[1], res1 + 1, ctx->aux[0]));
-    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, ctx->scratch[2], res1 + 2, ctx->aux[1]));
-    ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, ctx->scratch[3], res2, ctx->aux[2]));
-    ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, ctx->scratch[4], res1 + 3, ctx->aux[3]));
-    k_prove_smul<<<1, 32, 0, ctx->aux[4]>>>(pk->d_fixed, r, s, rs, sm1, sm2); ::ace::note_launch();
-    // main stream: QAP then the H MSM
-    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, st));
-    MsmPlan ph = pl.H;
-    ACE_TRY(msm_run<fp_t>(ph, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, st));
+    // main waits for the caller's inputs; the auxiliary streams start after
+    // main's previous proof (which joined them) and the inputs
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_in, st_in));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(sl.main, sl.ev_in, 0));
+    ACE_TRY_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), sl.main));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_start, sl.main));
+    for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(sl.aux[k], sl.ev_start, 0));
+    ACE_TRY(gathered_msm<fp_t>(pl.A, pk->A, d_z, sl.ar[1], res1 + 1, sl.aux[0]));
+    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, sl.ar[2], res1 + 2, sl.aux[1]));
+    ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, sl.ar[3], res2, sl.aux[2]));
+    ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, sl.ar[4], res1 + 3, sl.aux[3]));
+    k_prove_smul<<<1, 32, 0, sl.aux[4]>>>(pk->d_fixed, r, s, rs, sm1, sm2); ::ace::note_launch();
+    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, sl.main));
+    ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, sl.main));
     for (int k = 0; k < 5; k++) {
-        ACE_TRY_CUDA(cudaEventRecord(ctx->ev[1 + k], ctx->aux[k]));
-        ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->ev[1 + k], 0));
+        ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], sl.aux[k]));
+        ACE_TRY_CUDA(cudaStreamWaitEvent(sl.main, sl.ev_aux[k], 0));
     }
-    k_assemble<<<1, 32, 0, st>>>(pk->d_fixed, res1, res2, sm1, sm2, r, s, d_proof); ::ace::note_launch();
+    k_assemble<<<1, 32, 0, sl.main>>>(pk->d_fixed, res1, res2, sm1, sm2, r, s, d_proof); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_done, sl.main));
+    if (join) ACE_TRY_CUDA(cudaStreamWaitEvent(st_in, sl.ev_done, 0));
     return ACE_OK;
 }
 
@@ -288,7 +295,8 @@ int ace_prove_async(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace
     fr_t rr, ss;
     memcpy(rr.v, r->l, 32);
     memcpy(ss.v, s->l, 32);
-    return prove_run(ctx, pk, (const fr_t*)d_z, rr, ss, (uint32_t*)d_proof_out, d_status, pick_stream(ctx, stream));
+    return prove_run(ctx, 0, pk, (const fr_t*)d_z, rr, ss, (uint32_t*)d_proof_out, d_status,
+                     pick_stream(ctx, stream), true);
 }
 
 int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
@@ -303,10 +311,10 @@ int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r
         return ACE_E_ARG;
     }
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
-    // proof and status words live past the per-proof scratch of arena 5
-    ACE_TRY(arena_ensure(ctx, 5, 512));
-    uint8_t* d_out = (uint8_t*)ctx->scratch[5].take(256);
-    int32_t* d_status = (int32_t*)ctx->scratch[5].take(16);
+    // proof and status words in a scratch arena of their own
+    ACE_TRY(arena_ensure(ctx, 3, 512));
+    uint8_t* d_out = (uint8_t*)ctx->scratch[3].take(256);
+    int32_t* d_status = (int32_t*)ctx->scratch[3].take(16);
     cudaStream_t st = pick_stream(ctx, stream);
     ACE_TRY(ace_prove_async(ctx, pk, d_z, r, s, d_out, d_status, stream));
     int32_t status = 0;
@@ -327,15 +335,43 @@ int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_
         set_error("ace_prove_batch: NULL argument");
         return ACE_E_ARG;
     }
+    if (k == 0) return ACE_OK;
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     for (size_t i = 0; i < k; i++) {
-        int rc = ace_prove(ctx, pks[i], d_zs[i], rs + i, ss + i, proofs + 256 * i, nullptr);
-        if (rc == ACE_E_UNSAT) {
-            status[i] = 1;
-            continue;
+        if (!pks[i] || !d_zs[i] || !canonical_fr(rs + i) || !canonical_fr(ss + i)) {
+            set_error("ace_prove_batch: proof %zu has a NULL key / witness or non-canonical r, s", i);
+            return ACE_E_ARG;
         }
-        if (rc != ACE_OK) return rc;
-        status[i] = 0;
     }
+    // device outputs for all proofs, then one copy back
+    ACE_TRY(arena_ensure(ctx, 3, k * 256 + k * sizeof(int32_t) + 1024));
+    uint32_t* d_proofs = (uint32_t*)ctx->scratch[3].take(k * 256);
+    int32_t* d_status = (int32_t*)ctx->scratch[3].take(k * sizeof(int32_t));
+    cudaStream_t st = ctx->stream;
+    // proofs go round-robin over the slots: consecutive proofs overlap.  The
+    // slots' scratch is sized for their largest proof up front, so no arena
+    // grows (and synchronises the device) in the middle of the batch.
+    int nslots = (int)(k < (size_t)ctx->batch_slots ? k : (size_t)ctx->batch_slots);
+    for (int q = 0; q < nslots; q++) {
+        size_t need[PROVE_ARENAS] = {0, 0, 0, 0, 0};
+        for (size_t i = q; i < k; i += nslots) {
+            ProvePlans pl = prove_plans(pks[i]);
+            for (int a = 0; a < PROVE_ARENAS; a++) need[a] = need[a] > pl.slot_bytes[a] ? need[a] : pl.slot_bytes[a];
+        }
+        ACE_TRY(slot_ready(ctx, q));
+        for (int a = 0; a < PROVE_ARENAS; a++) ACE_TRY(slot_arena_ensure(ctx, q, a, need[a]));
+    }
+    for (size_t i = 0; i < k; i++) {
+        fr_t rr, sv;
+        memcpy(rr.v, rs[i].l, 32);
+        memcpy(sv.v, ss[i].l, 32);
+        ACE_TRY(prove_run(ctx, (int)(i % nslots), pks[i], (const fr_t*)d_zs[i], rr, sv, d_proofs + 64 * i,
+                          d_status + i, st, false));
+    }
+    for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));
+    ACE_TRY_CUDA(cudaMemcpyAsync(proofs, d_proofs, k * 256, cudaMemcpyDeviceToHost, st));
+    ACE_TRY_CUDA(cudaMemcpyAsync(status, d_status, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    ACE_TRY_CUDA(cudaStreamSynchronize(st));
     return ACE_OK;
 }
 

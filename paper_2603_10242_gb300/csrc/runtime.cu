@@ -46,11 +46,10 @@ void dev_free(ace_ctx* ctx, void* p, size_t bytes) {
     ctx->held -= bytes;
 }
 
-int arena_ensure(ace_ctx* ctx, int slot, size_t bytes) {
-    Arena& a = ctx->scratch[slot];
+static int grow(ace_ctx* ctx, Arena& a, size_t bytes) {
     a.reset();
     if (a.cap >= bytes) return ACE_OK;
-    // round up to limit regrowth
+    // round up to limit regrowth; the device is idle before the old block goes
     size_t want = bytes + bytes / 8 + (1u << 20);
     ACE_TRY_CUDA(cudaDeviceSynchronize());
     dev_free(ctx, a.base, a.cap);
@@ -63,10 +62,20 @@ int arena_ensure(ace_ctx* ctx, int slot, size_t bytes) {
     return ACE_OK;
 }
 
-int ctx_aux_streams(ace_ctx* ctx) {
-    if (ctx->aux[0]) return ACE_OK;
-    for (int i = 0; i < 8; i++) ACE_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
-    for (int i = 0; i < 16; i++) ACE_TRY_CUDA(cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming));
+int arena_ensure(ace_ctx* ctx, int slot, size_t bytes) { return grow(ctx, ctx->scratch[slot], bytes); }
+
+int slot_arena_ensure(ace_ctx* ctx, int s, int k, size_t bytes) { return grow(ctx, ctx->slots[s].ar[k], bytes); }
+
+int slot_ready(ace_ctx* ctx, int s) {
+    ProveSlot& sl = ctx->slots[s];
+    if (sl.ready) return ACE_OK;
+    ACE_TRY_CUDA(cudaStreamCreateWithFlags(&sl.main, cudaStreamNonBlocking));
+    for (auto& a : sl.aux) ACE_TRY_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming));
+    ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_start, cudaEventDisableTiming));
+    ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));
+    for (auto& e : sl.ev_aux) ACE_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    sl.ready = true;
     return ACE_OK;
 }
 

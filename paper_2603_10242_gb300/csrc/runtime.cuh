@@ -64,6 +64,19 @@ struct Sizer {
 
 struct NttPlan;  // twiddle tables for one size (ntt.cu)
 
+// A proving slot: the streams, events and scratch one proof needs.  Proofs on
+// different slots run concurrently; proofs on the same slot run in order.
+static const int PROVE_ARENAS = 5;  // QAP + H MSM, A, B1, B2, L
+static const int MAX_SLOTS = 4;
+struct ProveSlot {
+    bool ready = false;
+    Arena ar[PROVE_ARENAS];
+    cudaStream_t main = nullptr;
+    cudaStream_t aux[5] = {};
+    cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_aux[5] = {};
+};
+
 }  // namespace ace
 
 struct ace_ctx {
@@ -72,9 +85,9 @@ struct ace_ctx {
     size_t budget = 0;  // 0 = unbounded
     size_t held = 0;    // bytes of device memory held by caches and arenas
     std::mutex mu;
-    ace::Arena scratch[8];  // slot 0: single calls; 1..: concurrent MSMs of a proof
-    cudaStream_t aux[8] = {};
-    cudaEvent_t ev[16] = {};
+    ace::Arena scratch[4];  // scratch of single calls (MSM, NTT, QAP, batch outputs)
+    ace::ProveSlot slots[ace::MAX_SLOTS];
+    int batch_slots = 2;  // slots a batch spreads its proofs over
     std::map<int, ace::NttPlan*> ntt_plans;
     void* g1_fixed_tab = nullptr;  // fixed-base tables for the generators (setup.cu)
     void* g2_fixed_tab = nullptr;
@@ -86,7 +99,10 @@ void dev_free(ace_ctx* ctx, void* p, size_t bytes);
 // make arena `slot` hold at least `bytes` (synchronises the device if it grows)
 int arena_ensure(ace_ctx* ctx, int slot, size_t bytes);
 inline cudaStream_t pick_stream(ace_ctx* ctx, ace_stream s) { return s ? (cudaStream_t)s : ctx->stream; }
-int ctx_aux_streams(ace_ctx* ctx);  // lazily create aux streams and events
+// create the streams and events of proving slot s (once)
+int slot_ready(ace_ctx* ctx, int s);
+// make arena k of slot s hold at least `bytes` (synchronises the device if it grows)
+int slot_arena_ensure(ace_ctx* ctx, int s, int k, size_t bytes);
 
 // ---- launch counting and kernel timing ----------------------------------------
 // Every kernel launch of the library bumps a process-wide counter.  When the

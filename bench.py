@@ -390,6 +390,69 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batch_sizes(base_seed: int, k: int):
+    """Row counts of the batched workload: T_i = round(2^(12 + 6 u_i)), u_i
+    uniform in [0, 1) from SplitMix64 (seed, purpose 8); the QAP domain is the
+    next power of two; the circuit is floor((T_i - 3)/243) permutations plus the
+    chain up to T_i rows."""
+    from paper_2603_10242_gb300 import inputs
+
+    out = []
+    u64 = inputs.splitmix64(base_seed, inputs.PURPOSE["sizes"], k)
+    for x in u64:
+        u = float(int(x) >> 11) * (2.0 ** -53)
+        t = int(round(2.0 ** (12 + 6 * u)))
+        log_n = max(12, (t - 1).bit_length())
+        n_perm = (t - 3) // 243
+        out.append((log_n, t, n_perm, 0, 0))
+    return out
+
+
+def run_batch_workload(args):
+    """BASELINE config 4: 64 independent proofs of uneven sizes (2^12..2^18
+    rows), each with its own circuit, key and seed; one batch call (proofs
+    pipelined over proving slots) against one proof per call."""
+    import torch
+
+    import paper_2603_10242_gb300 as ace
+
+    ace.build()
+    ctx = ace.Context(0)
+    k = 64
+    base = 4000
+    sizes = batch_sizes(base, k)
+    t0 = time.perf_counter()
+    circs = [ace.Circuit(*p, seed=base + i) for i, p in enumerate(sizes)]
+    pks = [ace.ProvingKey(ctx, c, toxic_seed=base + i) for i, c in enumerate(circs)]
+    zs = [c.witness(base + i) for i, c in enumerate(circs)]
+    setup_s = time.perf_counter() - t0
+    dzs = [torch.frombuffer(bytearray(z), dtype=torch.uint8).cuda() for z in zs]
+    rss = [ace.rs_from_seed(base + i) for i in range(k)]
+    rs = b"".join(r for r, _ in rss)
+    ss = b"".join(s_ for _, s_ in rss)
+    ctx.prove_batch(pks, dzs, rs, ss)            # warm-up (sizes the slots)
+    for i in range(k):
+        ctx.prove(pks[i], dzs[i], *rss[i])
+    torch.cuda.synchronize()
+    best_b, best_p = 1e30, 1e30
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        proofs, status = ctx.prove_batch(pks, dzs, rs, ss)
+        best_b = min(best_b, time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        plain = [ctx.prove(pks[i], dzs[i], *rss[i]) for i in range(k)]
+        torch.cuda.synchronize()
+        best_p = min(best_p, time.perf_counter() - t0)
+    assert status == [0] * k and proofs == plain
+    ok = all(pks[i].verify(zs[i][32:64], proofs[i]) == 1 for i in (0, k // 2, k - 1))
+    rows = sum(p[1] for p in sizes)
+    print(json.dumps({"workload": "groth16_batch64_2p12_2p18", "proofs": k, "rows_total": rows,
+                      "log_n_hist": {str(l): sum(1 for p in sizes if p[0] == l) for l in range(12, 19)},
+                      "batched_proofs_per_s": k / best_b, "plain_proofs_per_s": k / best_p,
+                      "batched_constraints_per_s": rows / best_b, "setup_s": setup_s, "verified": ok,
+                      "batch_slots": 2}))
+
+
 def run_case(args):
     """Small fixed launches for profiler captures (not a bench line):
     msm_g1 -- one G1 MSM of 2^20 points (uniform scalars);
@@ -431,6 +494,8 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["block2p20", "batch64"], default="block2p20",
+                    help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
     ap.add_argument("--case", choices=["msm_g1", "ntt", "prove16"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,6 +506,8 @@ def main():
     args = ap.parse_args()
     if args.case:
         run_case(args)
+    elif args.workload == "batch64":
+        run_batch_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -256,6 +256,12 @@ int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s);
  * reductions and final combinations pay). */
 int ace_debug_chain_latency(ace_ctx* ctx, int what, double* ns_per_step);
 
+/* Montgomery products per second over all SMs and single-thread latency
+ * (ns) of product form 0 (32-bit low/high multiply-add chains) or form 1
+ * (64-bit wide products, one carry chain per row); digest: 4 words of output
+ * (optional) for comparing the forms. */
+int ace_debug_mul_rate(ace_ctx* ctx, int form, double* per_s, double* latency_ns, uint32_t* digest);
+
 /* Kernel launches issued by the library in this process so far. */
 int ace_launch_count(uint64_t* out);
 /* Kernel timing: when enabled (and reset), the hot kernels are bracketed

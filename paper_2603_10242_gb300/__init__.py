@@ -79,6 +79,8 @@ def lib():
             "ace_debug_pairing": (i32, [cp, cp, cp]),
             "ace_debug_imad_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "ace_debug_chain_latency": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
+            "ace_debug_mul_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_uint32)]),
             "ace_launch_count": (i32, [ctypes.POINTER(u64)]),
             "ace_profile_enable": (i32, [i32]),
             "ace_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
@@ -342,3 +344,11 @@ def chain_latency_ns(ctx: Context, what: int) -> float:
     v = ctypes.c_double()
     check(lib().ace_debug_chain_latency(ctx.h, what, ctypes.byref(v)))
     return v.value
+
+
+def mul_rate(ctx: Context, form: int):
+    """(products/s, single-thread latency ns, digest) of Montgomery product form 0 or 1."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    d = (ctypes.c_uint32 * 4)()
+    check(lib().ace_debug_mul_rate(ctx.h, form, ctypes.byref(a), ctypes.byref(b), d))
+    return a.value, b.value, list(d)

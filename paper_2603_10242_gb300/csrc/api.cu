@@ -477,4 +477,96 @@ int ace_debug_chain_latency(ace_ctx* ctx, int what, double* ns_per_step) {
     return ACE_OK;
 }
 
+
+}  // extern "C"
+
+namespace ace {
+// throughput of the two Montgomery product forms: 4 independent chains per
+// thread; out[thread] receives a digest so both forms can be compared
+template <int V>
+__global__ void k_mul_rate(int iters, uint32_t* out) {
+#if defined(__CUDA_ARCH__)
+    fp_t x[4];
+    for (int k = 0; k < 4; k++) {
+        x[k] = fe_from_u32<FpCfg>(threadIdx.x + 7u * k + 3u + blockIdx.x);
+    }
+    fp_t y = fe_from_u32<FpCfg>(blockIdx.x + 11u);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            fp_t r;
+            if (V == 0) d_mul<FpCfg>(r.v, x[k].v, y.v);
+            else d_mul_wide<FpCfg>(r.v, x[k].v, y.v);
+            x[k] = r;
+        }
+    }
+    uint32_t h = 0;
+    for (int k = 0; k < 4; k++)
+        for (int l = 0; l < 8; l++) h = h * 31u + x[k].v[l];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = h;
+#endif
+}
+template <int V>
+__global__ void k_mul_latency(int iters, fp_t x, uint32_t* out) {
+#if defined(__CUDA_ARCH__)
+    for (int i = 0; i < iters; i++) {
+        fp_t r;
+        if (V == 0) d_mul<FpCfg>(r.v, x.v, x.v);
+        else d_mul_wide<FpCfg>(r.v, x.v, x.v);
+        x = r;
+    }
+    out[0] = x.v[0];
+#endif
+}
+}  // namespace ace
+
+extern "C" {
+
+// Diagnostic: Montgomery products per second (all SMs) and single-thread
+// latency (ns) of form 0 (lo/hi multiply-add chains) or form 1 (64-bit wide
+// products); digest (optional, 4 words) lets callers compare the two forms.
+int ace_debug_mul_rate(ace_ctx* ctx, int form, double* per_s, double* latency_ns, uint32_t* digest) {
+    clear_error();
+    if (!ctx || !per_s || !latency_ns || form < 0 || form > 1) {
+        set_error("ace_debug_mul_rate: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    int sms = 0;
+    ACE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int threads = 256, blocks = sms * 4, iters = 256;
+    ACE_TRY(arena_ensure(ctx, 0, (size_t)blocks * threads * 4 + 4096));
+    uint32_t* d = (uint32_t*)ctx->scratch[0].take((size_t)blocks * threads * 4);
+    cudaEvent_t a, b;
+    ACE_TRY_CUDA(cudaEventCreate(&a));
+    ACE_TRY_CUDA(cudaEventCreate(&b));
+    auto run = [&](int it) {
+        if (form == 0) k_mul_rate<0><<<blocks, threads, 0, ctx->stream>>>(it, d);
+        else k_mul_rate<1><<<blocks, threads, 0, ctx->stream>>>(it, d);
+        ::ace::note_launch();
+    };
+    run(4);
+    ACE_TRY_CUDA(cudaEventRecord(a, ctx->stream));
+    run(iters);
+    ACE_TRY_CUDA(cudaEventRecord(b, ctx->stream));
+    ACE_TRY_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    ACE_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+    *per_s = (double)blocks * threads * iters * 4 / (ms * 1e-3);
+    if (digest) ACE_TRY_CUDA(cudaMemcpy(digest, d, 16, cudaMemcpyDeviceToHost));
+    fp_t x = fe_from_u32<FpCfg>(5);
+    const int lit = 4000;
+    ACE_TRY_CUDA(cudaEventRecord(a, ctx->stream));
+    if (form == 0) k_mul_latency<0><<<1, 1, 0, ctx->stream>>>(lit, x, d);
+    else k_mul_latency<1><<<1, 1, 0, ctx->stream>>>(lit, x, d);
+    ::ace::note_launch();
+    ACE_TRY_CUDA(cudaEventRecord(b, ctx->stream));
+    ACE_TRY_CUDA(cudaEventSynchronize(b));
+    ACE_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+    *latency_ns = ms * 1e6 / lit;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ACE_OK;
+}
+
 }  // extern "C"

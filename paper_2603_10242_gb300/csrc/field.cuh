@@ -186,7 +186,8 @@ inline void h_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
 }
 
 // ---------------------------------------------------------------------------
-// device arithmetic (PTX carry chains)
+// device arithmetic (PTX carry chains).  Products use d_mul_wide (64-bit
+// limb products); d_mul (32-bit low/high chains) is kept for comparison.
 // ---------------------------------------------------------------------------
 #if defined(__CUDA_ARCH__)
 
@@ -352,6 +353,112 @@ ACE_DEV void d_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
 #undef ACE_MAC_ROW
 #undef ACE_REDUCE_ROW
 
+// Same product with 64-bit limb products: per row, eight independent
+// mad.wide.u32 (a_j b_i + t_j, which cannot overflow 64 bits) followed by one
+// carry chain that adds each high half into the next limb; the reduction row
+// does the same with m p_j.  Per product this issues one wide multiply-add
+// instead of a low and a high multiply-add.
+#define ACE_WROW_MUL(bi)                                                                         \
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,p4,p5,p6,p7,c;\n\t"                                       \
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"                        \
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %9, %17, c;\n\t"                                \
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %10, %17, c;\n\t"                               \
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %11, %17, c;\n\t"                               \
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 p3, %12, %17, c;\n\t"                               \
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 p4, %13, %17, c;\n\t"                               \
+        "mov.b64 c, {%5, 0};\n\tmad.wide.u32 p5, %14, %17, c;\n\t"                               \
+        "mov.b64 c, {%6, 0};\n\tmad.wide.u32 p6, %15, %17, c;\n\t"                               \
+        "mov.b64 c, {%7, 0};\n\tmad.wide.u32 p7, %16, %17, c;\n\t"                               \
+        "mov.b64 {l0,h0}, p0;\n\tmov.b64 {l1,h1}, p1;\n\tmov.b64 {l2,h2}, p2;\n\t"             \
+        "mov.b64 {l3,h3}, p3;\n\tmov.b64 {l4,h4}, p4;\n\tmov.b64 {l5,h5}, p5;\n\t"             \
+        "mov.b64 {l6,h6}, p6;\n\tmov.b64 {l7,h7}, p7;\n\t"                                        \
+        "mov.b32 %0, l0;\n\t"                                                                    \
+        "add.cc.u32 %1, l1, h0;\n\t"                                                             \
+        "addc.cc.u32 %2, l2, h1;\n\t"                                                            \
+        "addc.cc.u32 %3, l3, h2;\n\t"                                                            \
+        "addc.cc.u32 %4, l4, h3;\n\t"                                                            \
+        "addc.cc.u32 %5, l5, h4;\n\t"                                                            \
+        "addc.cc.u32 %6, l6, h5;\n\t"                                                            \
+        "addc.cc.u32 %7, l7, h6;\n\t"                                                            \
+        "addc.u32 %8, h7, 0;\n\t}"                                                               \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), \
+          "r"(bi))
+
+// t = (t + m p) / 2^32, m = t0 * INV; t8 holds the ninth limb on entry and is
+// zero on exit (the shifted value is below 2p)
+#define ACE_WROW_RED()                                                                           \
+    asm("{\n\t.reg .u64 q0,q1,q2,q3,q4,q5,q6,q7,c;\n\t.reg .u32 m;\n\t"                       \
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"                        \
+        "mul.lo.u32 m, %0, %9;\n\t"                                                              \
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 q0, m, %10, c;\n\t"                                 \
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 q1, m, %11, c;\n\t"                                 \
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 q2, m, %12, c;\n\t"                                 \
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 q3, m, %13, c;\n\t"                                 \
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 q4, m, %14, c;\n\t"                                 \
+        "mov.b64 c, {%5, 0};\n\tmad.wide.u32 q5, m, %15, c;\n\t"                                 \
+        "mov.b64 c, {%6, 0};\n\tmad.wide.u32 q6, m, %16, c;\n\t"                                 \
+        "mov.b64 c, {%7, 0};\n\tmad.wide.u32 q7, m, %17, c;\n\t"                                 \
+        "mov.b64 {l0,h0}, q0;\n\tmov.b64 {l1,h1}, q1;\n\tmov.b64 {l2,h2}, q2;\n\t"             \
+        "mov.b64 {l3,h3}, q3;\n\tmov.b64 {l4,h4}, q4;\n\tmov.b64 {l5,h5}, q5;\n\t"             \
+        "mov.b64 {l6,h6}, q6;\n\tmov.b64 {l7,h7}, q7;\n\t"                                        \
+        "add.cc.u32 %0, h0, l1;\n\t"                                                             \
+        "addc.cc.u32 %1, h1, l2;\n\t"                                                            \
+        "addc.cc.u32 %2, h2, l3;\n\t"                                                            \
+        "addc.cc.u32 %3, h3, l4;\n\t"                                                            \
+        "addc.cc.u32 %4, h4, l5;\n\t"                                                            \
+        "addc.cc.u32 %5, h5, l6;\n\t"                                                            \
+        "addc.cc.u32 %6, h6, l7;\n\t"                                                            \
+        "addc.u32 %7, h7, %8;\n\t"                                                               \
+        "mov.u32 %8, 0;\n\t}"                                                                    \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+        : "n"(C::INV), "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5),  \
+          "n"(C::M6), "n"(C::M7))
+
+template <class C>
+ACE_DEV void d_mul_wide(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
+    ACE_WROW_MUL(b[0]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[1]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[2]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[3]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[4]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[5]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[6]);
+    ACE_WROW_RED();
+    ACE_WROW_MUL(b[7]);
+    ACE_WROW_RED();
+    uint32_t d0, d1, d2, d3, d4, d5, d6, d7, mask;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;\n\t"
+        : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3), "=r"(d4), "=r"(d5), "=r"(d6), "=r"(d7), "=r"(mask)
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7),
+          "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5), "n"(C::M6), "n"(C::M7));
+    r[0] = (t0 & mask) | (d0 & ~mask);
+    r[1] = (t1 & mask) | (d1 & ~mask);
+    r[2] = (t2 & mask) | (d2 & ~mask);
+    r[3] = (t3 & mask) | (d3 & ~mask);
+    r[4] = (t4 & mask) | (d4 & ~mask);
+    r[5] = (t5 & mask) | (d5 & ~mask);
+    r[6] = (t6 & mask) | (d6 & ~mask);
+    r[7] = (t7 & mask) | (d7 & ~mask);
+}
+#undef ACE_WROW_MUL
+#undef ACE_WROW_RED
+
 #endif  // __CUDA_ARCH__
 
 // ---------------------------------------------------------------------------
@@ -385,7 +492,7 @@ ACE_HD Fe<C> operator-(const Fe<C>& a, const Fe<C>& b) {
 template <class C>
 __device__ __noinline__ Fe<C> d_mul_call(const Fe<C> a, const Fe<C> b) {
     Fe<C> r;
-    d_mul<C>(r.v, a.v, b.v);
+    d_mul_wide<C>(r.v, a.v, b.v);
     return r;
 }
 #endif
@@ -397,7 +504,7 @@ ACE_HD Fe<C> operator*(const Fe<C>& a, const Fe<C>& b) {
 #else
     Fe<C> r;
 #if defined(__CUDA_ARCH__)
-    d_mul<C>(r.v, a.v, b.v);
+    d_mul_wide<C>(r.v, a.v, b.v);
 #else
     h_mul<C>(r.v, a.v, b.v);
 #endif

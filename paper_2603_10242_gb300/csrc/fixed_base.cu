@@ -139,6 +139,23 @@ int fixed_base_mul(ace_ctx* ctx, const uint32_t* d_scalars, size_t n, Affine<F>*
     return ACE_OK;
 }
 
+template <class F>
+int fixed_table_build(ace_ctx* ctx, const Affine<F>& base_mont, Affine<F>* d_tab, cudaStream_t st) {
+    void* q = nullptr;
+    ACE_TRY(dev_alloc(ctx, &q, 32 * sizeof(Xyzz<F>)));
+    k_fb_powers<F><<<1, 1, 0, st>>>(base_mont, (Xyzz<F>*)q); ::ace::note_launch();
+    k_fb_table<F><<<(32 * 255 + 127) / 128, 128, 0, st>>>((Xyzz<F>*)q, d_tab); ::ace::note_launch();
+    cudaError_t e = cudaStreamSynchronize(st);
+    dev_free(ctx, q, 32 * sizeof(Xyzz<F>));
+    if (e != cudaSuccess) {
+        set_error("fixed-base table: %s", cudaGetErrorString(e));
+        return ACE_E_CUDA;
+    }
+    return ACE_OK;
+}
+template int fixed_table_build<fp_t>(ace_ctx*, const Affine<fp_t>&, Affine<fp_t>*, cudaStream_t);
+template int fixed_table_build<fp2_t>(ace_ctx*, const Affine<fp2_t>&, Affine<fp2_t>*, cudaStream_t);
+
 template int fixed_base_mul<fp_t>(ace_ctx*, const uint32_t*, size_t, Affine<fp_t>*, bool, cudaStream_t);
 template int fixed_base_mul<fp2_t>(ace_ctx*, const uint32_t*, size_t, Affine<fp2_t>*, bool, cudaStream_t);
 

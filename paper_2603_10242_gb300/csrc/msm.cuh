@@ -11,6 +11,8 @@
 //   4. per window sum_b b S_b: running sums over segments of L buckets, then a
 //      binary tree over segments whose right child is weighted by 2^level L;
 //   5. Horner over windows (c doublings each) plus the ones-window total.
+// With precomputed window tables of the bases (the proving key's queries),
+// every window's digits share one bucket set and step 5 is a single sum.
 // These are the G1/G2 multi-scalar multiplications of Groth16.Prove (the
 // paper's Section 3.1, Algorithm 1), computed for the A, B1, L and H queries
 // on G1 and the B query on G2.
@@ -28,12 +30,23 @@ struct MsmPlan {
     int lambda = 0;  // log2 of the segment length L
     uint32_t L = 0;
     uint32_t M = 0;  // segments per window, B / L
-    uint32_t windows() const { return (uint32_t)K + 1; }  // + ones window
+    // tabled: the bases come with precomputed window tables
+    // tab[w n + i] = 2^(c w) P_i, so all K digit windows share one set of
+    // buckets (no Horner over windows)
+    bool tabled = false;
+    uint32_t bucket_windows() const { return tabled ? 1u : (uint32_t)K; }
+    uint32_t windows() const { return bucket_windows() + 1; }  // + ones window
     uint32_t keys() const { return windows() * B; }
 };
 
 // c chosen by the cost model  n K madd + 2 K 2^(c-1) add  (force_c > 0 overrides)
 MsmPlan msm_plan(size_t n, int force_c = 0);
+// plan for tabled bases: cost n K madd + 2 2^(c-1) add, c <= 20
+MsmPlan msm_plan_tabled(size_t n, int force_c = 0);
+// window table of n Montgomery affine points: tab[w n + i] = 2^(c w) pts[i]
+// for w < K (pts may be tab itself, i.e. window 0 already in place)
+template <class F>
+int msm_build_table(const MsmPlan& plan, const Affine<F>* pts, Affine<F>* tab, cudaStream_t st);
 
 template <class F, class A>
 struct MsmBufs {
@@ -74,6 +87,9 @@ static const uint32_t SIZE_BINS = 512;
 // order[] = keys sorted by decreasing bucket size (counting sort on sizes)
 int bucket_order(const uint32_t* offsets, uint32_t keys, uint32_t* bins, uint32_t* scan_tmp, uint32_t* order,
                  cudaStream_t st);
+// digits of n scalars into (key, entry) pairs: histogram (SCATTER = false)
+// or placement; tabled plans put every window's digit in one bucket set with
+// entry w n + i
 template <bool SCATTER>
-void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t* entries, cudaStream_t st);
+void launch_digits(const MsmPlan& plan, const uint32_t* sc, uint32_t* cnt, uint32_t* entries, cudaStream_t st);
 }  // namespace ace

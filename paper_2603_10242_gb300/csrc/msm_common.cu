@@ -37,6 +37,28 @@ __device__ __forceinline__ T ld_plain(const T* p) {
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
+MsmPlan msm_plan_tabled(size_t n, int force_c) {
+    MsmPlan p;
+    p.n = n;
+    int best_c = 8;
+    double best = 1e300;
+    for (int c = 8; c <= 20; c++) {
+        int K = (255 + c - 1) / c;
+        double cost = (double)n * K * 10.0 + 2.0 * 2.0 * (double)(1u << (c - 1)) * 14.0;
+        if (cost < best) { best = cost; best_c = c; }
+    }
+    p.c = force_c > 0 ? force_c : best_c;
+    if (p.c < 6) p.c = 6;
+    if (p.c > 20) p.c = 20;
+    p.K = (255 + p.c - 1) / p.c;
+    p.B = 1u << (p.c - 1);
+    p.lambda = p.c - 1 < 5 ? p.c - 1 : 5;
+    p.L = 1u << p.lambda;
+    p.M = p.B / p.L;
+    p.tabled = true;
+    return p;
+}
+
 MsmPlan msm_plan(size_t n, int force_c) {
     MsmPlan p;
     p.n = n;
@@ -171,11 +193,14 @@ __device__ __forceinline__ int scalar_kind(const uint32_t s[8]) {
     return 2;
 }
 
-// SCATTER = false: histogram into cnt; true: place entries using cnt as cursor
-template <int C, bool SCATTER>
+// SCATTER = false: histogram into cnt; true: place entries using cnt as cursor.
+// TAB: digits of all windows go to bucket window 0 with entry w n + i
+// (precomputed window tables); otherwise window w's buckets hold entry i.
+template <int C, bool SCATTER, bool TAB>
 __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t* cnt, uint32_t* entries) {
     constexpr int K = (255 + C - 1) / C;
     constexpr uint32_t B = 1u << (C - 1);
+    constexpr uint32_t BW = TAB ? 1u : (uint32_t)K;
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t s[8];
@@ -183,7 +208,7 @@ __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t
     int kind = scalar_kind(s);
     if (kind == 0) return;
     if (kind == 1) {
-        uint32_t key = (uint32_t)K * B + (uint32_t)(i & (B - 1));
+        uint32_t key = BW * B + (uint32_t)(i & (B - 1));
         if (SCATTER) {
             uint32_t pos = atomicAdd(&cnt[key], 1u);
             entries[pos] = (uint32_t)i;
@@ -207,10 +232,11 @@ __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t
             carry = 0u;
         }
         if (mag != 0) {
-            uint32_t key = (uint32_t)w * B + (mag - 1u);
+            uint32_t key = (TAB ? 0u : (uint32_t)w * B) + (mag - 1u);
             if (SCATTER) {
                 uint32_t pos = atomicAdd(&cnt[key], 1u);
-                entries[pos] = (uint32_t)i | (neg << 31);
+                uint32_t e = TAB ? (uint32_t)((size_t)w * n + i) : (uint32_t)i;
+                entries[pos] = e | (neg << 31);
             } else {
                 atomicAdd(&cnt[key], 1u);
             }
@@ -219,21 +245,24 @@ __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t
 }
 
 template <bool SCATTER>
-void launch_digits(int c, const uint32_t* sc, size_t n, uint32_t* cnt, uint32_t* entries, cudaStream_t st) {
+void launch_digits(const MsmPlan& plan, const uint32_t* sc, uint32_t* cnt, uint32_t* entries, cudaStream_t st) {
+    size_t n = plan.n;
     unsigned grid = (unsigned)((n + 255) / 256);
-    switch (c) {
-#define ACE_DIGITS_CASE(CC) \
-    case CC: k_msm_digits<CC, SCATTER><<<grid, 256, 0, st>>>(sc, n, cnt, entries); ::ace::note_launch(); break;
+    switch (plan.c * 2 + (plan.tabled ? 1 : 0)) {
+#define ACE_DIGITS_CASE(CC)                                                                          \
+    case 2 * CC: k_msm_digits<CC, SCATTER, false><<<grid, 256, 0, st>>>(sc, n, cnt, entries); break; \
+    case 2 * CC + 1: k_msm_digits<CC, SCATTER, true><<<grid, 256, 0, st>>>(sc, n, cnt, entries); break;
         ACE_DIGITS_CASE(6) ACE_DIGITS_CASE(7) ACE_DIGITS_CASE(8) ACE_DIGITS_CASE(9) ACE_DIGITS_CASE(10)
         ACE_DIGITS_CASE(11) ACE_DIGITS_CASE(12) ACE_DIGITS_CASE(13) ACE_DIGITS_CASE(14) ACE_DIGITS_CASE(15)
         ACE_DIGITS_CASE(16) ACE_DIGITS_CASE(17) ACE_DIGITS_CASE(18) ACE_DIGITS_CASE(19) ACE_DIGITS_CASE(20)
 #undef ACE_DIGITS_CASE
         default: break;
     }
+    ::ace::note_launch();
 }
 
-template void launch_digits<false>(int, const uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
-template void launch_digits<true>(int, const uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
+template void launch_digits<false>(const MsmPlan&, const uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
+template void launch_digits<true>(const MsmPlan&, const uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // bucket order: counting sort of keys by decreasing size

@@ -161,6 +161,29 @@ __global__ void k_bases_to_mont(const Affine<F>* in, size_t n, Affine<F>* out) {
     st_vec(out + i, aff_to_mont(p));
 }
 
+// tab[w n + i] = 2^(c w) P_i: c doublings per window, one inversion per
+// stored point (setup time only)
+template <class F>
+__global__ void __launch_bounds__(128) k_window_table(const Affine<F>* pts, size_t n, int c, int K, Affine<F>* tab) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Affine<F> p = ld_plain(pts + i);
+    st_vec(tab + i, p);
+    Xyzz<F> x = xyzz_from_aff(p);
+    for (int w = 1; w < K; w++) {
+        for (int k = 0; k < c; k++) x = xyzz_dbl(x);
+        st_vec(tab + (size_t)w * n + i, xyzz_to_aff(x));
+    }
+}
+
+template <class F>
+int msm_build_table(const MsmPlan& plan, const Affine<F>* pts, Affine<F>* tab, cudaStream_t st) {
+    if (plan.n == 0) return ACE_OK;
+    k_window_table<F><<<(unsigned)((plan.n + 127) / 128), 128, 0, st>>>(pts, plan.n, plan.c, plan.K, tab); ::ace::note_launch();
+    ACE_TRY_CUDA(cudaGetLastError());
+    return ACE_OK;
+}
+
 template <class F>
 int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
             Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st) {
@@ -182,10 +205,10 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
         bases = b.conv;
     }
     ACE_TRY_CUDA(cudaMemsetAsync(b.offsets, 0, (keys + 1) * sizeof(uint32_t), st));
-    launch_digits<false>(plan.c, d_scalars, n, b.offsets, nullptr, st);
+    launch_digits<false>(plan, d_scalars, b.offsets, nullptr, st);
     ACE_TRY(scan_exclusive_u32(b.offsets, keys + 1, b.scan_tmp, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(b.cursor, b.offsets, keys * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    launch_digits<true>(plan.c, d_scalars, n, b.cursor, b.entries, st);
+    launch_digits<true>(plan, d_scalars, b.cursor, b.entries, st);
     ACE_TRY(bucket_order(b.offsets, keys, b.size_bins, b.scan_tmp, b.order, st));
     int prof = prof_begin(sizeof(F) == sizeof(fp_t) ? PROF_G1_BUCKET : PROF_G2_BUCKET, st);
     k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, b.order, keys, b.buckets); ::ace::note_launch();
@@ -197,7 +220,7 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
         k_tree_level<F><<<(pairs + 127) / 128, 128, 0, st>>>(b.segW, b.segS, plan.windows(), plan.M, lev,
                                                              plan.lambda); ::ace::note_launch();
     }
-    k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, (uint32_t)plan.K, plan.M, plan.c, d_res, d_out); ::ace::note_launch();
+    k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, plan.bucket_windows(), plan.M, plan.c, d_res, d_out); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

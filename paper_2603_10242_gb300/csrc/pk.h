@@ -22,8 +22,9 @@ template <class F>
 struct Query {
     uint32_t count = 0;
     uint32_t* d_idx = nullptr;        // count (witness indices)
-    Affine<F>* d_pts = nullptr;       // count (Montgomery affine)
+    Affine<F>* d_pts = nullptr;       // plan.K x count: window table, window 0 = the points (Montgomery affine)
     std::vector<uint32_t> h_idx;      // host copy of the indices (ascending)
+    MsmPlan plan;                     // tabled MSM plan for count points
 };
 
 }  // namespace ace
@@ -40,8 +41,14 @@ struct ace_pk {
     uint64_t nnz[3] = {};
     ace::Query<ace::fp_t> A, B1, L;
     ace::Query<ace::fp2_t> B2;   // same indices as B1
-    ace::g1_aff* d_H = nullptr;  // N points: d_H[p] = H_{bitrev(p)}, H_{N-1} = infinity
+    ace::g1_aff* d_H = nullptr;  // window table of N points: d_H[p] = H_{bitrev(p)}, H_{N-1} = infinity
+    ace::MsmPlan H_plan;         // tabled plan of the H query
     ace::PkFixed* d_fixed = nullptr;
+    // 8-bit window tables (32 x 255 points) of alpha1, beta1, delta1 and delta2
+    ace::g1_aff* d_tab_alpha1 = nullptr;
+    ace::g1_aff* d_tab_beta1 = nullptr;
+    ace::g1_aff* d_tab_delta1 = nullptr;
+    ace::g2_aff* d_tab_delta2 = nullptr;
     ace_vk vk;
     size_t bytes = 0;            // device bytes held
     std::vector<std::pair<void*, size_t>> allocs;
@@ -51,4 +58,10 @@ struct ace_pk {
 
 namespace ace {
 int pk_alloc(ace_pk* pk, void** p, size_t bytes);
+// window tables of the fixed points (after d_fixed is set)
+int pk_build_tables(ace_pk* pk, const PkFixed& f);
+// allocate the window table of a query of `count` points (window 0 to be
+// filled by the caller), set its plan
+template <class F>
+int pk_alloc_table(ace_pk* pk, uint32_t count, MsmPlan* plan, Affine<F>** tab);
 }  // namespace ace

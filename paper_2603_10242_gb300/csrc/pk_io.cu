@@ -52,6 +52,17 @@ bool dev_to_host(const T* d, size_t n, std::vector<T>& h) {
     return n == 0 || cudaMemcpy(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
 }
 
+// upload window 0 of a query table and build the other windows
+template <class F>
+int table_to_dev(ace_pk* pk, const std::vector<Affine<F>>& h, MsmPlan* plan, Affine<F>** d) {
+    ACE_TRY(pk_alloc_table<F>(pk, (uint32_t)h.size(), plan, d));
+    if (h.empty()) return ACE_OK;
+    ACE_TRY_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(Affine<F>), cudaMemcpyHostToDevice));
+    ACE_TRY(msm_build_table<F>(*plan, *d, *d, pk->ctx->stream));
+    ACE_TRY_CUDA(cudaStreamSynchronize(pk->ctx->stream));
+    return ACE_OK;
+}
+
 template <class T>
 int host_to_dev(ace_pk* pk, const std::vector<T>& h, T** d) {
     void* p = nullptr;
@@ -217,15 +228,16 @@ int ace_pk_load(ace_ctx* ctx, const char* path, ace_pk** pk_out, ace_vk* vk_out)
     pk->L.count = (uint32_t)il.size();
     pk->L.h_idx = il;
     if (rc == ACE_OK) rc = host_to_dev(pk, ia, &pk->A.d_idx);
-    if (rc == ACE_OK) rc = host_to_dev(pk, pa, &pk->A.d_pts);
+    if (rc == ACE_OK) rc = table_to_dev(pk, pa, &pk->A.plan, &pk->A.d_pts);
     if (rc == ACE_OK) rc = host_to_dev(pk, ib, &pk->B1.d_idx);
-    if (rc == ACE_OK) rc = host_to_dev(pk, pb, &pk->B1.d_pts);
+    if (rc == ACE_OK) rc = table_to_dev(pk, pb, &pk->B1.plan, &pk->B1.d_pts);
     if (rc == ACE_OK) rc = host_to_dev(pk, ib, &pk->B2.d_idx);
-    if (rc == ACE_OK) rc = host_to_dev(pk, pb2, &pk->B2.d_pts);
+    if (rc == ACE_OK) rc = table_to_dev(pk, pb2, &pk->B2.plan, &pk->B2.d_pts);
     if (rc == ACE_OK) rc = host_to_dev(pk, il, &pk->L.d_idx);
-    if (rc == ACE_OK) rc = host_to_dev(pk, pl, &pk->L.d_pts);
-    if (rc == ACE_OK) rc = host_to_dev(pk, ph, &pk->d_H);
+    if (rc == ACE_OK) rc = table_to_dev(pk, pl, &pk->L.plan, &pk->L.d_pts);
+    if (rc == ACE_OK) rc = table_to_dev(pk, ph, &pk->H_plan, &pk->d_H);
     if (rc == ACE_OK) rc = host_to_dev(pk, fx, &pk->d_fixed);
+    if (rc == ACE_OK) rc = pk_build_tables(pk, fx[0]);
     if (rc != ACE_OK) return fail(rc);
     if (vk_out) *vk_out = pk->vk;
     *pk_out = pk;

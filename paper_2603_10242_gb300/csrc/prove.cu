@@ -10,13 +10,16 @@
 //      NTT scaled by g^-e / N leaving canonical h in bit-reversed order;
 //   3. five MSMs on their own streams: H (h, bit-reversed H query) on the
 //      main stream, A, B1 (G1), B2 (G2) and L on auxiliary streams, with the
-//      witness gathered per compacted query; the fixed-base terms r delta,
-//      s delta, r s delta run alongside;
-//   4. assembly: A = alpha + S_A + r delta, B = beta + S_B2 + s delta,
-//      B1 = beta + S_B1 + s delta, C = S_L + S_H + s A + r B1 - r s delta,
-//      s A + r B1 by one joint double-and-add; affine, canonical bytes.
+//      witness gathered per compacted query;
+//   4. assembly: A = alpha + S_A + r delta, B = beta + S_B2 + s delta and
+//      C = S_L + S_H + s A + r B1 - r s delta with B1 = beta + S_B1 + s delta,
+//      i.e. C = S_L + S_H + s alpha + r beta + r s delta + s S_A + r S_B1:
+//      the fixed-base terms come from the key's window tables at the start,
+//      s S_A + r S_B1 (one joint double-and-add) as soon as the A and B1
+//      MSMs are done, and the last kernel only adds and converts to affine.
 #include <string.h>
 
+#include "fixed_base.cuh"
 #include "pk.h"
 
 namespace ace {
@@ -78,13 +81,37 @@ __global__ void k_gather(const fr_t* __restrict__ z, const uint32_t* __restrict_
     st_fr2(out + k, ldg_fr(z + __ldg(idx + k)));
 }
 
-// the fixed-base terms: r delta1, s delta1, r s delta1 (G1) and s delta2 (G2)
-__global__ void k_prove_smul(const PkFixed* fx, fr_t r, fr_t s, fr_t rs, g1_xyzz* o1, g2_xyzz* o2) {
-    int t = threadIdx.x;
-    if (t == 0) o1[0] = xyzz_mul_aff(fx->delta1, r.v);
-    if (t == 1) o1[1] = xyzz_mul_aff(fx->delta1, s.v);
-    if (t == 2) o1[2] = xyzz_mul_aff(fx->delta1, rs.v);
-    if (t == 3) o2[0] = xyzz_mul_aff(fx->delta2, s.v);
+// Fixed-base terms from the key's window tables, one warp each (lane 0):
+// fx1 = {r delta1, s alpha1, r beta1, r s delta1}, fx2 = {s delta2}.
+struct PkTabs {
+    const g1_aff *alpha1, *beta1, *delta1;
+    const g2_aff* delta2;
+};
+__global__ void k_prove_fixed(PkTabs t, fr_t r, fr_t s, fr_t rs, g1_xyzz* fx1, g2_xyzz* fx2) {
+    if ((threadIdx.x & 31) != 0) return;
+    switch (threadIdx.x >> 5) {
+        case 0: fx1[0] = fixed_mul_tab(t.delta1, r.v); break;
+        case 1: fx1[1] = fixed_mul_tab(t.alpha1, s.v); break;
+        case 2: fx1[2] = fixed_mul_tab(t.beta1, r.v); break;
+        case 3: fx1[3] = fixed_mul_tab(t.delta1, rs.v); break;
+        default: fx2[0] = fixed_mul_tab(t.delta2, s.v); break;
+    }
+}
+
+// The variable-base part of C: V = s S_A + r S_B1 by one joint double-and-add
+// (XYZZ additions, no inversion), as soon as the A and B1 MSMs are done.
+__global__ void k_prove_var(const g1_xyzz* res1, fr_t r, fr_t s, g1_xyzz* v) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    g1_xyzz a = res1[1], b = res1[2], ab = xyzz_add(a, b);
+    g1_xyzz acc = xyzz_inf<fp_t>();
+    for (int i = 255; i >= 0; i--) {
+        acc = xyzz_dbl(acc);
+        uint32_t bs = (s.v[i >> 5] >> (i & 31)) & 1u, br = (r.v[i >> 5] >> (i & 31)) & 1u;
+        if (bs && br) acc = xyzz_add(acc, ab);
+        else if (bs) acc = xyzz_add(acc, a);
+        else if (br) acc = xyzz_add(acc, b);
+    }
+    *v = acc;
 }
 
 __device__ void write_g1(uint32_t* dst, const g1_xyzz& p) {
@@ -95,34 +122,30 @@ __device__ void write_g1(uint32_t* dst, const g1_xyzz& p) {
     }
 }
 
-// res1: S_H, S_A, S_B1, S_L; sm1: r delta1, s delta1, r s delta1; sm2: s delta2
-__global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2, const g1_xyzz* sm1,
-                           const g2_xyzz* sm2, fr_t r, fr_t s, uint32_t* proof) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    g1_xyzz A = xyzz_add(xyzz_add(xyzz_from_aff(fx->alpha1), res1[1]), sm1[0]);
-    g2_xyzz B = xyzz_add(xyzz_add(xyzz_from_aff(fx->beta2), resB2[0]), sm2[0]);
-    g1_xyzz B1 = xyzz_add(xyzz_add(xyzz_from_aff(fx->beta1), res1[2]), sm1[1]);
-    // s A + r B1, joint double-and-add over the bits of s and r
-    g1_aff Aa = xyzz_to_aff(A), Ba = xyzz_to_aff(B1), Ta = xyzz_to_aff(xyzz_add(A, B1));
-    g1_xyzz acc = xyzz_inf<fp_t>();
-    for (int i = 255; i >= 0; i--) {
-        acc = xyzz_dbl(acc);
-        uint32_t bs = (s.v[i >> 5] >> (i & 31)) & 1u, br = (r.v[i >> 5] >> (i & 31)) & 1u;
-        if (bs && br) acc = xyzz_add_aff(acc, Ta);
-        else if (bs) acc = xyzz_add_aff(acc, Aa);
-        else if (br) acc = xyzz_add_aff(acc, Ba);
+// A = alpha + S_A + r delta;  B = beta2 + S_B2 + s delta2;
+// C = S_L + S_H + (s alpha + r beta + r s delta) + V   (one warp each)
+// res1: S_H, S_A, S_B1, S_L;  fx1 / fx2 from k_prove_fixed;  v from k_prove_var
+__global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2, const g1_xyzz* fx1,
+                           const g2_xyzz* fx2, const g1_xyzz* v, uint32_t* proof) {
+    if ((threadIdx.x & 31) != 0) return;
+    int w = threadIdx.x >> 5;
+    if (w == 0) {
+        g1_xyzz A = xyzz_add(xyzz_add(xyzz_from_aff(fx->alpha1), res1[1]), fx1[0]);
+        write_g1(proof, A);
+    } else if (w == 1) {
+        g2_xyzz B = xyzz_add(xyzz_add(xyzz_from_aff(fx->beta2), resB2[0]), fx2[0]);
+        g2_aff b = aff_from_mont(xyzz_to_aff(B));
+        for (int i = 0; i < 8; i++) {
+            proof[16 + i] = b.x.c0.v[i];
+            proof[24 + i] = b.x.c1.v[i];
+            proof[32 + i] = b.y.c0.v[i];
+            proof[40 + i] = b.y.c1.v[i];
+        }
+    } else {
+        g1_xyzz C = xyzz_add(xyzz_add(res1[3], res1[0]), xyzz_add(xyzz_add(fx1[1], fx1[2]), fx1[3]));
+        C = xyzz_add(C, *v);
+        write_g1(proof + 48, C);
     }
-    g1_xyzz C = xyzz_add(xyzz_add(res1[3], res1[0]), acc);
-    C = xyzz_add(C, xyzz_neg(sm1[2]));
-    write_g1(proof, A);
-    g2_aff b = aff_from_mont(xyzz_to_aff(B));
-    for (int i = 0; i < 8; i++) {
-        proof[16 + i] = b.x.c0.v[i];
-        proof[24 + i] = b.x.c1.v[i];
-        proof[32 + i] = b.y.c0.v[i];
-        proof[40 + i] = b.y.c1.v[i];
-    }
-    write_g1(proof + 48, C);
 }
 
 // ---------------------------------------------------------------------------
@@ -170,10 +193,10 @@ struct ProvePlans {
 
 static ProvePlans prove_plans(const ace_pk* pk) {
     ProvePlans p;
-    p.H = msm_plan(pk->N);
-    p.A = msm_plan(pk->A.count);
-    p.B = msm_plan(pk->B1.count);
-    p.L = msm_plan(pk->L.count);
+    p.H = pk->H_plan;
+    p.A = pk->A.plan;
+    p.B = pk->B1.plan;
+    p.L = pk->L.plan;
     size_t N = pk->N;
     p.slot_bytes[0] = 3 * N * sizeof(fr_t) + msm_scratch_bytes<fp_t>(p.H, true) + (1 << 16);
     p.slot_bytes[1] = pk->A.count * sizeof(fr_t) + msm_scratch_bytes<fp_t>(p.A, true) + 4096;
@@ -212,14 +235,16 @@ int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const f
     for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, slot, k, pl.slot_bytes[k]));
     Arena& a0 = sl.ar[0];
     fr_t* abc = (fr_t*)a0.take(3 * pk->N * sizeof(fr_t));
-    g1_xyzz* res1 = (g1_xyzz*)a0.take(8 * sizeof(g1_xyzz));
+    g1_xyzz* res1 = (g1_xyzz*)a0.take(10 * sizeof(g1_xyzz));
     g2_xyzz* res2 = (g2_xyzz*)a0.take(2 * sizeof(g2_xyzz));
     if (!abc || !res1 || !res2) {
         set_error("prove: arena too small");
         return ACE_E_OOM;
     }
-    g1_xyzz* sm1 = res1 + 4;
-    g2_xyzz* sm2 = res2 + 1;
+    g1_xyzz* fx1 = res1 + 4;  // 4 fixed-base terms
+    g1_xyzz* vterm = res1 + 8;
+    g2_xyzz* fx2 = res2 + 1;
+    PkTabs tabs{pk->d_tab_alpha1, pk->d_tab_beta1, pk->d_tab_delta1, pk->d_tab_delta2};
     // r s mod r on the host
     fr_t rs = fe_from_mont(fe_to_mont(r) * fe_to_mont(s));
 
@@ -234,14 +259,20 @@ int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const f
     ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, sl.ar[2], res1 + 2, sl.aux[1]));
     ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, sl.ar[3], res2, sl.aux[2]));
     ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, sl.ar[4], res1 + 3, sl.aux[3]));
-    k_prove_smul<<<1, 32, 0, sl.aux[4]>>>(pk->d_fixed, r, s, rs, sm1, sm2); ::ace::note_launch();
+    k_prove_fixed<<<1, 160, 0, sl.aux[4]>>>(tabs, r, s, rs, fx1, fx2); ::ace::note_launch();
+    // V = s S_A + r S_B1 once the A and B1 MSMs are done, overlapping the rest
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[0], sl.aux[0]));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[1], sl.aux[1]));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(sl.aux[4], sl.ev_aux[0], 0));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(sl.aux[4], sl.ev_aux[1], 0));
+    k_prove_var<<<1, 32, 0, sl.aux[4]>>>(res1, r, s, vterm); ::ace::note_launch();
     ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, sl.main));
     ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, sl.main));
     for (int k = 0; k < 5; k++) {
         ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], sl.aux[k]));
         ACE_TRY_CUDA(cudaStreamWaitEvent(sl.main, sl.ev_aux[k], 0));
     }
-    k_assemble<<<1, 32, 0, sl.main>>>(pk->d_fixed, res1, res2, sm1, sm2, r, s, d_proof); ::ace::note_launch();
+    k_assemble<<<1, 96, 0, sl.main>>>(pk->d_fixed, res1, res2, fx1, fx2, vterm, d_proof); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     ACE_TRY_CUDA(cudaEventRecord(sl.ev_done, sl.main));
     if (join) ACE_TRY_CUDA(cudaStreamWaitEvent(st_in, sl.ev_done, 0));

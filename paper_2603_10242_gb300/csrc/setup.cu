@@ -8,7 +8,8 @@
 // Points (device): fixed-base multiplication of the generators, stored in
 // Montgomery affine form; zero scalars are compacted out of the queries, and
 // the H query is stored in bit-reversed order to match the quotient the QAP
-// step leaves in bit-reversed order.
+// step leaves in bit-reversed order.  Every query is kept with its MSM window
+// table (window w holds 2^(c w) times the points).
 #include <string.h>
 
 #include <algorithm>
@@ -18,6 +19,31 @@
 #include "pk.h"
 
 namespace ace {
+
+int pk_build_tables(ace_pk* pk, const PkFixed& f) {
+    const size_t T = 32 * 255;
+    ACE_TRY(pk_alloc(pk, (void**)&pk->d_tab_alpha1, T * sizeof(g1_aff)));
+    ACE_TRY(pk_alloc(pk, (void**)&pk->d_tab_beta1, T * sizeof(g1_aff)));
+    ACE_TRY(pk_alloc(pk, (void**)&pk->d_tab_delta1, T * sizeof(g1_aff)));
+    ACE_TRY(pk_alloc(pk, (void**)&pk->d_tab_delta2, T * sizeof(g2_aff)));
+    cudaStream_t st = pk->ctx->stream;
+    ACE_TRY(fixed_table_build<fp_t>(pk->ctx, f.alpha1, pk->d_tab_alpha1, st));
+    ACE_TRY(fixed_table_build<fp_t>(pk->ctx, f.beta1, pk->d_tab_beta1, st));
+    ACE_TRY(fixed_table_build<fp_t>(pk->ctx, f.delta1, pk->d_tab_delta1, st));
+    ACE_TRY(fixed_table_build<fp2_t>(pk->ctx, f.delta2, pk->d_tab_delta2, st));
+    return ACE_OK;
+}
+
+template <class F>
+int pk_alloc_table(ace_pk* pk, uint32_t count, MsmPlan* plan, Affine<F>** tab) {
+    *plan = msm_plan_tabled(count);
+    void* p = nullptr;
+    ACE_TRY(pk_alloc(pk, &p, (size_t)plan->K * count * sizeof(Affine<F>) + 16));
+    *tab = (Affine<F>*)p;
+    return ACE_OK;
+}
+template int pk_alloc_table<fp_t>(ace_pk*, uint32_t, MsmPlan*, Affine<fp_t>**);
+template int pk_alloc_table<fp2_t>(ace_pk*, uint32_t, MsmPlan*, Affine<fp2_t>**);
 
 int pk_alloc(ace_pk* pk, void** p, size_t bytes) {
     ACE_TRY(dev_alloc(pk->ctx, p, bytes));
@@ -95,14 +121,13 @@ static int build_query(ace_pk* pk, const std::vector<fr_t>& scal, uint64_t from,
     q.count = (uint32_t)idx.size();
     q.h_idx = idx;
     ACE_TRY(upload(pk, idx.data(), idx.size() * 4, &q.d_idx));
-    void* pts = nullptr;
-    ACE_TRY(pk_alloc(pk, &pts, (size_t)q.count * sizeof(Affine<F>) + 16));
-    q.d_pts = (Affine<F>*)pts;
+    ACE_TRY(pk_alloc_table<F>(pk, q.count, &q.plan, &q.d_pts));
     if (q.count) {
         fr_t* d_sc = nullptr;
         ACE_TRY_CUDA(cudaMalloc(&d_sc, sc.size() * sizeof(fr_t)));
         ACE_TRY_CUDA(cudaMemcpy(d_sc, sc.data(), sc.size() * sizeof(fr_t), cudaMemcpyHostToDevice));
         int rc = fixed_base_mul<F>(pk->ctx, (const uint32_t*)d_sc, q.count, q.d_pts, true, st);
+        if (rc == ACE_OK) rc = msm_build_table<F>(q.plan, q.d_pts, q.d_pts, st);
         cudaError_t e = cudaStreamSynchronize(st);
         cudaFree(d_sc);
         ACE_TRY(rc);
@@ -242,10 +267,9 @@ int ace_setup_toy(ace_ctx* ctx, const ace_circuit* c, uint64_t toxic_seed, ace_p
         for (uint64_t p = 0; p < N; p++) hs[p] = fe_from_mont(hq[h_brev((uint32_t)p, log_n)]);
         fr_t* d_sc = nullptr;
         SETUP_TRY(upload(pk, hs.data(), N * sizeof(fr_t), &d_sc));
-        void* pts = nullptr;
-        SETUP_TRY(pk_alloc(pk, &pts, N * sizeof(g1_aff)));
-        pk->d_H = (g1_aff*)pts;
+        SETUP_TRY(pk_alloc_table<fp_t>(pk, (uint32_t)N, &pk->H_plan, &pk->d_H));
         SETUP_TRY(fixed_base_mul<fp_t>(ctx, (const uint32_t*)d_sc, N, pk->d_H, true, st));
+        SETUP_TRY(msm_build_table<fp_t>(pk->H_plan, pk->d_H, pk->d_H, st));
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             set_error("setup: H query kernel failed");
             pk_release(pk);
@@ -282,6 +306,7 @@ int ace_setup_toy(ace_ctx* ctx, const ace_circuit* c, uint64_t toxic_seed, ace_p
         f.beta2 = h2[0];
         f.delta2 = h2[2];
         SETUP_TRY(upload(pk, &f, sizeof f, &pk->d_fixed));
+        SETUP_TRY(pk_build_tables(pk, f));
         canon_point<fp_t>(h1[0], &pk->vk.alpha1);
         canon_point<fp2_t>(h2[0], &pk->vk.beta2);
         canon_point<fp2_t>(h2[1], &pk->vk.gamma2);

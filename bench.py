@@ -453,6 +453,107 @@ def run_batch_workload(args):
                       "batch_slots": 2}))
 
 
+SERVE_CLASSES = (19, 20, 21, 22, 23)
+
+
+def serve_class_params(log_n):
+    """Size class of the served workload: 2 permutations per transaction, the
+    chain fills the domain; capacity floor((N - 3) / 486) transactions."""
+    n = 1 << log_n
+    cap = (n - 3) // 486
+    return (log_n, n, 2 * cap, 0, 0), cap
+
+
+def run_serve(args):
+    """BASELINE config 5: Poisson arrivals (mean 400 ms) of block-proof jobs
+    with 1,000..16,000 transactions, each proved under the smallest size class
+    (2^19..2^23) that holds it, by the continuous-batching server; keys of all
+    classes resident.  Reports p50/p99 latency (submission -> proof bytes on
+    the host) against the 600 ms budget, and proofs/s."""
+    import math
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2603_10242_gb300 as ace
+    from paper_2603_10242_gb300 import inputs
+
+    ace.build()
+    ctx = ace.Context(0)
+    t0 = time.perf_counter()
+    classes = {}
+    for ln in SERVE_CLASSES:
+        params, cap = serve_class_params(ln)
+        c = ace.Circuit(*params, seed=5000 + ln)
+        pk = ace.ProvingKey(ctx, c, toxic_seed=5000 + ln)
+        pool = []
+        for w in range(2):
+            z = c.witness(6000 + 10 * ln + w)
+            pool.append((torch.frombuffer(bytearray(z), dtype=torch.uint8).pin_memory(), z[32:64]))
+        classes[ln] = (cap, c, pk, pool)
+    setup_s = time.perf_counter() - t0
+    n_jobs = args.jobs
+    gaps = inputs.splitmix64(7, inputs.PURPOSE["arrivals"], n_jobs)
+    txs = inputs.splitmix64(7, inputs.PURPOSE["sizes"], n_jobs)
+    arrivals, t = [], 0.0
+    for g in gaps:
+        u = float(int(g) >> 11) * (2.0 ** -53)
+        t += -0.4 * math.log(1.0 - u)
+        arrivals.append(t)
+    tx_counts = [1000 + int(x) % 15001 for x in txs]
+    job_class = [min(ln for ln in SERVE_CLASSES if classes[ln][0] >= tx) for tx in tx_counts]
+    srv = ace.Server(ctx, classes[SERVE_CLASSES[-1]][2], slots=args.serve_slots)
+    ids = [None] * n_jobs
+    start = time.perf_counter()
+
+    def submitter():
+        for i in range(n_jobs):
+            now = time.perf_counter() - start
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            ln = job_class[i]
+            zh, _ = classes[ln][3][i % 2]
+            r, s_ = ace.rs_from_seed(9000 + i)
+            ids[i] = srv.submit(classes[ln][2], zh, r, s_)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, codes, proofs = [0.0] * n_jobs, [0] * n_jobs, {}
+    for i in range(n_jobs):
+        while ids[i] is None:
+            time.sleep(0.0005)
+        try:
+            proof, l = srv.wait(ids[i], 600)
+            lat[i] = l
+            if i % 97 == 0:
+                proofs[i] = proof
+        except ace.AceError as e:
+            codes[i] = e.code
+    th.join()
+    elapsed = time.perf_counter() - start
+    stats = srv.stats()
+    srv.close()
+    ok = [l for l, c in zip(lat, codes) if c == 0]
+    ok_sorted = sorted(ok)
+    verified = all(classes[job_class[i]][2].verify(classes[job_class[i]][3][i % 2][1], p) == 1
+                   for i, p in proofs.items())
+
+    def pct(q):
+        return ok_sorted[min(len(ok_sorted) - 1, int(round(q * (len(ok_sorted) - 1))))] if ok_sorted else None
+
+    print(json.dumps({
+        "workload": "groth16_served_poisson_400ms", "jobs": n_jobs, "completed": len(ok),
+        "errors": sum(1 for c in codes if c), "proofs_per_s": len(ok) / elapsed,
+        "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": ok_sorted[-1] if ok_sorted else None,
+                       "mean": float(np.mean(ok)) if ok else None, "budget_ms": 600.0,
+                       "over_budget_fraction": sum(1 for l in ok if l > 600.0) / max(1, len(ok))},
+        "class_counts": {str(ln): job_class.count(ln) for ln in SERVE_CLASSES},
+        "mean_tx": float(np.mean(tx_counts)), "slots": args.serve_slots, "server": stats,
+        "elapsed_s": elapsed, "setup_s": setup_s, "verified_sampled": verified,
+        "key_device_bytes": {str(ln): classes[ln][2].info[10] for ln in SERVE_CLASSES}}))
+
+
 def run_case(args):
     """Small fixed launches for profiler captures (not a bench line):
     msm_g1 -- one G1 MSM of 2^20 points (uniform scalars);
@@ -494,7 +595,9 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["block2p20", "batch64"], default="block2p20",
+    ap.add_argument("--jobs", type=int, default=300, help="served workload: number of jobs")
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--workload", choices=["block2p20", "batch64", "serve"], default="block2p20",
                     help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
     ap.add_argument("--case", choices=["msm_g1", "ntt", "prove16"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
@@ -508,6 +611,8 @@ def main():
         run_case(args)
     elif args.workload == "batch64":
         run_batch_workload(args)
+    elif args.workload == "serve":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

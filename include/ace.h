@@ -280,6 +280,68 @@ int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
 int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,
                     const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status);
 
+/* Proof server with continuous batching: block-proof jobs are proved as
+ * they arrive (the builder loop of Section 3.3, Algorithm 3).  A job starts
+ * as soon as one of `slots` proving slots is idle and the device memory it
+ * needs (witness + scratch of its key's size) fits hbm_budget_bytes (0 = the
+ * memory of `slots` jobs of max_pk's size); running jobs overlap on the
+ * device.  A job not started within max_queue_wait_s (> 0) seconds of its
+ * submission ends with ACE_E_TIMEOUT.  Slot scratch is sized for max_pk at
+ * creation.  While the server exists, one server thread owns the context:
+ * do not use the context from other threads (submit / poll / wait are
+ * thread-safe).  Latency is measured from submission to proof bytes on the
+ * host. */
+int ace_server_create(ace_ctx* ctx, const ace_pk* max_pk, int slots, size_t hbm_budget_bytes,
+                      double max_queue_wait_s, ace_server** out);
+/* Queue one proof of witness z_host (host, m canonical Fr; pinned memory
+ * recommended; must stay valid until the job's result is collected) under
+ * key pk (m <= max_pk's m) with randomness r, s. */
+int ace_server_submit(ace_server* srv, const ace_pk* pk, const ace_fr* z_host, const ace_fr* r, const ace_fr* s,
+                      uint64_t* job_id);
+/* ACE_E_BUSY while the job runs; otherwise its result (ACE_OK with the 256
+ * proof bytes, ACE_E_UNSAT, ACE_E_TIMEOUT, ...) and latency in ms, after
+ * which the job id is released. */
+int ace_server_poll(ace_server* srv, uint64_t job_id, uint8_t proof_out[256], double* latency_ms);
+/* Like ace_server_poll but blocks up to timeout_s (<= 0: no limit);
+ * ACE_E_BUSY if the job is still running when the time is up. */
+int ace_server_wait(ace_server* srv, uint64_t job_id, uint8_t proof_out[256], double* latency_ms, double timeout_s);
+/* submitted, collected, timeouts, waiting, peak running jobs, peak admitted
+ * device bytes, budget, slots */
+int ace_server_stats(ace_server* srv, uint64_t out[8]);
+/* Finishes the jobs already submitted, then stops the server thread. */
+int ace_server_destroy(ace_server* srv);
+/* Host-only check of the server's admission logic on a virtual clock: jobs
+ * with the given arrival time, run time and memory on `slots` slots and a
+ * memory budget; returns each job's start / finish time and status (0, -2
+ * never fits, -6 timed out) and peaks[0] = most jobs running at once,
+ * peaks[1] = most memory admitted at once. */
+int ace_debug_scheduler_sim(int slots, size_t budget, size_t n, const double* arrival, const double* duration,
+                            const size_t* mem, double max_wait, double* start_out, double* finish_out,
+                            int32_t* status_out, uint64_t* peaks);
+
+/* ---- autotuning ------------------------------------------------------------ */
+
+/* Measure candidate MSM window sizes c for the generic G1 MSM at
+ * n = 2^log_min .. 2^log_max (6 <= log_min <= log_max <= 24) on synthetic
+ * inputs and keep the fastest per size in the context (ace_msm_g1 then uses
+ * it).  report (optional, 5 doubles per size): log_n, chosen c, its ms,
+ * cost-model c, its ms. */
+int ace_autotune_msm(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* report);
+/* Measure the NTT pass width (2^10, 2^11 or 2^12 elements per block in shared
+ * memory) for N = 2^log_min .. 2^log_max (8..24) on three arrays and keep the
+ * fastest per size.  report (optional, 4 per size): log_n, chosen width, its
+ * ms, ms at 2^11. */
+int ace_autotune_ntt(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* report);
+/* Time batches of k proofs of (pk, d_z) over 1..max_slots proving slots and
+ * keep the fastest count for ace_prove_batch.  report (optional, max_slots
+ * doubles): ms per batch for each count. */
+int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, int k, int max_slots,
+                             double* report);
+/* Save / load the tuned choices (JSON keyed by the GPU name; loading a file
+ * tuned on another GPU fails with ACE_E_ARG and changes nothing). */
+int ace_autotune_save(ace_ctx* ctx, const char* path);
+int ace_autotune_load(ace_ctx* ctx, const char* path);
+
 /* ---- persistence ---------------------------------------------------------- */
 
 /* Save / load a proving key (with its circuit) to a versioned file. */

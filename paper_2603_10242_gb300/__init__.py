@@ -77,6 +77,19 @@ def lib():
             "ace_pk_save": (i32, [vp, cp]),
             "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
             "ace_debug_pairing": (i32, [cp, cp, cp]),
+            "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
+            "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
+            "ace_autotune_batch_slots": (i32, [vp, vp, vp, i32, i32, vp]),
+            "ace_autotune_save": (i32, [vp, cp]),
+            "ace_autotune_load": (i32, [vp, cp]),
+            "ace_server_create": (i32, [vp, vp, i32, sz, ctypes.c_double, ctypes.POINTER(vp)]),
+            "ace_server_submit": (i32, [vp, vp, vp, cp, cp, ctypes.POINTER(u64)]),
+            "ace_server_poll": (i32, [vp, u64, vp, ctypes.POINTER(ctypes.c_double)]),
+            "ace_server_wait": (i32, [vp, u64, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_double]),
+            "ace_server_stats": (i32, [vp, ctypes.POINTER(u64)]),
+            "ace_server_destroy": (i32, [vp]),
+            "ace_debug_scheduler_sim": (i32, [i32, sz, sz, vp, vp, vp, ctypes.c_double, vp, vp, vp,
+                                              ctypes.POINTER(u64)]),
             "ace_debug_imad_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "ace_debug_chain_latency": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "ace_debug_mul_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -178,6 +191,30 @@ class Context:
     def ntt_mont(self, data, log_n: int, count: int, dif: bool, inverse: bool, stream=None):
         check(lib().ace_ntt_mont(self.h, _ptr(data), log_n, count, 1 if dif else 0, 1 if inverse else 0,
                                  _stream(stream)))
+
+    # ---- autotuning ----
+    def autotune_msm(self, log_min: int, log_max: int):
+        n = log_max - log_min + 1
+        rep = (ctypes.c_double * (5 * n))()
+        check(lib().ace_autotune_msm(self.h, log_min, log_max, rep))
+        return [tuple(rep[5 * i:5 * i + 5]) for i in range(n)]
+
+    def autotune_ntt(self, log_min: int, log_max: int):
+        n = log_max - log_min + 1
+        rep = (ctypes.c_double * (4 * n))()
+        check(lib().ace_autotune_ntt(self.h, log_min, log_max, rep))
+        return [tuple(rep[4 * i:4 * i + 4]) for i in range(n)]
+
+    def autotune_batch_slots(self, pk: "ProvingKey", d_z, k: int, max_slots: int = 4):
+        rep = (ctypes.c_double * max_slots)()
+        check(lib().ace_autotune_batch_slots(self.h, pk.h, _ptr(d_z), k, max_slots, rep))
+        return list(rep)
+
+    def autotune_save(self, path: str):
+        check(lib().ace_autotune_save(self.h, path.encode()))
+
+    def autotune_load(self, path: str):
+        check(lib().ace_autotune_load(self.h, path.encode()))
 
     def qap_h(self, pk: "ProvingKey", d_z, d_h, stream=None):
         check(lib().ace_qap_h(self.h, pk.h, _ptr(d_z), _ptr(d_h), _stream(stream)))
@@ -352,3 +389,75 @@ def mul_rate(ctx: Context, form: int):
     d = (ctypes.c_uint32 * 4)()
     check(lib().ace_debug_mul_rate(ctx.h, form, ctypes.byref(a), ctypes.byref(b), d))
     return a.value, b.value, list(d)
+
+
+class Server:
+    """ace_server: continuous-batching proof server on its own context."""
+
+    def __init__(self, ctx: Context, max_pk: "ProvingKey", slots: int = 2, hbm_budget_bytes: int = 0,
+                 max_queue_wait_s: float = 0.0):
+        h = ctypes.c_void_p()
+        check(lib().ace_server_create(ctx.h, max_pk.h, slots, hbm_budget_bytes, max_queue_wait_s, ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, pk: "ProvingKey", z_host, r: bytes, s: bytes) -> int:
+        """z_host: a host buffer (ctypes buffer or pinned torch tensor) kept alive until collected."""
+        jid = ctypes.c_uint64()
+        addr = z_host.data_ptr() if hasattr(z_host, "data_ptr") else ctypes.addressof(z_host)
+        check(lib().ace_server_submit(self.h, pk.h, addr, r, s, ctypes.byref(jid)))
+        self._keep[jid.value] = z_host
+        return jid.value
+
+    def _result(self, rc, jid, out, lat):
+        self._keep.pop(jid, None)
+        if rc < 0:
+            raise AceError(rc, lib().ace_last_error().decode(errors="replace"))
+        return out.raw, lat.value
+
+    def poll(self, jid: int):
+        """None while running, else (proof bytes, latency ms); raises on job errors."""
+        out = ctypes.create_string_buffer(256)
+        lat = ctypes.c_double()
+        rc = lib().ace_server_poll(self.h, jid, out, ctypes.byref(lat))
+        if rc == -7:
+            return None
+        return self._result(rc, jid, out, lat)
+
+    def wait(self, jid: int, timeout_s: float = 0.0):
+        out = ctypes.create_string_buffer(256)
+        lat = ctypes.c_double()
+        rc = lib().ace_server_wait(self.h, jid, out, ctypes.byref(lat), timeout_s)
+        if rc == -7:
+            return None
+        return self._result(rc, jid, out, lat)
+
+    def stats(self) -> dict:
+        v = (ctypes.c_uint64 * 8)()
+        check(lib().ace_server_stats(self.h, v))
+        keys = ["submitted", "collected", "timeouts", "waiting", "peak_running", "peak_bytes", "budget", "slots"]
+        return dict(zip(keys, [int(x) for x in v]))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ace_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scheduler_sim(slots: int, budget: int, arrival, duration, mem, max_wait: float = 0.0):
+    """Run the server's admission logic on a virtual clock (host only)."""
+    n = len(arrival)
+    A = (ctypes.c_double * n)(*arrival)
+    D = (ctypes.c_double * n)(*duration)
+    M = (ctypes.c_size_t * n)(*mem)
+    st, fi = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    status = (ctypes.c_int32 * n)()
+    peaks = (ctypes.c_uint64 * 2)()
+    check(lib().ace_debug_scheduler_sim(slots, budget, n, A, D, M, max_wait, st, fi, status, peaks))
+    return list(st), list(fi), list(status), (int(peaks[0]), int(peaks[1]))

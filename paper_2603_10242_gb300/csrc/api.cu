@@ -33,7 +33,9 @@ static int msm_entry(ace_ctx* ctx, const void* d_bases, int base_form, const ace
         return ACE_E_ARG;
     }
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
-    MsmPlan plan = msm_plan(n);
+    int lg = 0;
+    while (lg < 31 && ((size_t)1 << (lg + 1)) <= n) lg++;
+    MsmPlan plan = msm_plan(n, ctx->tuned_msm_c[lg]);
     bool mont = base_form == ACE_FORM_MONT;
     ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<F>(plan, mont)));
     return msm_run<F>(plan, (const Affine<F>*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,

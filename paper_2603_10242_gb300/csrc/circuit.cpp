@@ -256,10 +256,34 @@ int ace_circuit_gen(const ace_circuit_params* p, ace_circuit** out) {
     b.c = c;
     b.alloc();  // z_0
     b.alloc();  // z_1
+    // Every permutation has the same rows over its own block of
+    // 3 + ROWS_PER_PERM variables (and z_0 for constants): build the first
+    // one with linear combinations, then replicate its rows with the
+    // variable block shifted.
     Lc chain_start;
-    for (uint32_t q = 0; q < p->n_perm; q++) {
-        Lc o = b.permutation();
-        if (q + 1 == p->n_perm) chain_start = o;
+    if (p->n_perm > 0) {
+        const uint32_t v0 = b.next_var, r0 = b.rows;
+        Lc out0 = b.permutation();
+        const uint32_t nv = b.next_var - v0, nr = b.rows - r0;
+        for (uint32_t q = 1; q < p->n_perm; q++) {
+            const uint32_t shift = q * nv;
+            for (uint32_t rr = 0; rr < nr; rr++) {
+                for (int k = 0; k < 3; k++) {
+                    Csr& m = c->mat[k];
+                    uint32_t a = m.rp[r0 + rr], bnd = m.rp[r0 + rr + 1];
+                    for (uint32_t e = a; e < bnd; e++) {
+                        uint32_t v = m.col[e];
+                        m.col.push_back(v == 0 ? 0u : v + shift);
+                        m.val.push_back(m.val[e]);
+                    }
+                    m.rp[b.rows + 1] = (uint32_t)m.col.size();
+                }
+                b.rows++;
+            }
+            b.next_var += nv;
+        }
+        const uint32_t last_shift = (p->n_perm - 1) * nv;
+        for (auto& t : out0) chain_start.push_back({t.first == 0 ? 0u : t.first + last_shift, t.second});
     }
     for (uint32_t q = 0; q < p->n_pack; q++) {
         Lc A;

@@ -145,6 +145,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
         delete p;
         return ACE_E_CUDA;
     }
+    if (ctx->tuned_ntt_smem[log_n]) p->smem_log = ctx->tuned_ntt_smem[log_n];
     ctx->ntt_plans[log_n] = p;
     *out = p;
     return ACE_OK;
@@ -250,12 +251,13 @@ __global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int l
     }
 }
 
-static const int NTT_MAX_T = 11;     // 2^11 elements x 32 B = 64 KB of shared memory per group
-static const int NTT_SMEM_LOG = 11;  // elements staged per block
+// a pass handles up to 2^smem_log elements per block (2^11 x 32 B = 64 KB of
+// shared memory); the plan's smem_log is chosen by the autotuner (10..12)
 
 int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, const NttScale& pre,
             const NttScale& post, cudaStream_t st) {
     const int k = plan.log_n;
+    const int NTT_MAX_T = plan.smem_log, NTT_SMEM_LOG = plan.smem_log;
     int passes[4], np = 0;
     if (k <= NTT_MAX_T) {
         passes[np++] = k;
@@ -270,8 +272,8 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
     }
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr_done = true;
     }
     const fr_t* tw = inverse ? plan.tw_inv : plan.tw_fwd;

@@ -32,6 +32,7 @@ struct NttPlan {
     fr_t* plain_one = nullptr;  // [1] as a plain value: multiplying by it leaves Montgomery form
     fr_t* rr = nullptr;       // [R^2 mod r] raw: multiplying by it enters Montgomery form
     fr_t zinv;                // (g^N - 1)^-1 (Montgomery)
+    int smem_log = 11;        // log2 of the elements one block stages in shared memory (tunable)
     void* mem = nullptr;
     size_t bytes = 0;
 };

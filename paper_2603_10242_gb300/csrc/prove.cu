@@ -206,6 +206,8 @@ static ProvePlans prove_plans(const ace_pk* pk) {
     return p;
 }
 
+size_t prove_slot_bytes(const ace_pk* pk, int arena) { return prove_plans(pk).slot_bytes[arena]; }
+
 template <class F>
 static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z, Arena& ar, Xyzz<F>* res,
                         cudaStream_t s) {

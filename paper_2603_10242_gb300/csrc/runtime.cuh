@@ -67,7 +67,7 @@ struct NttPlan;  // twiddle tables for one size (ntt.cu)
 // A proving slot: the streams, events and scratch one proof needs.  Proofs on
 // different slots run concurrently; proofs on the same slot run in order.
 static const int PROVE_ARENAS = 5;  // QAP + H MSM, A, B1, B2, L
-static const int MAX_SLOTS = 4;
+static const int MAX_SLOTS = 8;
 struct ProveSlot {
     bool ready = false;
     Arena ar[PROVE_ARENAS];
@@ -88,6 +88,10 @@ struct ace_ctx {
     ace::Arena scratch[4];  // scratch of single calls (MSM, NTT, QAP, batch outputs)
     ace::ProveSlot slots[ace::MAX_SLOTS];
     int batch_slots = 2;  // slots a batch spreads its proofs over
+    // autotuned choices (0 = cost model): MSM window bits by log2(n), NTT
+    // shared-memory width by log2(N)
+    int tuned_msm_c[32] = {};
+    int tuned_ntt_smem[32] = {};
     std::map<int, ace::NttPlan*> ntt_plans;
     void* g1_fixed_tab = nullptr;  // fixed-base tables for the generators (setup.cu)
     void* g2_fixed_tab = nullptr;

@@ -148,3 +148,25 @@ def test_block_scale_proof_in_the_exponent(log_n):
         assert pk.point("A", j) == O.g1_mul(g1, opk.scalar("u", j))
     for i in (0, lc.N - 2):
         assert pk.point("H", i) == O.g1_mul(g1, opk.scalar("h", i))
+
+
+def test_pk_save_load_roundtrip(tmp_path):
+    lc, oc = _pair((12, 4000, 8, 8, 172), seed=4)
+    ctx = gu.ctx()
+    pk = ace.ProvingKey(ctx, lc, toxic_seed=4)
+    z = lc.witness(4)
+    r, s = ace.rs_from_seed(4)
+    want = ctx.prove(pk, gu.dev(z), r, s)
+    path = str(tmp_path / "key.acepk")
+    pk.save(path)
+    pk2 = ace.ProvingKey.load(ctx, path)
+    assert (pk2.N, pk2.m) == (pk.N, pk.m) and pk2.info[7:10] == pk.info[7:10]
+    assert bytes(pk2.vk) == bytes(pk.vk)
+    assert ctx.prove(pk2, gu.dev(z), r, s) == want
+    assert pk2.verify(z[32:64], want) == 1
+    # a truncated file is rejected
+    data = open(path, "rb").read()
+    bad = str(tmp_path / "bad.acepk")
+    open(bad, "wb").write(data[: len(data) // 2])
+    with pytest.raises(ace.AceError):
+        ace.ProvingKey.load(ctx, bad)

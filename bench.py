@@ -343,6 +343,8 @@ def run_ours(args):
     achieved = units * IMAD_PER_G1_MADD / (ms / 1000.0) / 1e12 if ms > 0 else None
     measured_peak = {k: ace.imad_rate(ctx, mode) / 1e12 for k, mode in (("mad_lo", 0), ("mad_hi", 1),
                                                                        ("mad_lo_hi_chain", 2))}
+    # one mad.wide is one limb product = two 32-bit multiply-adds (lo and hi)
+    measured_peak["mad_wide_as_lo_hi"] = 2.0 * ace.imad_rate(ctx, 3) / 1e12
     traffic = None
     if G1_BUCKET_DRAM_BYTES_PER_MADD is not None and nl:
         traffic = G1_BUCKET_DRAM_BYTES_PER_MADD * units / nl
@@ -493,6 +495,23 @@ def run_serve(args):
             pool.append((torch.frombuffer(bytearray(z), dtype=torch.uint8).pin_memory(), z[32:64]))
         classes[ln] = (cap, c, pk, pool)
     setup_s = time.perf_counter() - t0
+    # latency of one proof per class with the GPU otherwise idle (same path:
+    # pinned host witness -> device, prove, proof bytes -> host)
+    alone_ms = {}
+    for ln in SERVE_CLASSES:
+        _, _, pk, pool = classes[ln]
+        zh = pool[0][0]
+        r, s_ = ace.rs_from_seed(8000 + ln)
+        ts = []
+        for _ in range(3):
+            dz = torch.empty(zh.numel(), dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            dz.copy_(zh, non_blocking=True)
+            ctx.prove(pk, dz, r, s_)
+            ts.append((time.perf_counter() - a) * 1e3)
+            del dz
+        alone_ms[str(ln)] = min(ts)
     n_jobs = args.jobs
     gaps = inputs.splitmix64(7, inputs.PURPOSE["arrivals"], n_jobs)
     txs = inputs.splitmix64(7, inputs.PURPOSE["sizes"], n_jobs)
@@ -539,8 +558,16 @@ def run_serve(args):
     verified = all(classes[job_class[i]][2].verify(classes[job_class[i]][3][i % 2][1], p) == 1
                    for i, p in proofs.items())
 
-    def pct(q):
-        return ok_sorted[min(len(ok_sorted) - 1, int(round(q * (len(ok_sorted) - 1))))] if ok_sorted else None
+    def pct(q, xs=None):
+        xs = ok_sorted if xs is None else xs
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+    per_class = {}
+    for ln in SERVE_CLASSES:
+        xs = sorted(l for l, c, jc in zip(lat, codes, job_class) if c == 0 and jc == ln)
+        if xs:
+            per_class[str(ln)] = {"jobs": len(xs), "p50": pct(0.5, xs), "p99": pct(0.99, xs), "max": xs[-1],
+                                  "alone_ms": alone_ms[str(ln)]}
 
     print(json.dumps({
         "workload": "groth16_served_poisson_400ms", "jobs": n_jobs, "completed": len(ok),
@@ -549,6 +576,7 @@ def run_serve(args):
                        "mean": float(np.mean(ok)) if ok else None, "budget_ms": 600.0,
                        "over_budget_fraction": sum(1 for l in ok if l > 600.0) / max(1, len(ok))},
         "class_counts": {str(ln): job_class.count(ln) for ln in SERVE_CLASSES},
+        "per_class_ms": per_class,
         "mean_tx": float(np.mean(tx_counts)), "slots": args.serve_slots, "server": stats,
         "elapsed_s": elapsed, "setup_s": setup_s, "verified_sampled": verified,
         "key_device_bytes": {str(ln): classes[ln][2].info[10] for ln in SERVE_CLASSES}}))

@@ -112,6 +112,9 @@ enum {
  * memory the context's caches and scratch may hold (0 = no bound); calls
  * that would exceed it return ACE_E_OOM. */
 int ace_ctx_create(ace_ctx** out, int device, size_t hbm_budget_bytes);
+/* Releases the context.  Proving keys and servers made on it keep it alive:
+ * with any of them left, the context is freed when the last one is freed
+ * (so the order in which a caller releases them does not matter). */
 int ace_ctx_destroy(ace_ctx* ctx);
 /* Message of the last error on this thread ("" if none).  Never NULL. */
 const char* ace_last_error(void);
@@ -248,7 +251,8 @@ int ace_debug_curve_op(int group, int op, const void* d_a, const void* d_b, cons
  * as 6 Fp2 coefficients (w^0, w^2, w^4, w^1, w^3, w^5), canonical. */
 int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
 /* Measured 32-bit multiply-add throughput of the device (operations/s):
- * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs. */
+ * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs, 3 mad.wide.u32
+ * (one 32 x 32 -> 64-bit limb product with 64-bit accumulate per operation). */
 int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s);
 
 /* Nanoseconds per step of a single-thread dependent chain: what = 0 Fp
@@ -257,9 +261,10 @@ int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s);
 int ace_debug_chain_latency(ace_ctx* ctx, int what, double* ns_per_step);
 
 /* Montgomery products per second over all SMs and single-thread latency
- * (ns) of product form 0 (32-bit low/high multiply-add chains) or form 1
- * (64-bit wide products, one carry chain per row); digest: 4 words of output
- * (optional) for comparing the forms. */
+ * (ns) of product form 0 (32-bit low/high multiply-add chains), form 1
+ * (64-bit wide multiply-adds, one carry chain per row) or form 2 (plain 64-bit
+ * products, two carry chains per row); digest: 4 words of output (optional)
+ * for comparing the forms. */
 int ace_debug_mul_rate(ace_ctx* ctx, int form, double* per_s, double* latency_ns, uint32_t* digest);
 
 /* Kernel launches issued by the library in this process so far. */
@@ -269,7 +274,10 @@ int ace_launch_count(uint64_t* out);
  * the device and returns, for one kind, the length of the union of the
  * bracketed intervals (ms), the launches and the work units:
  * kind 0 G1 bucket accumulation (units: mixed additions), 1 the same on G2,
- * 2 NTT passes (units: radix-2 butterflies), 3 sparse products (units: non-zeros). */
+ * 2 NTT passes (units: radix-2 butterflies), 3 sparse products (units:
+ * non-zeros), 4 MSM digit sort (units: scalars), 5 MSM bucket reduction
+ * (units: buckets), 6 proof-assembly scalar multiplications (units: launches).
+ * A bracket of kinds 4 and 5 spans several kernels of one MSM. */
 int ace_profile_enable(int on);
 int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
 

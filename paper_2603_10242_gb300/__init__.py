@@ -352,6 +352,7 @@ def verify(vk: VerifyingKey, public: bytes, proof: bytes) -> int:
 
 # ---- measurement hooks ----
 PROF_G1_BUCKET, PROF_G2_BUCKET, PROF_NTT, PROF_SPMV = 0, 1, 2, 3
+PROF_SORT, PROF_REDUCE, PROF_ASSEMBLY = 4, 5, 6
 
 
 def launch_count() -> int:
@@ -384,7 +385,7 @@ def chain_latency_ns(ctx: Context, what: int) -> float:
 
 
 def mul_rate(ctx: Context, form: int):
-    """(products/s, single-thread latency ns, digest) of Montgomery product form 0 or 1."""
+    """(products/s, single-thread latency ns, digest) of Montgomery product form 0, 1 or 2."""
     a, b = ctypes.c_double(), ctypes.c_double()
     d = (ctypes.c_uint32 * 4)()
     check(lib().ace_debug_mul_rate(ctx.h, form, ctypes.byref(a), ctypes.byref(b), d))
@@ -399,6 +400,9 @@ class Server:
         h = ctypes.c_void_p()
         check(lib().ace_server_create(ctx.h, max_pk.h, slots, hbm_budget_bytes, max_queue_wait_s, ctypes.byref(h)))
         self.h = h
+        # the server thread uses the context until destroyed, and each job its
+        # key and host witness until collected: keep them alive that long
+        self._ctx, self._max_pk = ctx, max_pk
         self._keep = {}
 
     def submit(self, pk: "ProvingKey", z_host, r: bytes, s: bytes) -> int:
@@ -406,7 +410,7 @@ class Server:
         jid = ctypes.c_uint64()
         addr = z_host.data_ptr() if hasattr(z_host, "data_ptr") else ctypes.addressof(z_host)
         check(lib().ace_server_submit(self.h, pk.h, addr, r, s, ctypes.byref(jid)))
-        self._keep[jid.value] = z_host
+        self._keep[jid.value] = (z_host, pk)
         return jid.value
 
     def _result(self, rc, jid, out, lat):

@@ -46,6 +46,15 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    # ACE_NVCC_FLAGS: extra compile flags (e.g. -DACE_MUL_FORM=2); a change of
+    # them rebuilds everything
+    extra = os.environ.get("ACE_NVCC_FLAGS", "").split()
+    stamp = os.path.join(BUILD, "flags.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if old != " ".join(extra):
+        force = True
+        with open(stamp, "w") as f:
+            f.write(" ".join(extra))
     hdr_time = max([os.path.getmtime(h) for h in _headers()] + [os.path.getmtime(__file__)])
     objs, todo = [], []
     for src in sources():
@@ -55,9 +64,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time)):
             continue
         if src.endswith(".cpp"):
-            cmd = [nvcc] + NVCC_FLAGS + ["-x", "c++", "-c", src, "-o", obj + ".tmp"]
+            cmd = [nvcc] + NVCC_FLAGS + extra + ["-x", "c++", "-c", src, "-o", obj + ".tmp"]
         else:
-            cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj + ".tmp"]
+            cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj + ".tmp"]
         todo.append((cmd, obj, src))
 
     def run(item):

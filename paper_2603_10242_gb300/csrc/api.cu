@@ -94,16 +94,20 @@ int ace_ctx_create(ace_ctx** out, int device, size_t hbm_budget_bytes) {
     return ACE_OK;
 }
 
-int ace_ctx_destroy(ace_ctx* c) {
-    if (!c) return ACE_OK;
+}  // extern "C"
+
+namespace {
+void ctx_destroy_now(ace_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto& a : c->scratch) dev_free(c, a.base, a.cap);
     for (auto& sl : c->slots) {
         for (auto& a : sl.ar) dev_free(c, a.base, a.cap);
         if (!sl.ready) continue;
-        cudaStreamDestroy(sl.main);
-        for (auto s : sl.aux) cudaStreamDestroy(s);
+        for (auto& lv : sl.lv) {
+            cudaStreamDestroy(lv.main);
+            for (auto s : lv.aux) cudaStreamDestroy(s);
+        }
         cudaEventDestroy(sl.ev_in);
         cudaEventDestroy(sl.ev_start);
         cudaEventDestroy(sl.ev_done);
@@ -114,6 +118,36 @@ int ace_ctx_destroy(ace_ctx* c) {
     if (c->g2_fixed_tab) dev_free(c, c->g2_fixed_tab, 32 * 255 * sizeof(g2_aff));
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+}  // namespace
+
+namespace ace {
+void ctx_ref(ace_ctx* ctx) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->users++;
+}
+void ctx_unref(ace_ctx* ctx) {
+    bool last;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        last = --ctx->users == 0 && ctx->closing;
+    }
+    if (last) ctx_destroy_now(ctx);
+}
+}  // namespace ace
+
+extern "C" {
+
+int ace_ctx_destroy(ace_ctx* c) {
+    if (!c) return ACE_OK;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        if (c->users > 0) {  // freed by the last key or server released
+            c->closing = true;
+            return ACE_OK;
+        }
+    }
+    ctx_destroy_now(c);
     return ACE_OK;
 }
 
@@ -359,8 +393,9 @@ int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units) 
 
 namespace ace {
 // Independent multiply-add chains: 8 per thread, `iters` rounds, in one of
-// three forms: 0 mad.lo.u32, 1 mad.hi.u32, 2 the carry-chained
-// mad.lo.cc / madc.hi.cc pairs of the Montgomery product.
+// four forms: 0 mad.lo.u32, 1 mad.hi.u32, 2 the carry-chained
+// mad.lo.cc / madc.hi.cc pairs of the Montgomery product, 3 mad.wide.u32
+// (32 x 32 + 64 -> 64 bits, the limb product of the wide form).
 __global__ void k_imad_rate(int mode, int iters, uint32_t seed, uint32_t* out) {
     uint32_t a[8], b = seed ^ (threadIdx.x * 2654435761u), c = blockIdx.x + 12345u;
 #pragma unroll
@@ -373,6 +408,19 @@ __global__ void k_imad_rate(int mode, int iters, uint32_t seed, uint32_t* out) {
         for (int i = 0; i < iters; i++)
 #pragma unroll
             for (int k = 0; k < 8; k++) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(b), "r"(c));
+    } else if (mode == 3) {
+        uint64_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) w[k] = a[k];
+        // the multiplier is the chain's own low word, so no product is loop-invariant
+        for (int i = 0; i < iters; i++)
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                asm volatile("{\n\t.reg .u32 lo, hi;\n\tmov.b64 {lo, hi}, %0;\n\tmad.wide.u32 %0, lo, %1, %0;\n\t}"
+                             : "+l"(w[k])
+                             : "r"(b | 1u));
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = (uint32_t)w[k] ^ (uint32_t)(w[k] >> 32);
     } else {
         for (int i = 0; i < iters; i++)
 #pragma unroll
@@ -391,10 +439,10 @@ __global__ void k_imad_rate(int mode, int iters, uint32_t seed, uint32_t* out) {
 extern "C" {
 
 // Measured 32-bit multiply-add rate (operations per second) of the device:
-// mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs.
+// mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs, 3 mad.wide.
 int ace_debug_imad_rate(ace_ctx* ctx, int mode, double* ops_per_s) {
     clear_error();
-    if (!ctx || !ops_per_s || mode < 0 || mode > 2) {
+    if (!ctx || !ops_per_s || mode < 0 || mode > 3) {
         set_error("ace_debug_imad_rate: bad argument");
         return ACE_E_ARG;
     }
@@ -498,7 +546,8 @@ __global__ void k_mul_rate(int iters, uint32_t* out) {
         for (int k = 0; k < 4; k++) {
             fp_t r;
             if (V == 0) d_mul<FpCfg>(r.v, x[k].v, y.v);
-            else d_mul_wide<FpCfg>(r.v, x[k].v, y.v);
+            else if (V == 1) d_mul_wide<FpCfg>(r.v, x[k].v, y.v);
+            else d_mul_pw<FpCfg>(r.v, x[k].v, y.v);
             x[k] = r;
         }
     }
@@ -514,7 +563,8 @@ __global__ void k_mul_latency(int iters, fp_t x, uint32_t* out) {
     for (int i = 0; i < iters; i++) {
         fp_t r;
         if (V == 0) d_mul<FpCfg>(r.v, x.v, x.v);
-        else d_mul_wide<FpCfg>(r.v, x.v, x.v);
+        else if (V == 1) d_mul_wide<FpCfg>(r.v, x.v, x.v);
+        else d_mul_pw<FpCfg>(r.v, x.v, x.v);
         x = r;
     }
     out[0] = x.v[0];
@@ -525,11 +575,12 @@ __global__ void k_mul_latency(int iters, fp_t x, uint32_t* out) {
 extern "C" {
 
 // Diagnostic: Montgomery products per second (all SMs) and single-thread
-// latency (ns) of form 0 (lo/hi multiply-add chains) or form 1 (64-bit wide
-// products); digest (optional, 4 words) lets callers compare the two forms.
+// latency (ns) of form 0 (lo/hi multiply-add chains), form 1 (64-bit wide
+// multiply-adds) or form 2 (plain wide products, two carry chains per row);
+// digest (optional, 4 words) lets callers compare the forms.
 int ace_debug_mul_rate(ace_ctx* ctx, int form, double* per_s, double* latency_ns, uint32_t* digest) {
     clear_error();
-    if (!ctx || !per_s || !latency_ns || form < 0 || form > 1) {
+    if (!ctx || !per_s || !latency_ns || form < 0 || form > 2) {
         set_error("ace_debug_mul_rate: bad argument");
         return ACE_E_ARG;
     }
@@ -544,7 +595,8 @@ int ace_debug_mul_rate(ace_ctx* ctx, int form, double* per_s, double* latency_ns
     ACE_TRY_CUDA(cudaEventCreate(&b));
     auto run = [&](int it) {
         if (form == 0) k_mul_rate<0><<<blocks, threads, 0, ctx->stream>>>(it, d);
-        else k_mul_rate<1><<<blocks, threads, 0, ctx->stream>>>(it, d);
+        else if (form == 1) k_mul_rate<1><<<blocks, threads, 0, ctx->stream>>>(it, d);
+        else k_mul_rate<2><<<blocks, threads, 0, ctx->stream>>>(it, d);
         ::ace::note_launch();
     };
     run(4);
@@ -560,7 +612,8 @@ int ace_debug_mul_rate(ace_ctx* ctx, int form, double* per_s, double* latency_ns
     const int lit = 4000;
     ACE_TRY_CUDA(cudaEventRecord(a, ctx->stream));
     if (form == 0) k_mul_latency<0><<<1, 1, 0, ctx->stream>>>(lit, x, d);
-    else k_mul_latency<1><<<1, 1, 0, ctx->stream>>>(lit, x, d);
+    else if (form == 1) k_mul_latency<1><<<1, 1, 0, ctx->stream>>>(lit, x, d);
+    else k_mul_latency<2><<<1, 1, 0, ctx->stream>>>(lit, x, d);
     ::ace::note_launch();
     ACE_TRY_CUDA(cudaEventRecord(b, ctx->stream));
     ACE_TRY_CUDA(cudaEventSynchronize(b));

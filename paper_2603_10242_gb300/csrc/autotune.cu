@@ -16,11 +16,6 @@
 #include "ntt.cuh"
 #include "pk.h"
 
-namespace ace {
-int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
-              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join);
-}
-
 using namespace ace;
 
 namespace {

@@ -459,6 +459,408 @@ ACE_DEV void d_mul_wide(uint32_t* r, const uint32_t* a, const uint32_t* b) {
 #undef ACE_WROW_MUL
 #undef ACE_WROW_RED
 
+// Third form: plain 64-bit products (mul.wide, no addend) folded into the
+// accumulator by two carry chains per row (low halves at limb j, high halves
+// at limb j+1).  Same result as d_mul / d_mul_wide.
+#define ACE_PROW_MUL(bi)                                                                         \
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,p4,p5,p6,p7;\n\t"                                       \
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"                        \
+        "mul.wide.u32 p0, %9, %17;\n\tmul.wide.u32 p1, %10, %17;\n\t"                         \
+        "mul.wide.u32 p2, %11, %17;\n\tmul.wide.u32 p3, %12, %17;\n\t"                        \
+        "mul.wide.u32 p4, %13, %17;\n\tmul.wide.u32 p5, %14, %17;\n\t"                        \
+        "mul.wide.u32 p6, %15, %17;\n\tmul.wide.u32 p7, %16, %17;\n\t"                        \
+        "mov.b64 {l0,h0}, p0;\n\tmov.b64 {l1,h1}, p1;\n\tmov.b64 {l2,h2}, p2;\n\t"             \
+        "mov.b64 {l3,h3}, p3;\n\tmov.b64 {l4,h4}, p4;\n\tmov.b64 {l5,h5}, p5;\n\t"             \
+        "mov.b64 {l6,h6}, p6;\n\tmov.b64 {l7,h7}, p7;\n\t"                                        \
+        "add.cc.u32 %0, %0, l0;\n\taddc.cc.u32 %1, %1, l1;\n\taddc.cc.u32 %2, %2, l2;\n\t"     \
+        "addc.cc.u32 %3, %3, l3;\n\taddc.cc.u32 %4, %4, l4;\n\taddc.cc.u32 %5, %5, l5;\n\t"    \
+        "addc.cc.u32 %6, %6, l6;\n\taddc.cc.u32 %7, %7, l7;\n\taddc.u32 %8, 0, 0;\n\t"          \
+        "add.cc.u32 %1, %1, h0;\n\taddc.cc.u32 %2, %2, h1;\n\taddc.cc.u32 %3, %3, h2;\n\t"     \
+        "addc.cc.u32 %4, %4, h3;\n\taddc.cc.u32 %5, %5, h4;\n\taddc.cc.u32 %6, %6, h5;\n\t"    \
+        "addc.cc.u32 %7, %7, h6;\n\taddc.u32 %8, %8, h7;\n\t}"                                   \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), \
+          "r"(bi))
+#define ACE_PROW_RED()                                                                           \
+    asm("{\n\t.reg .u64 q0,q1,q2,q3,q4,q5,q6,q7;\n\t.reg .u32 m;\n\t"                       \
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"                        \
+        "mul.lo.u32 m, %0, %9;\n\t"                                                              \
+        "mul.wide.u32 q0, m, %10;\n\tmul.wide.u32 q1, m, %11;\n\t"                             \
+        "mul.wide.u32 q2, m, %12;\n\tmul.wide.u32 q3, m, %13;\n\t"                             \
+        "mul.wide.u32 q4, m, %14;\n\tmul.wide.u32 q5, m, %15;\n\t"                             \
+        "mul.wide.u32 q6, m, %16;\n\tmul.wide.u32 q7, m, %17;\n\t"                             \
+        "mov.b64 {l0,h0}, q0;\n\tmov.b64 {l1,h1}, q1;\n\tmov.b64 {l2,h2}, q2;\n\t"             \
+        "mov.b64 {l3,h3}, q3;\n\tmov.b64 {l4,h4}, q4;\n\tmov.b64 {l5,h5}, q5;\n\t"             \
+        "mov.b64 {l6,h6}, q6;\n\tmov.b64 {l7,h7}, q7;\n\t"                                        \
+        "add.cc.u32 %0, %0, l0;\n\taddc.cc.u32 %1, %1, l1;\n\taddc.cc.u32 %2, %2, l2;\n\t"     \
+        "addc.cc.u32 %3, %3, l3;\n\taddc.cc.u32 %4, %4, l4;\n\taddc.cc.u32 %5, %5, l5;\n\t"    \
+        "addc.cc.u32 %6, %6, l6;\n\taddc.cc.u32 %7, %7, l7;\n\taddc.u32 %8, %8, 0;\n\t"         \
+        "add.cc.u32 %0, %1, h0;\n\taddc.cc.u32 %1, %2, h1;\n\taddc.cc.u32 %2, %3, h2;\n\t"     \
+        "addc.cc.u32 %3, %4, h3;\n\taddc.cc.u32 %4, %5, h4;\n\taddc.cc.u32 %5, %6, h5;\n\t"    \
+        "addc.cc.u32 %6, %7, h6;\n\taddc.u32 %7, %8, h7;\n\tmov.u32 %8, 0;\n\t}"               \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+        : "n"(C::INV), "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5),  \
+          "n"(C::M6), "n"(C::M7))
+
+template <class C>
+ACE_DEV void d_mul_pw(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
+    ACE_PROW_MUL(b[0]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[1]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[2]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[3]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[4]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[5]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[6]);
+    ACE_PROW_RED();
+    ACE_PROW_MUL(b[7]);
+    ACE_PROW_RED();
+    uint32_t d0, d1, d2, d3, d4, d5, d6, d7, mask;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;\n\t"
+        : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3), "=r"(d4), "=r"(d5), "=r"(d6), "=r"(d7), "=r"(mask)
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7),
+          "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5), "n"(C::M6), "n"(C::M7));
+    r[0] = (t0 & mask) | (d0 & ~mask);
+    r[1] = (t1 & mask) | (d1 & ~mask);
+    r[2] = (t2 & mask) | (d2 & ~mask);
+    r[3] = (t3 & mask) | (d3 & ~mask);
+    r[4] = (t4 & mask) | (d4 & ~mask);
+    r[5] = (t5 & mask) | (d5 & ~mask);
+    r[6] = (t6 & mask) | (d6 & ~mask);
+    r[7] = (t7 & mask) | (d7 & ~mask);
+}
+#undef ACE_PROW_MUL
+#undef ACE_PROW_RED
+
+// ---- separated product and reduction (lazy reduction) ----------------------
+// t[I..I+8] = t[I..I+7] + a * bi for the 512-bit product t (t[I+8] is not
+// read: no earlier row reached it)
+template <int I>
+ACE_DEV void d_w512_row(uint32_t (&t)[16], const uint32_t* a, uint32_t bi) {
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,p4,p5,p6,p7,c;\n\t"
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %9, %17, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %10, %17, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %11, %17, c;\n\t"
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 p3, %12, %17, c;\n\t"
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 p4, %13, %17, c;\n\t"
+        "mov.b64 c, {%5, 0};\n\tmad.wide.u32 p5, %14, %17, c;\n\t"
+        "mov.b64 c, {%6, 0};\n\tmad.wide.u32 p6, %15, %17, c;\n\t"
+        "mov.b64 c, {%7, 0};\n\tmad.wide.u32 p7, %16, %17, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\tmov.b64 {l1,h1}, p1;\n\tmov.b64 {l2,h2}, p2;\n\t"
+        "mov.b64 {l3,h3}, p3;\n\tmov.b64 {l4,h4}, p4;\n\tmov.b64 {l5,h5}, p5;\n\t"
+        "mov.b64 {l6,h6}, p6;\n\tmov.b64 {l7,h7}, p7;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.cc.u32 %2, l2, h1;\n\t"
+        "addc.cc.u32 %3, l3, h2;\n\t"
+        "addc.cc.u32 %4, l4, h3;\n\t"
+        "addc.cc.u32 %5, l5, h4;\n\t"
+        "addc.cc.u32 %6, l6, h5;\n\t"
+        "addc.cc.u32 %7, l7, h6;\n\t"
+        "addc.u32 %8, h7, 0;\n\t}"
+        : "+r"(t[I]), "+r"(t[I + 1]), "+r"(t[I + 2]), "+r"(t[I + 3]), "+r"(t[I + 4]), "+r"(t[I + 5]),
+          "+r"(t[I + 6]), "+r"(t[I + 7]), "=r"(t[I + 8])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(bi));
+}
+// the full 512-bit product of two 256-bit integers
+ACE_DEV void d_mul512(uint32_t (&t)[16], const uint32_t* a, const uint32_t* b) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) t[i] = 0;
+    d_w512_row<0>(t, a, b[0]);
+    d_w512_row<1>(t, a, b[1]);
+    d_w512_row<2>(t, a, b[2]);
+    d_w512_row<3>(t, a, b[3]);
+    d_w512_row<4>(t, a, b[4]);
+    d_w512_row<5>(t, a, b[5]);
+    d_w512_row<6>(t, a, b[6]);
+    d_w512_row<7>(t, a, b[7]);
+}
+// one Montgomery reduction row of a 512-bit value: m = t[I] * INV,
+// t += m p 2^(32 I); e carries the bit that overflowed limb I+7 of the
+// previous row into limb I+8 (e is 0/1 on entry and exit)
+template <class C, int I>
+ACE_DEV void d_redc_row(uint32_t (&t)[16], uint32_t& e) {
+    asm("{\n\t.reg .u64 q0,q1,q2,q3,q4,q5,q6,q7,c;\n\t.reg .u32 m;\n\t"
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"
+        "mul.lo.u32 m, %0, %10;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 q0, m, %11, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 q1, m, %12, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 q2, m, %13, c;\n\t"
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 q3, m, %14, c;\n\t"
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 q4, m, %15, c;\n\t"
+        "mov.b64 c, {%5, 0};\n\tmad.wide.u32 q5, m, %16, c;\n\t"
+        "mov.b64 c, {%6, 0};\n\tmad.wide.u32 q6, m, %17, c;\n\t"
+        "mov.b64 c, {%7, 0};\n\tmad.wide.u32 q7, m, %18, c;\n\t"
+        "mov.b64 {l0,h0}, q0;\n\tmov.b64 {l1,h1}, q1;\n\tmov.b64 {l2,h2}, q2;\n\t"
+        "mov.b64 {l3,h3}, q3;\n\tmov.b64 {l4,h4}, q4;\n\tmov.b64 {l5,h5}, q5;\n\t"
+        "mov.b64 {l6,h6}, q6;\n\tmov.b64 {l7,h7}, q7;\n\t"
+        "add.u32 h7, h7, %9;\n\t"
+        "add.cc.u32 %1, h0, l1;\n\t"
+        "addc.cc.u32 %2, h1, l2;\n\t"
+        "addc.cc.u32 %3, h2, l3;\n\t"
+        "addc.cc.u32 %4, h3, l4;\n\t"
+        "addc.cc.u32 %5, h4, l5;\n\t"
+        "addc.cc.u32 %6, h5, l6;\n\t"
+        "addc.cc.u32 %7, h6, l7;\n\t"
+        "addc.cc.u32 %8, %8, h7;\n\t"
+        "addc.u32 %9, 0, 0;\n\t}"
+        : "+r"(t[I]), "+r"(t[I + 1]), "+r"(t[I + 2]), "+r"(t[I + 3]), "+r"(t[I + 4]), "+r"(t[I + 5]),
+          "+r"(t[I + 6]), "+r"(t[I + 7]), "+r"(t[I + 8]), "+r"(e)
+        : "n"(C::INV), "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5), "n"(C::M6),
+          "n"(C::M7));
+}
+// r = t / 2^256 mod m for 0 <= t < m 2^256 (result fully reduced)
+template <class C>
+ACE_DEV void d_redc512(uint32_t* r, uint32_t (&t)[16]) {
+    uint32_t e = 0;
+    d_redc_row<C, 0>(t, e);
+    d_redc_row<C, 1>(t, e);
+    d_redc_row<C, 2>(t, e);
+    d_redc_row<C, 3>(t, e);
+    d_redc_row<C, 4>(t, e);
+    d_redc_row<C, 5>(t, e);
+    d_redc_row<C, 6>(t, e);
+    d_redc_row<C, 7>(t, e);
+    // t[8..15] < 2m (and e == 0): one conditional subtraction
+    uint32_t d0, d1, d2, d3, d4, d5, d6, d7, mask;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;\n\t"
+        : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3), "=r"(d4), "=r"(d5), "=r"(d6), "=r"(d7), "=r"(mask)
+        : "r"(t[8]), "r"(t[9]), "r"(t[10]), "r"(t[11]), "r"(t[12]), "r"(t[13]), "r"(t[14]), "r"(t[15]),
+          "n"(C::M0), "n"(C::M1), "n"(C::M2), "n"(C::M3), "n"(C::M4), "n"(C::M5), "n"(C::M6), "n"(C::M7));
+    r[0] = (t[8] & mask) | (d0 & ~mask);
+    r[1] = (t[9] & mask) | (d1 & ~mask);
+    r[2] = (t[10] & mask) | (d2 & ~mask);
+    r[3] = (t[11] & mask) | (d3 & ~mask);
+    r[4] = (t[12] & mask) | (d4 & ~mask);
+    r[5] = (t[13] & mask) | (d5 & ~mask);
+    r[6] = (t[14] & mask) | (d6 & ~mask);
+    r[7] = (t[15] & mask) | (d7 & ~mask);
+}
+// the 512-bit square of a 256-bit integer: the 28 products a_i a_j (i < j)
+// row by row, doubled, plus the 8 squares a_i^2 on the diagonal (36 limb
+// products instead of 64)
+ACE_DEV void d_sqr512(uint32_t (&t)[16], const uint32_t* a) {
+    t[0] = 0;
+#pragma unroll
+    for (int i = 1; i < 8; i++) t[i] = 0;
+    t[15] = 0;
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,p4,p5,p6,c;\n\t.reg .u32 l0,l1,l2,l3,l4,l5,l6,h0,h1,h2,h3,h4,h5,h6;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %8, %15, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %9, %15, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %10, %15, c;\n\t"
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 p3, %11, %15, c;\n\t"
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 p4, %12, %15, c;\n\t"
+        "mov.b64 c, {%5, 0};\n\tmad.wide.u32 p5, %13, %15, c;\n\t"
+        "mov.b64 c, {%6, 0};\n\tmad.wide.u32 p6, %14, %15, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b64 {l1,h1}, p1;\n\t"
+        "mov.b64 {l2,h2}, p2;\n\t"
+        "mov.b64 {l3,h3}, p3;\n\t"
+        "mov.b64 {l4,h4}, p4;\n\t"
+        "mov.b64 {l5,h5}, p5;\n\t"
+        "mov.b64 {l6,h6}, p6;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.cc.u32 %2, l2, h1;\n\t"
+        "addc.cc.u32 %3, l3, h2;\n\t"
+        "addc.cc.u32 %4, l4, h3;\n\t"
+        "addc.cc.u32 %5, l5, h4;\n\t"
+        "addc.cc.u32 %6, l6, h5;\n\t"
+        "addc.u32 %7, h6, 0;\n\t}"
+        : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "=r"(t[8])
+        : "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[0]));
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,p4,p5,c;\n\t.reg .u32 l0,l1,l2,l3,l4,l5,h0,h1,h2,h3,h4,h5;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %7, %13, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %8, %13, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %9, %13, c;\n\t"
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 p3, %10, %13, c;\n\t"
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 p4, %11, %13, c;\n\t"
+        "mov.b64 c, {%5, 0};\n\tmad.wide.u32 p5, %12, %13, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b64 {l1,h1}, p1;\n\t"
+        "mov.b64 {l2,h2}, p2;\n\t"
+        "mov.b64 {l3,h3}, p3;\n\t"
+        "mov.b64 {l4,h4}, p4;\n\t"
+        "mov.b64 {l5,h5}, p5;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.cc.u32 %2, l2, h1;\n\t"
+        "addc.cc.u32 %3, l3, h2;\n\t"
+        "addc.cc.u32 %4, l4, h3;\n\t"
+        "addc.cc.u32 %5, l5, h4;\n\t"
+        "addc.u32 %6, h5, 0;\n\t}"
+        : "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "=r"(t[9])
+        : "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[1]));
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,p4,c;\n\t.reg .u32 l0,l1,l2,l3,l4,h0,h1,h2,h3,h4;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %6, %11, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %7, %11, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %8, %11, c;\n\t"
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 p3, %9, %11, c;\n\t"
+        "mov.b64 c, {%4, 0};\n\tmad.wide.u32 p4, %10, %11, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b64 {l1,h1}, p1;\n\t"
+        "mov.b64 {l2,h2}, p2;\n\t"
+        "mov.b64 {l3,h3}, p3;\n\t"
+        "mov.b64 {l4,h4}, p4;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.cc.u32 %2, l2, h1;\n\t"
+        "addc.cc.u32 %3, l3, h2;\n\t"
+        "addc.cc.u32 %4, l4, h3;\n\t"
+        "addc.u32 %5, h4, 0;\n\t}"
+        : "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "=r"(t[10])
+        : "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[2]));
+    asm("{\n\t.reg .u64 p0,p1,p2,p3,c;\n\t.reg .u32 l0,l1,l2,l3,h0,h1,h2,h3;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %5, %9, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %6, %9, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %7, %9, c;\n\t"
+        "mov.b64 c, {%3, 0};\n\tmad.wide.u32 p3, %8, %9, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b64 {l1,h1}, p1;\n\t"
+        "mov.b64 {l2,h2}, p2;\n\t"
+        "mov.b64 {l3,h3}, p3;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.cc.u32 %2, l2, h1;\n\t"
+        "addc.cc.u32 %3, l3, h2;\n\t"
+        "addc.u32 %4, h3, 0;\n\t}"
+        : "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "=r"(t[11])
+        : "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[3]));
+    asm("{\n\t.reg .u64 p0,p1,p2,c;\n\t.reg .u32 l0,l1,l2,h0,h1,h2;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %4, %7, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %5, %7, c;\n\t"
+        "mov.b64 c, {%2, 0};\n\tmad.wide.u32 p2, %6, %7, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b64 {l1,h1}, p1;\n\t"
+        "mov.b64 {l2,h2}, p2;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.cc.u32 %2, l2, h1;\n\t"
+        "addc.u32 %3, h2, 0;\n\t}"
+        : "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "=r"(t[12])
+        : "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[4]));
+    asm("{\n\t.reg .u64 p0,p1,c;\n\t.reg .u32 l0,l1,h0,h1;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %3, %5, c;\n\t"
+        "mov.b64 c, {%1, 0};\n\tmad.wide.u32 p1, %4, %5, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b64 {l1,h1}, p1;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "add.cc.u32 %1, l1, h0;\n\t"
+        "addc.u32 %2, h1, 0;\n\t}"
+        : "+r"(t[11]), "+r"(t[12]), "=r"(t[13])
+        : "r"(a[6]), "r"(a[7]), "r"(a[5]));
+    asm("{\n\t.reg .u64 p0,c;\n\t.reg .u32 l0,h0;\n\t"
+        "mov.b64 c, {%0, 0};\n\tmad.wide.u32 p0, %2, %3, c;\n\t"
+        "mov.b64 {l0,h0}, p0;\n\t"
+        "mov.b32 %0, l0;\n\t"
+        "mov.b32 %1, h0;\n\t}"
+        : "+r"(t[13]), "=r"(t[14])
+        : "r"(a[7]), "r"(a[6]));
+    // t = 2 t + sum_i a_i^2 2^(64 i)
+    asm("{\n\t.reg .u64 d0,d1,d2,d3,d4,d5,d6,d7;\n\t"
+        ".reg .u32 l0,l1,l2,l3,l4,l5,l6,l7,h0,h1,h2,h3,h4,h5,h6,h7;\n\t"
+        "add.cc.u32 %0, %0, %0;\n\taddc.cc.u32 %1, %1, %1;\n\taddc.cc.u32 %2, %2, %2;\n\t"
+        "addc.cc.u32 %3, %3, %3;\n\taddc.cc.u32 %4, %4, %4;\n\taddc.cc.u32 %5, %5, %5;\n\t"
+        "addc.cc.u32 %6, %6, %6;\n\taddc.cc.u32 %7, %7, %7;\n\taddc.cc.u32 %8, %8, %8;\n\t"
+        "addc.cc.u32 %9, %9, %9;\n\taddc.cc.u32 %10, %10, %10;\n\taddc.cc.u32 %11, %11, %11;\n\t"
+        "addc.cc.u32 %12, %12, %12;\n\taddc.cc.u32 %13, %13, %13;\n\taddc.cc.u32 %14, %14, %14;\n\t"
+        "addc.u32 %15, %15, %15;\n\t"
+        "mul.wide.u32 d0, %16, %16;\n\tmul.wide.u32 d1, %17, %17;\n\t"
+        "mul.wide.u32 d2, %18, %18;\n\tmul.wide.u32 d3, %19, %19;\n\t"
+        "mul.wide.u32 d4, %20, %20;\n\tmul.wide.u32 d5, %21, %21;\n\t"
+        "mul.wide.u32 d6, %22, %22;\n\tmul.wide.u32 d7, %23, %23;\n\t"
+        "mov.b64 {l0,h0}, d0;\n\tmov.b64 {l1,h1}, d1;\n\tmov.b64 {l2,h2}, d2;\n\tmov.b64 {l3,h3}, d3;\n\t"
+        "mov.b64 {l4,h4}, d4;\n\tmov.b64 {l5,h5}, d5;\n\tmov.b64 {l6,h6}, d6;\n\tmov.b64 {l7,h7}, d7;\n\t"
+        "add.cc.u32 %0, %0, l0;\n\taddc.cc.u32 %1, %1, h0;\n\taddc.cc.u32 %2, %2, l1;\n\t"
+        "addc.cc.u32 %3, %3, h1;\n\taddc.cc.u32 %4, %4, l2;\n\taddc.cc.u32 %5, %5, h2;\n\t"
+        "addc.cc.u32 %6, %6, l3;\n\taddc.cc.u32 %7, %7, h3;\n\taddc.cc.u32 %8, %8, l4;\n\t"
+        "addc.cc.u32 %9, %9, h4;\n\taddc.cc.u32 %10, %10, l5;\n\taddc.cc.u32 %11, %11, h5;\n\t"
+        "addc.cc.u32 %12, %12, l6;\n\taddc.cc.u32 %13, %13, h6;\n\taddc.cc.u32 %14, %14, l7;\n\t"
+        "addc.u32 %15, %15, h7;\n\t}"
+        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+          "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]));
+}
+// a -= b over 16 limbs; returns the borrow mask (0xffffffff on borrow)
+ACE_DEV uint32_t d_sub512(uint32_t (&a)[16], const uint32_t (&b)[16]) {
+    uint32_t br;
+    asm("sub.cc.u32 %0, %0, %17;\n\t"
+        "subc.cc.u32 %1, %1, %18;\n\t"
+        "subc.cc.u32 %2, %2, %19;\n\t"
+        "subc.cc.u32 %3, %3, %20;\n\t"
+        "subc.cc.u32 %4, %4, %21;\n\t"
+        "subc.cc.u32 %5, %5, %22;\n\t"
+        "subc.cc.u32 %6, %6, %23;\n\t"
+        "subc.cc.u32 %7, %7, %24;\n\t"
+        "subc.cc.u32 %8, %8, %25;\n\t"
+        "subc.cc.u32 %9, %9, %26;\n\t"
+        "subc.cc.u32 %10, %10, %27;\n\t"
+        "subc.cc.u32 %11, %11, %28;\n\t"
+        "subc.cc.u32 %12, %12, %29;\n\t"
+        "subc.cc.u32 %13, %13, %30;\n\t"
+        "subc.cc.u32 %14, %14, %31;\n\t"
+        "subc.cc.u32 %15, %15, %32;\n\t"
+        "subc.u32 %16, 0, 0;\n\t"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+          "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]),
+          "=r"(br)
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]),
+          "r"(b[9]), "r"(b[10]), "r"(b[11]), "r"(b[12]), "r"(b[13]), "r"(b[14]), "r"(b[15]));
+    return br;
+}
+// a[8..15] += m & mask (adds m 2^256 when mask is all ones)
+template <class C>
+ACE_DEV void d_add_hi_mod(uint32_t (&a)[16], uint32_t mask) {
+    asm("add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32 %7, %7, %15;\n\t"
+        : "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15])
+        : "r"(C::M0 & mask), "r"(C::M1 & mask), "r"(C::M2 & mask), "r"(C::M3 & mask), "r"(C::M4 & mask),
+          "r"(C::M5 & mask), "r"(C::M6 & mask), "r"(C::M7 & mask));
+}
+// a + b of two reduced elements as a plain 256-bit integer (< 2m < 2^255)
+ACE_DEV void d_add_raw(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    asm("add.cc.u32 %0, %8, %16;\n\t"
+        "addc.cc.u32 %1, %9, %17;\n\t"
+        "addc.cc.u32 %2, %10, %18;\n\t"
+        "addc.cc.u32 %3, %11, %19;\n\t"
+        "addc.cc.u32 %4, %12, %20;\n\t"
+        "addc.cc.u32 %5, %13, %21;\n\t"
+        "addc.cc.u32 %6, %14, %22;\n\t"
+        "addc.u32 %7, %15, %23;\n\t"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+}
+
 #endif  // __CUDA_ARCH__
 
 // ---------------------------------------------------------------------------
@@ -484,6 +886,24 @@ ACE_HD Fe<C> operator-(const Fe<C>& a, const Fe<C>& b) {
 #endif
     return r;
 }
+// Product form used by the field operators on the device: 0 lo/hi chains
+// (d_mul), 1 wide multiply-adds (d_mul_wide), 2 plain wide products with two
+// carry chains per row (d_mul_pw).  All three give identical results.
+#ifndef ACE_MUL_FORM
+#define ACE_MUL_FORM 2
+#endif
+#if defined(__CUDA_ARCH__)
+template <class C>
+ACE_DEV void d_mul_form(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+#if ACE_MUL_FORM == 0
+    d_mul<C>(r, a, b);
+#elif ACE_MUL_FORM == 2
+    d_mul_pw<C>(r, a, b);
+#else
+    d_mul_wide<C>(r, a, b);
+#endif
+}
+#endif
 #if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
 // Out-of-line Montgomery product: translation units whose kernels chain many
 // products (the MSM bucket loops) define ACE_FIELD_MUL_CALL so that all warps
@@ -492,7 +912,7 @@ ACE_HD Fe<C> operator-(const Fe<C>& a, const Fe<C>& b) {
 template <class C>
 __device__ __noinline__ Fe<C> d_mul_call(const Fe<C> a, const Fe<C> b) {
     Fe<C> r;
-    d_mul_wide<C>(r.v, a.v, b.v);
+    d_mul_form<C>(r.v, a.v, b.v);
     return r;
 }
 #endif
@@ -504,15 +924,43 @@ ACE_HD Fe<C> operator*(const Fe<C>& a, const Fe<C>& b) {
 #else
     Fe<C> r;
 #if defined(__CUDA_ARCH__)
-    d_mul_wide<C>(r.v, a.v, b.v);
+    d_mul_form<C>(r.v, a.v, b.v);
 #else
     h_mul<C>(r.v, a.v, b.v);
 #endif
     return r;
 #endif
 }
+// Squaring: on the device the 36-product square plus a separate Montgomery
+// reduction (108 limb products instead of the 136 of a general product).
+#if defined(__CUDA_ARCH__)
 template <class C>
-ACE_HD Fe<C> fe_sqr(const Fe<C>& a) { return a * a; }
+ACE_DEV void d_sqr_form(uint32_t* r, const uint32_t* a) {
+    uint32_t t[16];
+    d_sqr512(t, a);
+    d_redc512<C>(r, t);
+}
+#if defined(ACE_FIELD_MUL_CALL)
+template <class C>
+__device__ __noinline__ Fe<C> d_sqr_call(const Fe<C> a) {
+    Fe<C> r;
+    d_sqr_form<C>(r.v, a.v);
+    return r;
+}
+#endif
+#endif
+template <class C>
+ACE_HD Fe<C> fe_sqr(const Fe<C>& a) {
+#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
+    return d_sqr_call<C>(a);
+#elif defined(__CUDA_ARCH__)
+    Fe<C> r;
+    d_sqr_form<C>(r.v, a.v);
+    return r;
+#else
+    return a * a;
+#endif
+}
 template <class C>
 ACE_HD Fe<C> fe_dbl(const Fe<C>& a) { return a + a; }
 template <class C>
@@ -562,12 +1010,48 @@ struct fp2_t {
 };
 ACE_HD fp2_t operator+(const fp2_t& a, const fp2_t& b) { return {a.c0 + b.c0, a.c1 + b.c1}; }
 ACE_HD fp2_t operator-(const fp2_t& a, const fp2_t& b) { return {a.c0 - b.c0, a.c1 - b.c1}; }
-// Karatsuba: (a0 b0 - a1 b1) + ((a0 + a1)(b0 + b1) - a0 b0 - a1 b1) u
+// Karatsuba: (a0 b0 - a1 b1) + ((a0 + a1)(b0 + b1) - a0 b0 - a1 b1) u.
+// On the device the three products stay unreduced (512 bits) and only the two
+// coefficients are reduced (lazy reduction, Aranha, Karabina, Longa, Gebotys
+// and Lopez, Eurocrypt 2011): with p < 2^254 both inputs to the reduction lie
+// in [0, p 2^256) -- a0 b0 - a1 b1 after adding p 2^256 when it is negative,
+// and a0 b1 + a1 b0 < 2 p^2 -- so each needs one conditional subtraction.
+#if defined(__CUDA_ARCH__)
+ACE_DEV void d_fp2_mul(fp2_t& r, const fp2_t& a, const fp2_t& b) {
+    uint32_t t0[16], t1[16], t2[16], sa[8], sb[8];
+    d_mul512(t0, a.c0.v, b.c0.v);
+    d_mul512(t1, a.c1.v, b.c1.v);
+    d_add_raw(sa, a.c0.v, a.c1.v);
+    d_add_raw(sb, b.c0.v, b.c1.v);
+    d_mul512(t2, sa, sb);
+    d_sub512(t2, t0);
+    d_sub512(t2, t1);
+    uint32_t br = d_sub512(t0, t1);
+    d_add_hi_mod<FpCfg>(t0, br);
+    d_redc512<FpCfg>(r.c0.v, t0);
+    d_redc512<FpCfg>(r.c1.v, t2);
+}
+#if defined(ACE_FIELD_MUL_CALL)
+static __device__ __noinline__ fp2_t d_fp2_mul_call(const fp2_t a, const fp2_t b) {
+    fp2_t r;
+    d_fp2_mul(r, a, b);
+    return r;
+}
+#endif
+#endif
 ACE_HD fp2_t operator*(const fp2_t& a, const fp2_t& b) {
+#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
+    return d_fp2_mul_call(a, b);
+#elif defined(__CUDA_ARCH__)
+    fp2_t r;
+    d_fp2_mul(r, a, b);
+    return r;
+#else
     fp_t v0 = a.c0 * b.c0;
     fp_t v1 = a.c1 * b.c1;
     fp_t s = (a.c0 + a.c1) * (b.c0 + b.c1);
     return {v0 - v1, s - v0 - v1};
+#endif
 }
 ACE_HD fp2_t fe_sqr(const fp2_t& a) {
     // (a0 + a1)(a0 - a1) + 2 a0 a1 u

@@ -37,48 +37,60 @@ __device__ __forceinline__ T ld_plain(const T* p) {
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
-MsmPlan msm_plan_tabled(size_t n, int force_c) {
+// Window size c: the throughput cost n K mixed additions plus the bucket
+// reduction (2 full additions per bucket of 1.4 mixed-addition costs each, per
+// bucket set, counted twice for the single bucket set of a tabled MSM), over
+// the sizes whose top window is not a long pole.  The top window holds only
+// 254 - c (K - 1) scalar bits (c = 18: 2, c = 19: 7), so its digits fall into
+// few buckets, and one thread adds each bucket's entries in sequence; one
+// sequential addition costs about MSM_SEQ_MADD additions of the whole GPU.
+// c is skipped when a top-window bucket gets more than MSM_TOP_LOAD entries
+// and that sequence would take more than half the throughput time.
+static const double MSM_TOP_LOAD = 512.0;
+static const double MSM_SEQ_MADD = 2.0e4;
+static double msm_cost(size_t n, int c, bool tabled) {
+    const int K = (255 + c - 1) / c;
+    const double B = (double)(1u << (c - 1));
+    const double work = (double)n * K + (tabled ? 5.6 * B : 2.8 * K * B);
+    int top_bits = 254 - c * (K - 1);
+    if (top_bits < 1) top_bits = 1;
+    if (top_bits > c - 1) top_bits = c - 1;
+    const double top_load = (double)n / (double)(1u << top_bits);
+    if (top_load > MSM_TOP_LOAD && top_load * MSM_SEQ_MADD > 0.5 * work) return 1e300;
+    return work;
+}
+
+static MsmPlan plan_for(size_t n, int c, bool tabled) {
     MsmPlan p;
     p.n = n;
-    int best_c = 8;
-    double best = 1e300;
-    for (int c = 8; c <= 20; c++) {
-        int K = (255 + c - 1) / c;
-        double cost = (double)n * K * 10.0 + 2.0 * 2.0 * (double)(1u << (c - 1)) * 14.0;
-        if (cost < best) { best = cost; best_c = c; }
-    }
-    p.c = force_c > 0 ? force_c : best_c;
-    if (p.c < 6) p.c = 6;
-    if (p.c > 20) p.c = 20;
+    if (c < 6) c = 6;
+    if (c > 20) c = 20;
+    p.c = c;
     p.K = (255 + p.c - 1) / p.c;
     p.B = 1u << (p.c - 1);
     p.lambda = p.c - 1 < 5 ? p.c - 1 : 5;
     p.L = 1u << p.lambda;
     p.M = p.B / p.L;
-    p.tabled = true;
+    p.tabled = tabled;
     return p;
 }
 
-MsmPlan msm_plan(size_t n, int force_c) {
-    MsmPlan p;
-    p.n = n;
-    int best_c = 8;
+static int best_window(size_t n, bool tabled) {
+    int best_c = 20;  // top window of 14 bits: the fallback for any n
     double best = 1e300;
-    for (int c = 6; c <= 20; c++) {
-        int K = (255 + c - 1) / c;
-        double cost = (double)n * K * 10.0 + 2.0 * K * (double)(1u << (c - 1)) * 14.0;
-        if (cost < best) { best = cost; best_c = c; }
+    for (int c = tabled ? 8 : 6; c <= 20; c++) {
+        double cost = msm_cost(n, c, tabled);
+        if (cost < best) {
+            best = cost;
+            best_c = c;
+        }
     }
-    p.c = force_c > 0 ? force_c : best_c;
-    if (p.c < 6) p.c = 6;
-    if (p.c > 20) p.c = 20;
-    p.K = (255 + p.c - 1) / p.c;
-    p.B = 1u << (p.c - 1);
-    p.lambda = p.c - 1 < 5 ? p.c - 1 : 5;
-    p.L = 1u << p.lambda;
-    p.M = p.B / p.L;
-    return p;
+    return best_c;
 }
+
+MsmPlan msm_plan_tabled(size_t n, int force_c) { return plan_for(n, force_c > 0 ? force_c : best_window(n, true), true); }
+
+MsmPlan msm_plan(size_t n, int force_c) { return plan_for(n, force_c > 0 ? force_c : best_window(n, false), false); }
 
 // ---------------------------------------------------------------------------
 // scan

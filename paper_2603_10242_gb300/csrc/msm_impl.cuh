@@ -204,16 +204,19 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
         k_bases_to_mont<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_bases, n, b.conv); ::ace::note_launch();
         bases = b.conv;
     }
+    int prof_sort = prof_begin(PROF_SORT, st);
     ACE_TRY_CUDA(cudaMemsetAsync(b.offsets, 0, (keys + 1) * sizeof(uint32_t), st));
     launch_digits<false>(plan, d_scalars, b.offsets, nullptr, st);
     ACE_TRY(scan_exclusive_u32(b.offsets, keys + 1, b.scan_tmp, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(b.cursor, b.offsets, keys * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     launch_digits<true>(plan, d_scalars, b.cursor, b.entries, st);
     ACE_TRY(bucket_order(b.offsets, keys, b.size_bins, b.scan_tmp, b.order, st));
+    prof_end(prof_sort, st, nullptr, n);
     int prof = prof_begin(sizeof(F) == sizeof(fp_t) ? PROF_G1_BUCKET : PROF_G2_BUCKET, st);
     k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, b.order, keys, b.buckets); ::ace::note_launch();
     prof_end(prof, st, b.offsets + keys, 0);
     uint32_t nseg = plan.windows() * plan.M;
+    int prof_red = prof_begin(PROF_REDUCE, st);
     k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS); ::ace::note_launch();
     for (int lev = 0; (1u << lev) < plan.M; lev++) {
         uint32_t pairs = plan.windows() * (plan.M >> (lev + 1));
@@ -221,6 +224,7 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
                                                              plan.lambda); ::ace::note_launch();
     }
     k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, plan.bucket_windows(), plan.M, plan.c, d_res, d_out); ::ace::note_launch();
+    prof_end(prof_red, st, nullptr, (uint64_t)plan.windows() * plan.B);
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

@@ -64,4 +64,10 @@ int pk_build_tables(ace_pk* pk, const PkFixed& f);
 // filled by the caller), set its plan
 template <class F>
 int pk_alloc_table(ace_pk* pk, uint32_t count, MsmPlan* plan, Affine<F>** tab);
+// one whole proof on proving slot `slot` at stream priority level `prio`
+// (prove.cu)
+int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
+              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join);
+// device bytes of scratch arena `arena` of a slot proving with `pk`
+size_t prove_slot_bytes(const ace_pk* pk, int arena);
 }  // namespace ace

@@ -165,6 +165,7 @@ int ace_pk_load(ace_ctx* ctx, const char* path, ace_pk** pk_out, ace_vk* vk_out)
     }
     ace_pk* pk = new ace_pk();
     pk->ctx = ctx;
+    ctx_ref(ctx);
     uint64_t hdr[9];
     r.raw(&pk->params, sizeof pk->params);
     r.raw(hdr, sizeof hdr);

@@ -223,16 +223,22 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
     return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
 }
 
-// Full proof on proving slot `slot`: ordered after the work already on
-// `st_in`; writes the 256 proof bytes to d_proof and the R1CS status to
-// d_status (0 ok, 1 unsat), both device memory.  With join, st_in waits for
-// the proof; without, the caller joins on the slot's ev_done.  The slot's
-// main stream runs the QAP and the H MSM, its auxiliary streams the A, B1,
-// B2 and L MSMs and the fixed-base terms; proofs on other slots overlap.
-int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
+// Full proof on proving slot `slot`, on the slot's streams of priority level
+// `prio`: ordered after the work already on `st_in` and after the slot's
+// previous proof; writes the 256 proof bytes to d_proof and the R1CS status
+// to d_status (0 ok, 1 unsat), both device memory.  With join, st_in waits
+// for the proof; without, the caller joins on the slot's ev_done.  The main
+// stream runs the QAP and the H MSM, the auxiliary streams the A, B1, B2 and
+// L MSMs and the fixed-base terms; proofs on other slots overlap.
+int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
               uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join) {
+    if (prio < 0 || prio >= PRIO_LEVELS || slot < 0 || slot >= MAX_SLOTS) {
+        set_error("prove: slot %d / priority level %d out of range", slot, prio);
+        return ACE_E_ARG;
+    }
     ACE_TRY(slot_ready(ctx, slot));
     ProveSlot& sl = ctx->slots[slot];
+    SlotStreams& ss = sl.lv[prio];
     ProvePlans pl = prove_plans(pk);
     for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, slot, k, pl.slot_bytes[k]));
     Arena& a0 = sl.ar[0];
@@ -250,33 +256,41 @@ int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const f
     // r s mod r on the host
     fr_t rs = fe_from_mont(fe_to_mont(r) * fe_to_mont(s));
 
-    // main waits for the caller's inputs; the auxiliary streams start after
-    // main's previous proof (which joined them) and the inputs
+    // main waits for the caller's inputs and for the slot's previous proof
+    // (its arenas are reused; it joined its own auxiliary streams); the
+    // auxiliary streams start after main
     ACE_TRY_CUDA(cudaEventRecord(sl.ev_in, st_in));
-    ACE_TRY_CUDA(cudaStreamWaitEvent(sl.main, sl.ev_in, 0));
-    ACE_TRY_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), sl.main));
-    ACE_TRY_CUDA(cudaEventRecord(sl.ev_start, sl.main));
-    for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(sl.aux[k], sl.ev_start, 0));
-    ACE_TRY(gathered_msm<fp_t>(pl.A, pk->A, d_z, sl.ar[1], res1 + 1, sl.aux[0]));
-    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, sl.ar[2], res1 + 2, sl.aux[1]));
-    ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, sl.ar[3], res2, sl.aux[2]));
-    ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, sl.ar[4], res1 + 3, sl.aux[3]));
-    k_prove_fixed<<<1, 160, 0, sl.aux[4]>>>(tabs, r, s, rs, fx1, fx2); ::ace::note_launch();
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_in, 0));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_done, 0));
+    ACE_TRY_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), ss.main));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_start, ss.main));
+    for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[k], sl.ev_start, 0));
+    ACE_TRY(gathered_msm<fp_t>(pl.A, pk->A, d_z, sl.ar[1], res1 + 1, ss.aux[0]));
+    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, sl.ar[2], res1 + 2, ss.aux[1]));
+    ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, sl.ar[3], res2, ss.aux[2]));
+    ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, sl.ar[4], res1 + 3, ss.aux[3]));
+    int pf = prof_begin(PROF_ASSEMBLY, ss.aux[4]);
+    k_prove_fixed<<<1, 160, 0, ss.aux[4]>>>(tabs, r, s, rs, fx1, fx2); ::ace::note_launch();
+    prof_end(pf, ss.aux[4], nullptr, 1);
     // V = s S_A + r S_B1 once the A and B1 MSMs are done, overlapping the rest
-    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[0], sl.aux[0]));
-    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[1], sl.aux[1]));
-    ACE_TRY_CUDA(cudaStreamWaitEvent(sl.aux[4], sl.ev_aux[0], 0));
-    ACE_TRY_CUDA(cudaStreamWaitEvent(sl.aux[4], sl.ev_aux[1], 0));
-    k_prove_var<<<1, 32, 0, sl.aux[4]>>>(res1, r, s, vterm); ::ace::note_launch();
-    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, sl.main));
-    ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, sl.main));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[0], ss.aux[0]));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[1], ss.aux[1]));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[4], sl.ev_aux[0], 0));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[4], sl.ev_aux[1], 0));
+    int pv = prof_begin(PROF_ASSEMBLY, ss.aux[4]);
+    k_prove_var<<<1, 32, 0, ss.aux[4]>>>(res1, r, s, vterm); ::ace::note_launch();
+    prof_end(pv, ss.aux[4], nullptr, 1);
+    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, ss.main));
+    ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, ss.main));
     for (int k = 0; k < 5; k++) {
-        ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], sl.aux[k]));
-        ACE_TRY_CUDA(cudaStreamWaitEvent(sl.main, sl.ev_aux[k], 0));
+        ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], ss.aux[k]));
+        ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_aux[k], 0));
     }
-    k_assemble<<<1, 96, 0, sl.main>>>(pk->d_fixed, res1, res2, fx1, fx2, vterm, d_proof); ::ace::note_launch();
+    int pa = prof_begin(PROF_ASSEMBLY, ss.main);
+    k_assemble<<<1, 96, 0, ss.main>>>(pk->d_fixed, res1, res2, fx1, fx2, vterm, d_proof); ::ace::note_launch();
+    prof_end(pa, ss.main, nullptr, 1);
     ACE_TRY_CUDA(cudaGetLastError());
-    ACE_TRY_CUDA(cudaEventRecord(sl.ev_done, sl.main));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_done, ss.main));
     if (join) ACE_TRY_CUDA(cudaStreamWaitEvent(st_in, sl.ev_done, 0));
     return ACE_OK;
 }
@@ -328,7 +342,7 @@ int ace_prove_async(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace
     fr_t rr, ss;
     memcpy(rr.v, r->l, 32);
     memcpy(ss.v, s->l, 32);
-    return prove_run(ctx, 0, pk, (const fr_t*)d_z, rr, ss, (uint32_t*)d_proof_out, d_status,
+    return prove_run(ctx, 0, 0, pk, (const fr_t*)d_z, rr, ss, (uint32_t*)d_proof_out, d_status,
                      pick_stream(ctx, stream), true);
 }
 
@@ -398,7 +412,7 @@ int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_
         fr_t rr, sv;
         memcpy(rr.v, rs[i].l, 32);
         memcpy(sv.v, ss[i].l, 32);
-        ACE_TRY(prove_run(ctx, (int)(i % nslots), pks[i], (const fr_t*)d_zs[i], rr, sv, d_proofs + 64 * i,
+        ACE_TRY(prove_run(ctx, (int)(i % nslots), 0, pks[i], (const fr_t*)d_zs[i], rr, sv, d_proofs + 64 * i,
                           d_status + i, st, false));
     }
     for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));

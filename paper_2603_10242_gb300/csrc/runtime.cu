@@ -69,8 +69,18 @@ int slot_arena_ensure(ace_ctx* ctx, int s, int k, size_t bytes) { return grow(ct
 int slot_ready(ace_ctx* ctx, int s) {
     ProveSlot& sl = ctx->slots[s];
     if (sl.ready) return ACE_OK;
-    ACE_TRY_CUDA(cudaStreamCreateWithFlags(&sl.main, cudaStreamNonBlocking));
-    for (auto& a : sl.aux) ACE_TRY_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    ACE_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    // greatest is the numerically lowest (highest) priority.  Within a level
+    // the main stream (QAP, then the H MSM: the longest chain of a proof) is
+    // one step above the auxiliary streams.
+    for (int l = 0; l < PRIO_LEVELS; l++) {
+        int pm = greatest + 2 * l, pa = pm + 1;
+        if (pm > least) pm = least;
+        if (pa > least) pa = least;
+        ACE_TRY_CUDA(cudaStreamCreateWithPriority(&sl.lv[l].main, cudaStreamNonBlocking, pm));
+        for (auto& a : sl.lv[l].aux) ACE_TRY_CUDA(cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, pa));
+    }
     ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming));
     ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_start, cudaEventDisableTiming));
     ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));

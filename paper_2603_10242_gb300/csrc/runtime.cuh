@@ -66,13 +66,21 @@ struct NttPlan;  // twiddle tables for one size (ntt.cu)
 
 // A proving slot: the streams, events and scratch one proof needs.  Proofs on
 // different slots run concurrently; proofs on the same slot run in order.
+// Each slot has its streams at PRIO_LEVELS CUDA stream priorities (level 0
+// the highest; in a level the main stream above the auxiliary ones): a proof
+// runs on one level's streams, so that a server can let the proofs admitted
+// first keep the SMs while later ones fill the gaps.
 static const int PROVE_ARENAS = 5;  // QAP + H MSM, A, B1, B2, L
 static const int MAX_SLOTS = 8;
+static const int PRIO_LEVELS = 3;
+struct SlotStreams {
+    cudaStream_t main = nullptr;
+    cudaStream_t aux[5] = {};
+};
 struct ProveSlot {
     bool ready = false;
     Arena ar[PROVE_ARENAS];
-    cudaStream_t main = nullptr;
-    cudaStream_t aux[5] = {};
+    SlotStreams lv[PRIO_LEVELS];
     cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_aux[5] = {};
 };
@@ -95,6 +103,10 @@ struct ace_ctx {
     std::map<int, ace::NttPlan*> ntt_plans;
     void* g1_fixed_tab = nullptr;  // fixed-base tables for the generators (setup.cu)
     void* g2_fixed_tab = nullptr;
+    // proving keys and servers that use this context; ace_ctx_destroy with
+    // users left only marks it, and the last user's release frees it
+    int users = 0;
+    bool closing = false;
 };
 
 namespace ace {
@@ -103,6 +115,9 @@ void dev_free(ace_ctx* ctx, void* p, size_t bytes);
 // make arena `slot` hold at least `bytes` (synchronises the device if it grows)
 int arena_ensure(ace_ctx* ctx, int slot, size_t bytes);
 inline cudaStream_t pick_stream(ace_ctx* ctx, ace_stream s) { return s ? (cudaStream_t)s : ctx->stream; }
+// users of a context (proving keys, servers): see ace_ctx::users
+void ctx_ref(ace_ctx* ctx);
+void ctx_unref(ace_ctx* ctx);
 // create the streams and events of proving slot s (once)
 int slot_ready(ace_ctx* ctx, int s);
 // make arena k of slot s hold at least `bytes` (synchronises the device if it grows)
@@ -115,7 +130,19 @@ int slot_arena_ensure(ace_ctx* ctx, int s, int k, size_t bytes);
 // when only the device knows it).
 void note_launch();
 uint64_t launch_count();
-enum ProfKind { PROF_G1_BUCKET = 0, PROF_G2_BUCKET = 1, PROF_NTT = 2, PROF_SPMV = 3, PROF_KINDS = 4 };
+// kinds: bucket accumulation (G1, G2), NTT passes, sparse products, MSM
+// digit sort (digits, scans, scatter, bucket order), MSM bucket reduction
+// (segments, tree, final), proof-assembly scalar multiplications
+enum ProfKind {
+    PROF_G1_BUCKET = 0,
+    PROF_G2_BUCKET = 1,
+    PROF_NTT = 2,
+    PROF_SPMV = 3,
+    PROF_SORT = 4,
+    PROF_REDUCE = 5,
+    PROF_ASSEMBLY = 6,
+    PROF_KINDS = 7
+};
 bool prof_on();
 int prof_begin(int kind, cudaStream_t st);  // returns a record slot, or -1 when off / full
 // device_units (optional): a u32 on the device copied into the record;

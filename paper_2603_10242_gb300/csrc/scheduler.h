@@ -23,6 +23,7 @@ struct SchedJob {
     double deadline = 0;    // latest start time (arrival + max queue wait); <= 0: none
     size_t mem = 0;         // device bytes the job needs while it runs
     int slot = -1;
+    int prio = 0;           // jobs already running when this one started
     double start = -1, finish = -1;
     int status = 0;         // 0 pending/ok, 1 unsat, -6 timeout, other < 0 error
     bool done = false;
@@ -78,6 +79,8 @@ class Scheduler {
             }
             if (used_ + j->mem > budget_) break;  // wait for memory
             j->slot = slot;
+            j->prio = 0;
+            for (auto* b : busy_) j->prio += b != nullptr;
             j->start = clock_.now();
             int rc = ex_.start(*j, slot);
             queue_.pop_front();

@@ -16,11 +16,6 @@
 #include "pk.h"
 #include "scheduler.h"
 
-namespace ace {
-int prove_run(ace_ctx* ctx, int slot, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
-              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join);
-size_t prove_slot_bytes(const ace_pk* pk, int arena);
-}  // namespace ace
 
 using namespace ace;
 
@@ -58,14 +53,20 @@ struct CudaExecutor {
         ServerJob& j = static_cast<ServerJob&>(sj);
         SlotIo& s = (*io)[slot];
         ProveSlot& sl = ctx->slots[slot];
+        // jobs admitted while others run get lower stream priorities, so the
+        // device keeps serving jobs roughly in admission order
+        int prio = j.prio < PRIO_LEVELS ? j.prio : PRIO_LEVELS - 1;
+        cudaStream_t m = sl.lv[prio].main;
         size_t zb = (size_t)j.pk->m * sizeof(fr_t);
         if (zb > s.z_cap) return ACE_E_OOM;
-        if (cudaMemcpyAsync(s.d_z, j.z, zb, cudaMemcpyHostToDevice, sl.main) != cudaSuccess) return ACE_E_CUDA;
-        int rc = prove_run(ctx, slot, j.pk, s.d_z, j.r, j.s, s.d_proof, s.d_status, sl.main, false);
+        // the slot's previous job may still read d_z
+        if (cudaStreamWaitEvent(m, sl.ev_done, 0) != cudaSuccess) return ACE_E_CUDA;
+        if (cudaMemcpyAsync(s.d_z, j.z, zb, cudaMemcpyHostToDevice, m) != cudaSuccess) return ACE_E_CUDA;
+        int rc = prove_run(ctx, slot, prio, j.pk, s.d_z, j.r, j.s, s.d_proof, s.d_status, m, false);
         if (rc != ACE_OK) return rc;
-        if (cudaMemcpyAsync(s.h_proof, s.d_proof, 256, cudaMemcpyDeviceToHost, sl.main) != cudaSuccess ||
-            cudaMemcpyAsync(s.h_status, s.d_status, 4, cudaMemcpyDeviceToHost, sl.main) != cudaSuccess ||
-            cudaEventRecord(s.done, sl.main) != cudaSuccess)
+        if (cudaMemcpyAsync(s.h_proof, s.d_proof, 256, cudaMemcpyDeviceToHost, m) != cudaSuccess ||
+            cudaMemcpyAsync(s.h_status, s.d_status, 4, cudaMemcpyDeviceToHost, m) != cudaSuccess ||
+            cudaEventRecord(s.done, m) != cudaSuccess)
             return ACE_E_CUDA;
         return ACE_OK;
     }
@@ -137,6 +138,7 @@ int ace_server_create(ace_ctx* ctx, const ace_pk* max_pk, int slots, size_t hbm_
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     ace_server* sv = new ace_server();
     sv->ctx = ctx;
+    ctx_ref(ctx);
     sv->slots = slots;
     sv->max_wait = max_queue_wait_s;
     sv->io.resize(slots);
@@ -154,6 +156,7 @@ int ace_server_create(ace_ctx* ctx, const ace_pk* max_pk, int slots, size_t hbm_
             if (s.done) cudaEventDestroy(s.done);
         }
         delete sv;
+        ctx_unref(ctx);
         return rc;
     };
     for (int q = 0; q < slots; q++) {
@@ -302,7 +305,9 @@ int ace_server_destroy(ace_server* sv) {
         cudaEventDestroy(s.done);
     }
     delete sv->sched;
+    ace_ctx* ctx = sv->ctx;
     delete sv;
+    ctx_unref(ctx);
     return ACE_OK;
 }
 

@@ -155,13 +155,15 @@ using namespace ace;
 
 static void pk_release(ace_pk* pk) {
     if (!pk) return;
-    if (pk->ctx) {
-        cudaSetDevice(pk->ctx->device);
+    ace_ctx* ctx = pk->ctx;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
         cudaDeviceSynchronize();
-        for (auto& a : pk->allocs) dev_free(pk->ctx, a.first, a.second);
+        for (auto& a : pk->allocs) dev_free(ctx, a.first, a.second);
     }
     delete pk->circ;
     delete pk;
+    if (ctx) ctx_unref(ctx);
 }
 
 extern "C" {
@@ -179,6 +181,7 @@ int ace_setup_toy(ace_ctx* ctx, const ace_circuit* c, uint64_t toxic_seed, ace_p
     const int log_n = (int)c->p.log_n;
     ace_pk* pk = new ace_pk();
     pk->ctx = ctx;
+    ctx_ref(ctx);
     pk->params = c->p;
     pk->N = N;
     pk->m = m;

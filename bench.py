@@ -63,6 +63,30 @@ def _dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (x itself without a process
+    group): every rank's timed region is bracketed by barriers, and the job
+    takes as long as its slowest rank."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world_size: int, seconds: float) -> float:
+    """Throughput of the whole job: the units all ranks processed (each rank
+    proves its own, no data is exchanged) over the slowest rank's time."""
+    return world_size * units_per_rank / seconds
+
+
+# compacted query sizes of the block circuit (m_A, m_B, m_L: witness values
+# whose A / B / L setup scalar is non-zero); run_ours checks them against the key
+BLOCK_SHAPE = {"N": 1 << 20, "m": 1765375, "m_A": 1748994, "m_B": 712705, "m_L": 1765373}
+
+
 def _clock_sampler(path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -164,8 +188,7 @@ def run_reference(args):
     ws, rank, _ = _dist_env()
     if rank != 0:
         return
-    shape = {"N": 1 << 20, "m_A": 1765375, "m_B": 1060865, "m_L": 1765373}
-    s = CpuSample(shape)
+    s = CpuSample(BLOCK_SHAPE)
     for _ in range(args.warmup):
         s.measure()
     runs = [s.measure() for _ in range(args.steps)]
@@ -204,6 +227,7 @@ def run_ours(args):
     pk = ace.ProvingKey(ctx, circ, toxic_seed=SEED)
     m, N = circ.m, circ.N
     shape = {"N": N, "m": m, "m_A": pk.info[7], "m_B": pk.info[8], "m_L": pk.info[9]}
+    assert shape == BLOCK_SHAPE, f"block circuit shape changed: {shape}"
     zb = np.frombuffer(z, dtype=np.uint8)
     bool_frac = float(np.mean((zb.reshape(-1, 32)[:, 1:] == 0).all(axis=1) & (zb.reshape(-1, 32)[:, 0] <= 1)))
     stream = torch.cuda.current_stream(device)
@@ -225,6 +249,9 @@ def run_ours(args):
 
     for i in range(args.warmup):
         ctx.prove_async(pk, dz, rs[i][0], rs[i][1], proofs[256 * i:], status[i:])
+    # proving slots for the batch: the autotuner times 1..4 slots (untimed)
+    slot_ms = ctx.autotune_batch_slots(pk, dz, 6, 4)
+    batch_slots = 1 + min(range(len(slot_ms)), key=lambda q: slot_ms[q])
     batch(min(4, args.steps), 0)
     torch.cuda.synchronize()
 
@@ -242,8 +269,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = ace.launch_count() - launches0
     total_ms = eb0.elapsed_time(eb1)
-    prof = {k: ace.profile_read(k) for k in (ace.PROF_G1_BUCKET, ace.PROF_G2_BUCKET, ace.PROF_NTT,
-                                             ace.PROF_SPMV)}
+    prof = {k: ace.profile_read(k) for k in range(7)}
     ace.profile_enable(False)
     if sampler:
         sampler.terminate()
@@ -273,11 +299,8 @@ def run_ours(args):
     for i in (0, args.steps - 1):
         assert bytes(allp[args.warmup + i]) == bproofs[i], "batched and plain proofs differ"
 
-    if dist:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(total_ms, dist, device)
+    value = whole_job_rate(args.steps, ws, total_ms / 1000.0)
     plain_value = args.steps / (plain_ms / 1000.0)
 
     # ---- e2e: every witness copied from pinned host memory, proofs read back ----
@@ -309,11 +332,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     assert e2e_proofs[0] == bproofs[0]
-    if dist:
-        t = torch.tensor([e2e_s], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * m,
+    e2e_s = max_over_ranks(e2e_s, dist, device)
+    e2e = {"value": whole_job_rate(args.steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 32 * m,
            "d2h_bytes_per_step": 256 + 4}
 
     # ---- G1 MSM points/s at 2^20 (second half of the metric) ----
@@ -322,6 +342,7 @@ def run_ours(args):
     bases = torch.empty(64 * n, dtype=torch.uint8, device=device)
     ctx.g1_fixed_base(torch.from_numpy(kb.view(np.uint8).reshape(-1)).to(device), n, bases, ace.FORM_MONT)
     msm = {}
+    iso = None
     for dist_name in ("uniform", "sparse"):
         sc = torch.from_numpy(inputs.sample_scalars(20, n, dist_name).view(np.uint8).reshape(-1)).to(device)
         out = torch.empty(64, dtype=torch.uint8, device=device)
@@ -330,12 +351,17 @@ def run_ours(args):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 10
         torch.cuda.synchronize()
+        if dist_name == "uniform":
+            ace.profile_enable(True)
         a.record(stream)
         for _ in range(reps):
             ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT)
         b.record(stream)
         torch.cuda.synchronize()
         msm[dist_name] = n * reps / (a.elapsed_time(b) / 1000.0)
+        if dist_name == "uniform":
+            iso = ace.profile_read(ace.PROF_G1_BUCKET)
+            ace.profile_enable(False)
 
     # ---- roofline of the dominant kernel (G1 bucket accumulation) ----
     ms, nl, units = prof[ace.PROF_G1_BUCKET]
@@ -348,18 +374,42 @@ def run_ours(args):
     traffic = None
     if G1_BUCKET_DRAM_BYTES_PER_MADD is not None and nl:
         traffic = G1_BUCKET_DRAM_BYTES_PER_MADD * units / nl
+    # the same kernel with the GPU to itself (the 2^20 G1 MSM loop above)
+    iso_ms, iso_nl, iso_units = iso
+    isolated = {"achieved": iso_units * IMAD_PER_G1_MADD / (iso_ms / 1000.0) / 1e12 if iso_ms > 0 else None,
+                "units_per_launch": iso_units / iso_nl if iso_nl else None, "launches": iso_nl,
+                "where": "G1 MSM of 2^20 points, uniform scalars, alone on the GPU"}
+    isolated["frac"] = isolated["achieved"] / peak if isolated["achieved"] else None
+    # every kernel of the proof: algorithmic multiply-adds per proof / step time
+    per_proof = {
+        "g1_bucket": prof[ace.PROF_G1_BUCKET][2] / args.steps * IMAD_PER_G1_MADD,
+        "g2_bucket": prof[ace.PROF_G2_BUCKET][2] / args.steps * IMAD_PER_G2_MADD,
+        "ntt": prof[ace.PROF_NTT][2] / args.steps * IMAD_PER_FP_MUL,
+        "spmv": prof[ace.PROF_SPMV][2] / args.steps * IMAD_PER_FP_MUL,
+    }
+    step_imad = sum(per_proof.values())
+    step_alu = {"achieved": step_imad / (total_ms / args.steps / 1000.0) / 1e12, "imad_per_proof": step_imad,
+                "counted": "bucket additions (G1, G2), NTT butterflies, sparse-product non-zeros"}
+    step_alu["frac"] = step_alu["achieved"] / peak
     roofline = {"bound": "alu", "kernel": "k_bucket_acc<G1>", "achieved": achieved, "peak": peak,
                 "unit": "T IMAD/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "algorithmic_per_unit": f"{IMAD_PER_G1_MADD} IMAD per mixed addition (10 Fp mul x 272)",
                 "units_per_launch": units / nl if nl else None, "launches": nl, "ms_union": ms,
                 "peak_source": "152 SMs x 64 IMAD/clk/SM x 2070 MHz (nominal unit counts and max clock)",
-                "peak_measured_T_per_s": measured_peak}
+                "peak_measured_T_per_s": measured_peak,
+                "measured": "union of the kernel's launch intervals inside the timed proofs (other kernels "
+                            "share the SMs meanwhile)",
+                "isolated": isolated, "whole_step": step_alu}
     stages = {
         "g1_bucket_ms_per_proof": ms / args.steps,
         "g2_bucket_ms_per_proof": prof[ace.PROF_G2_BUCKET][0] / args.steps,
         "ntt_ms_per_proof": prof[ace.PROF_NTT][0] / args.steps,
         "spmv_ms_per_proof": prof[ace.PROF_SPMV][0] / args.steps,
         "ntt_butterflies_per_proof": prof[ace.PROF_NTT][2] / args.steps,
+        "msm_sort_ms_per_proof": prof[ace.PROF_SORT][0] / args.steps,
+        "msm_reduce_ms_per_proof": prof[ace.PROF_REDUCE][0] / args.steps,
+        "assembly_ms_per_proof": prof[ace.PROF_ASSEMBLY][0] / args.steps,
+        "note": "union of each kind's launch intervals per proof; kinds overlap one another",
     }
     step_sorted = sorted(step_ms)
     p50 = statistics.median(step_sorted)
@@ -379,7 +429,8 @@ def run_ours(args):
             "latency_ms": {"p50": p50, "p99": p99, "budget_ms": 600.0,
                            "path": "one proof per call, back to back"},
             "plain_proofs_per_s": plain_value,
-            "batch_slots": 2,
+            "batch_slots": batch_slots,
+            "batch_slot_ms": slot_ms,
             "msm_g1_2p20_points_per_s": msm,
             "stages": stages,
             "verified": bool(verified),
@@ -586,7 +637,9 @@ def run_case(args):
     """Small fixed launches for profiler captures (not a bench line):
     msm_g1 -- one G1 MSM of 2^20 points (uniform scalars);
     ntt -- one 2^20 forward transform of three arrays (QAP batch shape);
-    prove16 -- one proof of the 2^16 instance of the block circuit family."""
+    prove16 -- one proof of the 2^16 instance of the block circuit family;
+    prove20 -- `steps` proofs of the 2^20 block circuit in one batch (prints
+    the launches issued before the batch, for a profiler's skip count)."""
     import numpy as np
     import torch
 
@@ -609,6 +662,20 @@ def run_case(args):
         d = torch.from_numpy(inputs.sample_fr(1, 7, 3 * n).view(np.uint8).reshape(-1)).cuda()
         for _ in range(args.steps):
             ctx.ntt_mont(d, 20, 3, True, False)
+    elif args.case == "prove20":
+        c = ace.Circuit(seed=SEED, **CIRCUIT)
+        z = c.witness(SEED)
+        pk = ace.ProvingKey(ctx, c, toxic_seed=SEED)
+        dz = torch.frombuffer(bytearray(z), dtype=torch.uint8).cuda()
+        r, s_ = ace.rs_from_seed(1)
+        torch.cuda.synchronize()
+        before = ace.launch_count()
+        proofs, st = ctx.prove_batch([pk] * args.steps, [dz] * args.steps, r * args.steps, s_ * args.steps)
+        assert st == [0] * args.steps and pk.verify(z[32:64], proofs[0]) == 1
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "steps": args.steps, "launches_before_batch": before,
+                          "launches": ace.launch_count()}))
+        return
     else:
         c = ace.Circuit(16, 1 << 16, 256, 256, 172, seed=SEED)
         z = c.witness(SEED)
@@ -627,7 +694,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--workload", choices=["block2p20", "batch64", "serve"], default="block2p20",
                     help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
-    ap.add_argument("--case", choices=["msm_g1", "ntt", "prove16"], default=None,
+    ap.add_argument("--case", choices=["msm_g1", "ntt", "prove16", "prove20"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

@@ -327,6 +327,19 @@ int ace_debug_scheduler_sim(int slots, size_t budget, size_t n, const double* ar
                             const size_t* mem, double max_wait, double* start_out, double* finish_out,
                             int32_t* status_out, uint64_t* peaks);
 
+/* Many proofs of ONE key in one pass: the per-transaction proofs of a block
+ * (every transaction proves the same circuit; Section 3.3, Algorithm 3
+ * ParallelMap over the block's transactions).  Every stage runs once for
+ * all k proofs (one sparse-product launch, NTT launches over 3k arrays, MSMs
+ * whose k bucket sets share the key's point tables), in chunks that keep the
+ * scratch within 24 GB.  d_z: k witnesses of pk's m values each, contiguous
+ * (k x m ace_fr, canonical, 16-byte aligned, device); rs, ss: k canonical
+ * values each (host); proofs (host, k x 256 bytes) and status (host, k: 0 ok,
+ * 1 the witness does not satisfy the R1CS).  Synchronous; each proof equals
+ * the one ace_prove makes with the same (z, r, s). */
+int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, const ace_fr* rs, const ace_fr* ss,
+                   uint8_t* proofs, int32_t* status);
+
 /* ---- autotuning ------------------------------------------------------------ */
 
 /* Measure candidate MSM window sizes c for the generic G1 MSM at

@@ -77,6 +77,7 @@ def lib():
             "ace_pk_save": (i32, [vp, cp]),
             "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
             "ace_debug_pairing": (i32, [cp, cp, cp]),
+            "ace_prove_many": (i32, [vp, vp, sz, vp, cp, cp, vp, vp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
             "ace_autotune_batch_slots": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -191,6 +192,13 @@ class Context:
     def ntt_mont(self, data, log_n: int, count: int, dif: bool, inverse: bool, stream=None):
         check(lib().ace_ntt_mont(self.h, _ptr(data), log_n, count, 1 if dif else 0, 1 if inverse else 0,
                                  _stream(stream)))
+
+    def prove_many(self, pk: "ProvingKey", d_z, k: int, rs: bytes, ss: bytes):
+        """k proofs of one key in one pass; d_z holds the k witnesses back to back."""
+        proofs = ctypes.create_string_buffer(256 * k)
+        status = (ctypes.c_int32 * k)()
+        check(lib().ace_prove_many(self.h, pk.h, k, _ptr(d_z), rs, ss, proofs, status))
+        return [proofs.raw[256 * i:256 * i + 256] for i in range(k)], list(status)
 
     # ---- autotuning ----
     def autotune_msm(self, log_min: int, log_max: int):

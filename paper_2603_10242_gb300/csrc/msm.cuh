@@ -34,9 +34,16 @@ struct MsmPlan {
     // tab[w n + i] = 2^(c w) P_i, so all K digit windows share one set of
     // buckets (no Horner over windows)
     bool tabled = false;
+    // batch > 1: that many MSMs over the same n points, each with its own n
+    // scalars (scalars and results laid out one MSM after another) and its
+    // own bucket sets; every reduction step runs over all of them at once
+    uint32_t batch = 1;
     uint32_t bucket_windows() const { return tabled ? 1u : (uint32_t)K; }
     uint32_t windows() const { return bucket_windows() + 1; }  // + ones window
-    uint32_t keys() const { return windows() * B; }
+    uint32_t keys_per() const { return windows() * B; }         // keys of one MSM
+    uint32_t keys() const { return batch * keys_per(); }
+    uint32_t all_windows() const { return batch * windows(); }
+    size_t scalars() const { return (size_t)batch * n; }
 };
 
 // c chosen by the cost model  n K madd + 2 K 2^(c-1) add  (force_c > 0 overrides)
@@ -64,10 +71,11 @@ struct MsmBufs {
     bool carve(Alloc& a, const MsmPlan& p, bool need_conv);
 };
 
-// Run one MSM.  d_bases: n affine points; base_mont says whether they are in
-// Montgomery form.  Writes the XYZZ result (Montgomery) to d_res if non-null
-// and the canonical affine result to d_out if non-null.  Scratch comes from
-// `ar` (size it with msm_scratch_bytes).  Asynchronous on st.
+// Run one MSM (plan.batch of them over the same bases).  d_bases: n affine
+// points; base_mont says whether they are in Montgomery form.  Writes the
+// XYZZ results (Montgomery, plan.batch of them) to d_res if non-null and the
+// canonical affine results to d_out if non-null.  Scratch comes from `ar`
+// (size it with msm_scratch_bytes).  Asynchronous on st.
 template <class F>
 int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
             Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st);

@@ -208,17 +208,23 @@ __device__ __forceinline__ int scalar_kind(const uint32_t s[8]) {
 // SCATTER = false: histogram into cnt; true: place entries using cnt as cursor.
 // TAB: digits of all windows go to bucket window 0 with entry w n + i
 // (precomputed window tables); otherwise window w's buckets hold entry i.
+// A batch of MSMs over the same n points: scalar t belongs to MSM t / n and
+// multiplies point t mod n; each MSM has its own keys_per keys.
 template <int C, bool SCATTER, bool TAB>
-__global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t* cnt, uint32_t* entries) {
+__global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t total, size_t n, uint32_t keys_per,
+                             uint32_t* cnt, uint32_t* entries) {
     constexpr int K = (255 + C - 1) / C;
     constexpr uint32_t B = 1u << (C - 1);
     constexpr uint32_t BW = TAB ? 1u : (uint32_t)K;
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
     uint32_t s[8];
-    ld_scalar(sc, i, s);
+    ld_scalar(sc, t, s);
     int kind = scalar_kind(s);
     if (kind == 0) return;
+    const size_t q = total == n ? 0 : t / n;  // which MSM of the batch
+    const size_t i = t - q * n;               // which point
+    cnt += q * keys_per;
     if (kind == 1) {
         uint32_t key = BW * B + (uint32_t)(i & (B - 1));
         if (SCATTER) {
@@ -258,12 +264,13 @@ __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t n, uint32_t
 
 template <bool SCATTER>
 void launch_digits(const MsmPlan& plan, const uint32_t* sc, uint32_t* cnt, uint32_t* entries, cudaStream_t st) {
-    size_t n = plan.n;
-    unsigned grid = (unsigned)((n + 255) / 256);
+    const size_t total = plan.scalars(), n = plan.n;
+    const uint32_t kp = plan.keys_per();
+    unsigned grid = (unsigned)((total + 255) / 256);
     switch (plan.c * 2 + (plan.tabled ? 1 : 0)) {
-#define ACE_DIGITS_CASE(CC)                                                                          \
-    case 2 * CC: k_msm_digits<CC, SCATTER, false><<<grid, 256, 0, st>>>(sc, n, cnt, entries); break; \
-    case 2 * CC + 1: k_msm_digits<CC, SCATTER, true><<<grid, 256, 0, st>>>(sc, n, cnt, entries); break;
+#define ACE_DIGITS_CASE(CC)                                                                                        \
+    case 2 * CC: k_msm_digits<CC, SCATTER, false><<<grid, 256, 0, st>>>(sc, total, n, kp, cnt, entries); break; \
+    case 2 * CC + 1: k_msm_digits<CC, SCATTER, true><<<grid, 256, 0, st>>>(sc, total, n, kp, cnt, entries); break;
         ACE_DIGITS_CASE(6) ACE_DIGITS_CASE(7) ACE_DIGITS_CASE(8) ACE_DIGITS_CASE(9) ACE_DIGITS_CASE(10)
         ACE_DIGITS_CASE(11) ACE_DIGITS_CASE(12) ACE_DIGITS_CASE(13) ACE_DIGITS_CASE(14) ACE_DIGITS_CASE(15)
         ACE_DIGITS_CASE(16) ACE_DIGITS_CASE(17) ACE_DIGITS_CASE(18) ACE_DIGITS_CASE(19) ACE_DIGITS_CASE(20)

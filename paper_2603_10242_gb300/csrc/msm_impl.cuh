@@ -42,12 +42,12 @@ bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
     offsets = (uint32_t*)a.take((keys + 1) * 4);
     cursor = (uint32_t*)a.take(keys * 4);
     scan_tmp = (uint32_t*)a.take(scan_tmp_words(keys + 1) * 4);
-    entries = (uint32_t*)a.take(p.n * (size_t)p.K * 4 + 4);
+    entries = (uint32_t*)a.take(p.scalars() * (size_t)p.K * 4 + 4);
     order = (uint32_t*)a.take(keys * 4);
     size_bins = (uint32_t*)a.take((SIZE_BINS + 1) * 4);
     buckets = (Xyzz<F>*)a.take(keys * sizeof(Xyzz<F>));
-    segW = (Xyzz<F>*)a.take((size_t)p.windows() * p.M * sizeof(Xyzz<F>));
-    segS = (Xyzz<F>*)a.take((size_t)p.windows() * p.M * sizeof(Xyzz<F>));
+    segW = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
+    segS = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
     conv = need_conv ? (Affine<F>*)a.take(p.n * sizeof(Affine<F>)) : nullptr;
     return offsets && cursor && scan_tmp && entries && order && size_bins && buckets && segW && segS &&
            (!need_conv || conv);
@@ -125,11 +125,17 @@ __global__ void __launch_bounds__(128) k_tree_level(Xyzz<F>* W, Xyzz<F>* S, uint
     st_vec(S + l, xyzz_add(ld_plain(S + l), sr));
 }
 
-// Horner over the K digit windows, plus the ones-window total
+// Horner over the K digit windows, plus the ones-window total; one thread
+// per MSM of a batch (its windows follow the previous MSM's: K + 1 of them)
 template <class F>
-__global__ void k_msm_final(const Xyzz<F>* W, const Xyzz<F>* S, uint32_t K, uint32_t M, int c, Xyzz<F>* res,
-                            Affine<F>* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void k_msm_final(const Xyzz<F>* W, const Xyzz<F>* S, uint32_t K, uint32_t M, int c, uint32_t batch,
+                            Xyzz<F>* res, Affine<F>* out) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= batch) return;
+    W += (size_t)q * (K + 1) * M;
+    S += (size_t)q * (K + 1) * M;
+    if (res) res += q;
+    if (out) out += q;
     Xyzz<F> acc = ld_plain(W + (size_t)(K - 1) * M);
     for (int w = (int)K - 2; w >= 0; w--) {
         for (int k = 0; k < c; k++) acc = xyzz_dbl(acc);
@@ -144,12 +150,13 @@ __global__ void k_msm_final(const Xyzz<F>* W, const Xyzz<F>* S, uint32_t K, uint
 }
 
 template <class F>
-__global__ void k_msm_empty(Xyzz<F>* res, Affine<F>* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (res) *res = xyzz_inf<F>();
+__global__ void k_msm_empty(uint32_t batch, Xyzz<F>* res, Affine<F>* out) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= batch) return;
+    if (res) res[q] = xyzz_inf<F>();
     if (out) {
-        out->x = field_zero<F>();
-        out->y = field_zero<F>();
+        out[q].x = field_zero<F>();
+        out[q].y = field_zero<F>();
     }
 }
 
@@ -188,7 +195,7 @@ template <class F>
 int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
             Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st) {
     if (plan.n == 0) {
-        k_msm_empty<F><<<1, 1, 0, st>>>(d_res, d_out); ::ace::note_launch();
+        k_msm_empty<F><<<(plan.batch + 31) / 32, 32, 0, st>>>(plan.batch, d_res, d_out); ::ace::note_launch();
         ACE_TRY_CUDA(cudaGetLastError());
         return ACE_OK;
     }
@@ -197,11 +204,11 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
         set_error("msm: scratch arena too small");
         return ACE_E_OOM;
     }
-    const size_t n = plan.n;
+    const size_t n = plan.scalars();
     const uint32_t keys = plan.keys();
     const Affine<F>* bases = d_bases;
     if (!base_mont) {
-        k_bases_to_mont<F><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_bases, n, b.conv); ::ace::note_launch();
+        k_bases_to_mont<F><<<(unsigned)((plan.n + 127) / 128), 128, 0, st>>>(d_bases, plan.n, b.conv); ::ace::note_launch();
         bases = b.conv;
     }
     int prof_sort = prof_begin(PROF_SORT, st);
@@ -215,15 +222,16 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     int prof = prof_begin(sizeof(F) == sizeof(fp_t) ? PROF_G1_BUCKET : PROF_G2_BUCKET, st);
     k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, b.order, keys, b.buckets); ::ace::note_launch();
     prof_end(prof, st, b.offsets + keys, 0);
-    uint32_t nseg = plan.windows() * plan.M;
+    uint32_t nseg = plan.all_windows() * plan.M;
     int prof_red = prof_begin(PROF_REDUCE, st);
     k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS); ::ace::note_launch();
     for (int lev = 0; (1u << lev) < plan.M; lev++) {
-        uint32_t pairs = plan.windows() * (plan.M >> (lev + 1));
-        k_tree_level<F><<<(pairs + 127) / 128, 128, 0, st>>>(b.segW, b.segS, plan.windows(), plan.M, lev,
+        uint32_t pairs = plan.all_windows() * (plan.M >> (lev + 1));
+        k_tree_level<F><<<(pairs + 127) / 128, 128, 0, st>>>(b.segW, b.segS, plan.all_windows(), plan.M, lev,
                                                              plan.lambda); ::ace::note_launch();
     }
-    k_msm_final<F><<<1, 32, 0, st>>>(b.segW, b.segS, plan.bucket_windows(), plan.M, plan.c, d_res, d_out); ::ace::note_launch();
+    k_msm_final<F><<<(plan.batch + 31) / 32, 32, 0, st>>>(b.segW, b.segS, plan.bucket_windows(), plan.M, plan.c,
+                                                           plan.batch, d_res, d_out); ::ace::note_launch();
     prof_end(prof_red, st, nullptr, (uint64_t)plan.windows() * plan.B);
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;

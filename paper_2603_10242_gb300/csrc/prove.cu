@@ -19,6 +19,8 @@
 //      MSMs are done, and the last kernel only adds and converts to affine.
 #include <string.h>
 
+#include <vector>
+
 #include "fixed_base.cuh"
 #include "pk.h"
 
@@ -144,6 +146,109 @@ __global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz
     } else {
         g1_xyzz C = xyzz_add(xyzz_add(res1[3], res1[0]), xyzz_add(xyzz_add(fx1[1], fx1[2]), fx1[3]));
         C = xyzz_add(C, *v);
+        write_g1(proof + 48, C);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// many proofs of one key in one pass (per-transaction proofs: every
+// transaction of a block proves the same circuit, Section 3.3, Algorithm 3
+// ParallelMap).  Proof q's witness is z + q m, its a, b, c are abc + 3 q N,
+// its quotient h + q N; every kernel covers all proofs (blockIdx.y or one
+// thread per proof).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_spmv3_many(CsrDev m, const fr_t* __restrict__ z, uint64_t wit, uint32_t N,
+                                                    fr_t* abc, int32_t* status) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t q = blockIdx.y;
+    z += (size_t)q * wit;
+    abc += (size_t)q * 3 * N;
+    fr_t v[3];
+#pragma unroll 1
+    for (int k = 0; k < 3; k++) {
+        fr_t acc = fe_zero<FrCfg>();
+        uint32_t b = m.rp[k][i], e = m.rp[k][i + 1];
+        for (uint32_t t = b; t < e; t++) acc = acc + ldg_fr(m.val[k] + t) * ldg_fr(z + __ldg(m.col[k] + t));
+        v[k] = acc * fe_rr<FrCfg>();
+        st_fr2(abc + (size_t)k * N + i, v[k]);
+    }
+    if (!fe_eq(v[0] * v[1], v[2])) atomicOr(status + q, 1);
+}
+
+__global__ void k_quotient_many(const fr_t* abc, uint32_t N, fr_t zinv, fr_t* h) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t q = blockIdx.y;
+    abc += (size_t)q * 3 * N;
+    fr_t a = ldg_fr(abc + i), b = ldg_fr(abc + N + i), c = ldg_fr(abc + 2 * (size_t)N + i);
+    st_fr2(h + (size_t)q * N + i, (a * b - c) * zinv);
+}
+
+__global__ void k_gather_many(const fr_t* __restrict__ z, uint64_t wit, const uint32_t* __restrict__ idx, uint32_t n,
+                              fr_t* out) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t q = blockIdx.y;
+    st_fr2(out + (size_t)q * n + k, ldg_fr(z + (size_t)q * wit + __ldg(idx + k)));
+}
+
+// per proof q: r_q, s_q, r_q s_q (canonical) at rsv[3 q .. 3 q + 2]
+__global__ void k_prove_fixed_many(PkTabs t, const fr_t* rsv, uint32_t count, g1_xyzz* fx1, g2_xyzz* fx2) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 5 * count) return;
+    const uint32_t q = g / 5, term = g % 5;
+    const fr_t r = rsv[3 * q], s = rsv[3 * q + 1], rs = rsv[3 * q + 2];
+    switch (term) {
+        case 0: fx1[4 * q + 0] = fixed_mul_tab(t.delta1, r.v); break;
+        case 1: fx1[4 * q + 1] = fixed_mul_tab(t.alpha1, s.v); break;
+        case 2: fx1[4 * q + 2] = fixed_mul_tab(t.beta1, r.v); break;
+        case 3: fx1[4 * q + 3] = fixed_mul_tab(t.delta1, rs.v); break;
+        default: fx2[q] = fixed_mul_tab(t.delta2, s.v); break;
+    }
+}
+
+__global__ void k_prove_var_many(const g1_xyzz* sa, const g1_xyzz* sb, const fr_t* rsv, uint32_t count,
+                                 g1_xyzz* v) {
+    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    const fr_t r = rsv[3 * q], s = rsv[3 * q + 1];
+    g1_xyzz a = sa[q], b = sb[q], ab = xyzz_add(a, b);
+    g1_xyzz acc = xyzz_inf<fp_t>();
+    for (int i = 255; i >= 0; i--) {
+        acc = xyzz_dbl(acc);
+        uint32_t bs = (s.v[i >> 5] >> (i & 31)) & 1u, br = (r.v[i >> 5] >> (i & 31)) & 1u;
+        if (bs && br) acc = xyzz_add(acc, ab);
+        else if (bs) acc = xyzz_add(acc, a);
+        else if (br) acc = xyzz_add(acc, b);
+    }
+    v[q] = acc;
+}
+
+// res1: S_H, S_A, S_B1, S_L, each `count` results; proof q at proof + 64 q
+__global__ void k_assemble_many(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2, const g1_xyzz* fx1,
+                                const g2_xyzz* fx2, const g1_xyzz* v, uint32_t count, uint32_t* proof) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 3 * count) return;
+    const uint32_t q = g / 3, w = g % 3;
+    const g1_xyzz *SH = res1, *SA = res1 + count, *SL = res1 + 3 * (size_t)count;
+    proof += 64 * (size_t)q;
+    if (w == 0) {
+        g1_xyzz A = xyzz_add(xyzz_add(xyzz_from_aff(fx->alpha1), SA[q]), fx1[4 * q + 0]);
+        write_g1(proof, A);
+    } else if (w == 1) {
+        g2_xyzz B = xyzz_add(xyzz_add(xyzz_from_aff(fx->beta2), resB2[q]), fx2[q]);
+        g2_aff b = aff_from_mont(xyzz_to_aff(B));
+        for (int i = 0; i < 8; i++) {
+            proof[16 + i] = b.x.c0.v[i];
+            proof[24 + i] = b.x.c1.v[i];
+            proof[32 + i] = b.y.c0.v[i];
+            proof[40 + i] = b.y.c1.v[i];
+        }
+    } else {
+        g1_xyzz C = xyzz_add(xyzz_add(SL[q], SH[q]),
+                             xyzz_add(xyzz_add(fx1[4 * q + 1], fx1[4 * q + 2]), fx1[4 * q + 3]));
+        C = xyzz_add(C, v[q]);
         write_g1(proof + 48, C);
     }
 }
@@ -295,6 +400,125 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     return ACE_OK;
 }
 
+// ---- many proofs of one key ---------------------------------------------------
+struct ManyPlans {
+    MsmPlan H, A, B, L;
+    size_t arena[PROVE_ARENAS];
+};
+
+static ManyPlans many_plans(const ace_pk* pk, uint32_t count) {
+    ManyPlans p;
+    p.H = pk->H_plan;
+    p.A = pk->A.plan;
+    p.B = pk->B1.plan;
+    p.L = pk->L.plan;
+    p.H.batch = p.A.batch = p.B.batch = p.L.batch = count;
+    const size_t N = pk->N, fr = sizeof(fr_t);
+    // arena 0: a, b, c and h of every proof, the H MSM, all per-proof points
+    p.arena[0] = 4 * N * count * fr + msm_scratch_bytes<fp_t>(p.H, true) +
+                 (size_t)count * (10 * sizeof(g1_xyzz) + 2 * sizeof(g2_xyzz) + 3 * fr) + (1 << 16);
+    p.arena[1] = pk->A.count * count * fr + msm_scratch_bytes<fp_t>(p.A, true) + 4096;
+    p.arena[2] = pk->B1.count * count * fr + msm_scratch_bytes<fp_t>(p.B, true) + 4096;
+    p.arena[3] = pk->B2.count * count * fr + msm_scratch_bytes<fp2_t>(p.B, true) + 4096;
+    p.arena[4] = pk->L.count * count * fr + msm_scratch_bytes<fp_t>(p.L, true) + 4096;
+    return p;
+}
+
+template <class F>
+static int gathered_msm_many(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z, uint64_t wit, Arena& ar,
+                             Xyzz<F>* res, cudaStream_t s) {
+    fr_t* zq = (fr_t*)ar.take((size_t)q.count * plan.batch * sizeof(fr_t) + 32);
+    if (!zq) {
+        set_error("prove_many: arena too small");
+        return ACE_E_OOM;
+    }
+    if (q.count) {
+        dim3 grid((q.count + 255) / 256, plan.batch);
+        k_gather_many<<<grid, 256, 0, s>>>(d_z, wit, q.d_idx, q.count, zq);
+        ::ace::note_launch();
+    }
+    return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
+}
+
+// `count` proofs of pk on proving slot 0 (level 0 streams), after the work on
+// st_in; d_z: count witnesses of pk->m values; h_rsv: per proof r, s, r s
+// (canonical); proofs and R1CS status to device memory; st_in waits for the end.
+static int prove_many_run(ace_ctx* ctx, const ace_pk* pk, uint32_t count, const fr_t* d_z, const fr_t* h_rsv,
+                          uint32_t* d_proofs, int32_t* d_status, cudaStream_t st_in) {
+    NttPlan* plan = nullptr;
+    ACE_TRY(ntt_get_plan(ctx, pk->log_n, &plan));
+    ACE_TRY(slot_ready(ctx, 0));
+    ProveSlot& sl = ctx->slots[0];
+    SlotStreams& ss = sl.lv[0];
+    ManyPlans pl = many_plans(pk, count);
+    for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, 0, k, pl.arena[k]));
+    for (auto& a : sl.ar) a.reset();
+    const uint32_t N = (uint32_t)pk->N;
+    const uint64_t wit = pk->m;
+    Arena& a0 = sl.ar[0];
+    fr_t* abc = (fr_t*)a0.take(3 * (size_t)N * count * sizeof(fr_t));
+    fr_t* h = (fr_t*)a0.take((size_t)N * count * sizeof(fr_t));
+    g1_xyzz* res1 = (g1_xyzz*)a0.take(4 * (size_t)count * sizeof(g1_xyzz));  // S_H, S_A, S_B1, S_L
+    g1_xyzz* fx1 = (g1_xyzz*)a0.take(4 * (size_t)count * sizeof(g1_xyzz));
+    g1_xyzz* vterm = (g1_xyzz*)a0.take((size_t)count * sizeof(g1_xyzz));
+    g2_xyzz* res2 = (g2_xyzz*)a0.take((size_t)count * sizeof(g2_xyzz));
+    g2_xyzz* fx2 = (g2_xyzz*)a0.take((size_t)count * sizeof(g2_xyzz));
+    fr_t* rsv = (fr_t*)a0.take(3 * (size_t)count * sizeof(fr_t));
+    if (!abc || !h || !res1 || !fx1 || !vterm || !res2 || !fx2 || !rsv) {
+        set_error("prove_many: arena too small");
+        return ACE_E_OOM;
+    }
+    PkTabs tabs{pk->d_tab_alpha1, pk->d_tab_beta1, pk->d_tab_delta1, pk->d_tab_delta2};
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_in, st_in));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_in, 0));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_done, 0));
+    ACE_TRY_CUDA(cudaMemcpyAsync(rsv, h_rsv, 3 * (size_t)count * sizeof(fr_t), cudaMemcpyHostToDevice, ss.main));
+    ACE_TRY_CUDA(cudaMemsetAsync(d_status, 0, count * sizeof(int32_t), ss.main));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_start, ss.main));
+    for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[k], sl.ev_start, 0));
+    // MSMs over the witness on the auxiliary streams
+    ACE_TRY(gathered_msm_many<fp_t>(pl.A, pk->A, d_z, wit, sl.ar[1], res1 + count, ss.aux[0]));
+    ACE_TRY(gathered_msm_many<fp_t>(pl.B, pk->B1, d_z, wit, sl.ar[2], res1 + 2 * (size_t)count, ss.aux[1]));
+    ACE_TRY(gathered_msm_many<fp2_t>(pl.B, pk->B2, d_z, wit, sl.ar[3], res2, ss.aux[2]));
+    ACE_TRY(gathered_msm_many<fp_t>(pl.L, pk->L, d_z, wit, sl.ar[4], res1 + 3 * (size_t)count, ss.aux[3]));
+    k_prove_fixed_many<<<(5 * count + 127) / 128, 128, 0, ss.aux[4]>>>(tabs, rsv, count, fx1, fx2); ::ace::note_launch();
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[0], ss.aux[0]));
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[1], ss.aux[1]));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[4], sl.ev_aux[0], 0));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[4], sl.ev_aux[1], 0));
+    k_prove_var_many<<<(count + 63) / 64, 64, 0, ss.aux[4]>>>(res1 + count, res1 + 2 * (size_t)count, rsv, count,
+                                                              vterm); ::ace::note_launch();
+    // QAP of every proof, then the H MSM, on the main stream
+    NttScale none, cos, icos;
+    cos.hi = plan->cos_hi;
+    cos.lo = plan->cos_lo;
+    cos.h = plan->h;
+    cos.brev = 1;
+    icos.hi = plan->icos_hi;
+    icos.lo = plan->icos_lo;
+    icos.h = plan->h;
+    icos.brev = 1;
+    int prof = prof_begin(PROF_SPMV, ss.main);
+    k_spmv3_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(csr_of(pk), d_z, wit, N, abc, d_status);
+    ::ace::note_launch();
+    prof_end(prof, ss.main, nullptr, (pk->nnz[0] + pk->nnz[1] + pk->nnz[2]) * count);
+    ACE_TRY(ntt_run(*plan, abc, 3 * (int)count, true, true, none, cos, ss.main));
+    ACE_TRY(ntt_run(*plan, abc, 3 * (int)count, false, false, none, none, ss.main));
+    k_quotient_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(abc, N, plan->zinv, h); ::ace::note_launch();
+    ACE_TRY(ntt_run(*plan, h, (int)count, true, true, none, icos, ss.main));
+    ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)h, a0, res1, nullptr, ss.main));
+    for (int k = 0; k < 5; k++) {
+        ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], ss.aux[k]));
+        ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_aux[k], 0));
+    }
+    k_assemble_many<<<(3 * count + 63) / 64, 64, 0, ss.main>>>(pk->d_fixed, res1, res2, fx1, fx2, vterm, count,
+                                                               d_proofs); ::ace::note_launch();
+    ACE_TRY_CUDA(cudaGetLastError());
+    ACE_TRY_CUDA(cudaEventRecord(sl.ev_done, ss.main));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(st_in, sl.ev_done, 0));
+    return ACE_OK;
+}
+
 static bool canonical_fr(const ace_fr* x) {
     fr_t t;
     memcpy(t.v, x->l, 32);
@@ -419,6 +643,63 @@ int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_
     ACE_TRY_CUDA(cudaMemcpyAsync(proofs, d_proofs, k * 256, cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(status, d_status, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaStreamSynchronize(st));
+    return ACE_OK;
+}
+
+int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, const ace_fr* rs, const ace_fr* ss,
+                   uint8_t* proofs, int32_t* status) {
+    clear_error();
+    if (!ctx || !pk || (k && (!d_z || !rs || !ss || !proofs || !status))) {
+        set_error("ace_prove_many: NULL argument");
+        return ACE_E_ARG;
+    }
+    if (k == 0) return ACE_OK;
+    if ((uintptr_t)d_z & 15u) {
+        set_error("ace_prove_many: d_z must be 16-byte aligned");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<fr_t> rsv(3 * k);
+    for (size_t i = 0; i < k; i++) {
+        if (!canonical_fr(rs + i) || !canonical_fr(ss + i)) {
+            set_error("ace_prove_many: r and s of proof %zu must be canonical Fr values", i);
+            return ACE_E_ARG;
+        }
+        memcpy(rsv[3 * i].v, rs[i].l, 32);
+        memcpy(rsv[3 * i + 1].v, ss[i].l, 32);
+        rsv[3 * i + 2] = fe_from_mont(fe_to_mont(rsv[3 * i]) * fe_to_mont(rsv[3 * i + 1]));
+    }
+    // chunks of proofs whose scratch stays within MANY_SCRATCH bytes (one
+    // proof per chunk at least); 65535 bounds the grid's y dimension / 3
+    const size_t MANY_SCRATCH = (size_t)24 << 30;
+    ManyPlans one = many_plans(pk, 1);
+    size_t per = 0;
+    for (int a = 0; a < PROVE_ARENAS; a++) per += one.arena[a];
+    size_t chunk = MANY_SCRATCH / (per ? per : 1);
+    // entries (count n K) and keys (count windows 2^(c-1)) are 32-bit indices
+    size_t ent = 1, keys = 1;
+    for (const MsmPlan* q : {&one.H, &one.A, &one.B, &one.L}) {
+        ent = ent > q->n * (size_t)q->K ? ent : q->n * (size_t)q->K;
+        keys = keys > (size_t)q->keys_per() ? keys : (size_t)q->keys_per();
+    }
+    if (chunk > ((size_t)1 << 31) / ent) chunk = ((size_t)1 << 31) / ent;
+    if (chunk > ((size_t)1 << 31) / keys) chunk = ((size_t)1 << 31) / keys;
+    if (chunk < 1) chunk = 1;
+    if (chunk > 21845) chunk = 21845;
+    if (chunk > k) chunk = k;
+    ACE_TRY(arena_ensure(ctx, 3, chunk * (256 + sizeof(int32_t)) + 1024));
+    ctx->scratch[3].reset();
+    uint32_t* d_proofs = (uint32_t*)ctx->scratch[3].take(chunk * 256);
+    int32_t* d_status = (int32_t*)ctx->scratch[3].take(chunk * sizeof(int32_t));
+    cudaStream_t st = ctx->stream;
+    for (size_t b = 0; b < k; b += chunk) {
+        uint32_t c = (uint32_t)(k - b < chunk ? k - b : chunk);
+        ACE_TRY(prove_many_run(ctx, pk, c, (const fr_t*)d_z + b * pk->m, rsv.data() + 3 * b, d_proofs, d_status, st));
+        ACE_TRY_CUDA(cudaMemcpyAsync(proofs + 256 * b, d_proofs, (size_t)c * 256, cudaMemcpyDeviceToHost, st));
+        ACE_TRY_CUDA(cudaMemcpyAsync(status + b, d_status, (size_t)c * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        // the next chunk reuses the device outputs and the host r, s copy
+        ACE_TRY_CUDA(cudaStreamSynchronize(st));
+    }
     return ACE_OK;
 }
 

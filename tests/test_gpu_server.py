@@ -62,9 +62,14 @@ def test_server_unsat_and_deadline():
     p3, _ = srv.wait(j3, 120)
     assert p1 == p3 == ref.prove(pks[1], gu.dev(z), r, s)
     srv.close()
-    # one slot, a tiny queue deadline: jobs behind the first cannot start in time
-    srv = ace.Server(sctx, spk, slots=1, max_queue_wait_s=1e-4)
-    ids = [srv.submit(spk, good_h, r, s) for _ in range(4)]
+    # one slot and a 2 ms queue deadline: the first job starts at once (the
+    # server thread polls every 50 us), the jobs behind a proof of several
+    # milliseconds cannot start in time
+    big = ace.Circuit(15, 1 << 15, 100, 0, 0, seed=90)
+    bpk = ace.ProvingKey(sctx, big, toxic_seed=91)
+    big_h = torch.frombuffer(bytearray(big.witness(92)), dtype=torch.uint8).pin_memory()
+    srv = ace.Server(sctx, bpk, slots=1, max_queue_wait_s=2e-3)
+    ids = [srv.submit(bpk, big_h, r, s) for _ in range(4)]
     codes = []
     for jid in ids:
         try:

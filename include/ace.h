@@ -327,6 +327,16 @@ int ace_debug_scheduler_sim(int slots, size_t budget, size_t n, const double* ar
                             const size_t* mem, double max_wait, double* start_out, double* finish_out,
                             int32_t* status_out, uint64_t* peaks);
 
+/* Witnesses of k instances of circuit c on the device, instance q from input
+ * seed seeds[q] (host array): the same values, in the same order, as
+ * ace_witness(c, seeds[q]) (the w_tx each transaction's proof starts from,
+ * Section 3.3, Algorithm 3).  d_z: k x m canonical values (device, caller
+ * owned), laid out as ace_prove_many expects.  The R1CS is not checked here
+ * (the provers check it and report it per proof).  Synchronises `stream`.
+ * Scratch: the circuit's constants and k x 3 n_perm draw positions. */
+int ace_witness_many(ace_ctx* ctx, const ace_circuit* c, size_t k, const uint64_t* seeds, ace_fr* d_z,
+                     ace_stream stream);
+
 /* Many proofs of ONE key in one pass: the per-transaction proofs of a block
  * (every transaction proves the same circuit; Section 3.3, Algorithm 3
  * ParallelMap over the block's transactions).  Every stage runs once for

@@ -78,6 +78,7 @@ def lib():
             "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
             "ace_debug_pairing": (i32, [cp, cp, cp]),
             "ace_prove_many": (i32, [vp, vp, sz, vp, cp, cp, vp, vp]),
+            "ace_witness_many": (i32, [vp, vp, sz, vp, vp, vp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
             "ace_autotune_batch_slots": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -192,6 +193,12 @@ class Context:
     def ntt_mont(self, data, log_n: int, count: int, dif: bool, inverse: bool, stream=None):
         check(lib().ace_ntt_mont(self.h, _ptr(data), log_n, count, 1 if dif else 0, 1 if inverse else 0,
                                  _stream(stream)))
+
+    def witness_many(self, circuit: "Circuit", seeds, d_z, stream=None):
+        """Witnesses of len(seeds) instances into d_z (k x m canonical values) on the device."""
+        k = len(seeds)
+        arr = (ctypes.c_uint64 * max(1, k))(*seeds)
+        check(lib().ace_witness_many(self.h, circuit.h, k, arr, _ptr(d_z), _stream(stream)))
 
     def prove_many(self, pk: "ProvingKey", d_z, k: int, rs: bytes, ss: bytes):
         """k proofs of one key in one pass; d_z holds the k witnesses back to back."""

@@ -63,9 +63,14 @@ size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont) {
 
 // ---------------------------------------------------------------------------
 // bucket accumulation: one thread per bucket, one mixed addition per entry
+// (ACE_BUCKET_MIN_BLOCKS: resident blocks of 128 threads per SM the compiler
+// must allow, which caps the registers per thread)
 // ---------------------------------------------------------------------------
+#ifndef ACE_BUCKET_MIN_BLOCKS
+#define ACE_BUCKET_MIN_BLOCKS 1
+#endif
 template <class F>
-__global__ void __launch_bounds__(128) k_bucket_acc(const Affine<F>* __restrict__ bases,
+__global__ void __launch_bounds__(128, ACE_BUCKET_MIN_BLOCKS) k_bucket_acc(const Affine<F>* __restrict__ bases,
                                                     const uint32_t* __restrict__ entries,
                                                     const uint32_t* __restrict__ offsets,
                                                     const uint32_t* __restrict__ order, uint32_t nkeys,

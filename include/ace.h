@@ -218,6 +218,21 @@ int ace_rs_from_seed(uint64_t seed, ace_fr* r, ace_fr* s);
  * (the three-pairing check of Section 3.3 / Section 3.4).  n_pub must be 1. */
 int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t proof[256]);
 
+/* Batch verification of k proofs of one verifying key (the validators'
+ * check, Section 3.4 Algorithm 4, for many proofs at once): returns 1 iff
+ *   prod_i e(rho_i A_i, B_i) e(-(sum rho_i) alpha1, beta2)
+ *          e(-(sum rho_i)(ic[0] + ...) , gamma2) e(-(sum rho_i C_i), delta2) = 1
+ * with IC folded as (sum rho_i) ic[0] + (sum rho_i x_i) ic[1], and every B_i
+ * in the order-r subgroup; 0 if some proof is invalid (then at least one is,
+ * except with probability about k 2^-128), negative on malformed input.
+ * rho_i are 128-bit values drawn from SplitMix64(seed, purpose 12): a
+ * verifier facing adversarial provers must pass a seed they cannot predict.
+ * pubs: k public inputs (host, canonical); proofs: k x 256 bytes (host).
+ * The per-proof work (subgroup check, rho_i A_i, rho_i C_i, Miller loop) runs
+ * on the device, the final exponentiation on the host. */
+int ace_verify_batch(ace_ctx* ctx, const ace_vk* vk, size_t k, const ace_fr* pubs, const uint8_t* proofs,
+                     uint64_t seed);
+
 /* NTT of N = 2^log_n canonical Fr values in natural order, in place on the
  * device: the transforms of the QAP step (H = {omega^i}, omega = 5^((r-1)/N),
  * coset g H with g = 5).  kind: 0 forward (coefficients -> values on H),
@@ -250,6 +265,10 @@ int ace_debug_curve_op(int group, int op, const void* d_a, const void* d_b, cons
 /* Host: the library's optimal-ate pairing e(P, Q) after final exponentiation,
  * as 6 Fp2 coefficients (w^0, w^2, w^4, w^1, w^3, w^5), canonical. */
 int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
+/* The same pairing by Miller-loop form 0 (affine, the single verifier's) or 1
+ * (homogeneous projective, the loop the batch verifier runs on the device),
+ * computed on the host. */
+int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
 /* Measured 32-bit multiply-add throughput of the device (operations/s):
  * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs, 3 mad.wide.u32
  * (one 32 x 32 -> 64-bit limb product with 64-bit accumulate per operation). */

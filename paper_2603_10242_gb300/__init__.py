@@ -79,6 +79,8 @@ def lib():
             "ace_debug_pairing": (i32, [cp, cp, cp]),
             "ace_prove_many": (i32, [vp, vp, sz, vp, cp, cp, vp, vp]),
             "ace_witness_many": (i32, [vp, vp, sz, vp, vp, vp]),
+            "ace_verify_batch": (i32, [vp, vp, sz, cp, cp, u64]),
+            "ace_debug_pairing_form": (i32, [i32, cp, cp, cp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
             "ace_autotune_batch_slots": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -199,6 +201,11 @@ class Context:
         k = len(seeds)
         arr = (ctypes.c_uint64 * max(1, k))(*seeds)
         check(lib().ace_witness_many(self.h, circuit.h, k, arr, _ptr(d_z), _stream(stream)))
+
+    def verify_batch(self, vk: "VerifyingKey", pubs: bytes, proofs: bytes, seed: int) -> int:
+        """1 if all len(proofs) / 256 proofs verify (random linear combination), else 0."""
+        k = len(proofs) // 256
+        return check(lib().ace_verify_batch(self.h, ctypes.byref(vk), k, pubs, proofs, seed))
 
     def prove_many(self, pk: "ProvingKey", d_z, k: int, rs: bytes, ss: bytes):
         """k proofs of one key in one pass; d_z holds the k witnesses back to back."""

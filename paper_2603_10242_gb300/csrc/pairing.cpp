@@ -18,6 +18,7 @@
 
 #include "../../include/ace.h"
 #include "field.cuh"
+#include "pairing.cuh"
 
 namespace ace {
 void set_error(const char* fmt, ...);
@@ -26,59 +27,6 @@ void clear_error();
 
 namespace ace {
 namespace {
-
-typedef fp2_t F2;
-struct F6 {
-    F2 a0, a1, a2;
-};
-struct F12 {
-    F6 c0, c1;
-};
-
-F2 f2_zero() { return field_zero<fp2_t>(); }
-F2 f2_one() { return field_one<fp2_t>(); }
-F2 f2_conj(const F2& a) { return {a.c0, fe_neg(a.c1)}; }
-F2 f2_scale(const F2& a, const fp_t& s) { return {a.c0 * s, a.c1 * s}; }
-// (a0 + a1 u)(9 + u) = (9 a0 - a1) + (a0 + 9 a1) u
-F2 mul_xi(const F2& a) {
-    fp_t nine = fe_from_u32<FpCfg>(9);
-    return {a.c0 * nine - a.c1, a.c0 + a.c1 * nine};
-}
-
-F6 f6_zero() { return {f2_zero(), f2_zero(), f2_zero()}; }
-F6 f6_one() { return {f2_one(), f2_zero(), f2_zero()}; }
-F6 operator+(const F6& a, const F6& b) { return {a.a0 + b.a0, a.a1 + b.a1, a.a2 + b.a2}; }
-F6 operator-(const F6& a, const F6& b) { return {a.a0 - b.a0, a.a1 - b.a1, a.a2 - b.a2}; }
-F6 f6_neg(const F6& a) { return {fe_neg(a.a0), fe_neg(a.a1), fe_neg(a.a2)}; }
-F6 operator*(const F6& a, const F6& b) {
-    F2 c0 = a.a0 * b.a0 + mul_xi(a.a1 * b.a2 + a.a2 * b.a1);
-    F2 c1 = a.a0 * b.a1 + a.a1 * b.a0 + mul_xi(a.a2 * b.a2);
-    F2 c2 = a.a0 * b.a2 + a.a1 * b.a1 + a.a2 * b.a0;
-    return {c0, c1, c2};
-}
-F6 mul_v(const F6& a) { return {mul_xi(a.a2), a.a0, a.a1}; }
-F6 f6_inv(const F6& a) {
-    F2 t0 = fe_sqr(a.a0) - mul_xi(a.a1 * a.a2);
-    F2 t1 = mul_xi(fe_sqr(a.a2)) - a.a0 * a.a1;
-    F2 t2 = fe_sqr(a.a1) - a.a0 * a.a2;
-    F2 d = a.a0 * t0 + mul_xi(a.a2 * t1 + a.a1 * t2);
-    F2 di = fe_inv(d);
-    return {t0 * di, t1 * di, t2 * di};
-}
-bool f6_eq(const F6& a, const F6& b) { return fe_eq(a.a0, b.a0) && fe_eq(a.a1, b.a1) && fe_eq(a.a2, b.a2); }
-
-F12 f12_one() { return {f6_one(), f6_zero()}; }
-F12 operator*(const F12& a, const F12& b) {
-    F6 t0 = a.c0 * b.c0, t1 = a.c1 * b.c1;
-    return {t0 + mul_v(t1), a.c0 * b.c1 + a.c1 * b.c0};
-}
-F12 f12_conj(const F12& a) { return {a.c0, f6_neg(a.c1)}; }
-F12 f12_inv(const F12& a) {
-    F6 d = a.c0 * a.c0 - mul_v(a.c1 * a.c1);
-    F6 di = f6_inv(d);
-    return {a.c0 * di, f6_neg(a.c1 * di)};
-}
-bool f12_eq(const F12& a, const F12& b) { return f6_eq(a.c0, b.c0) && f6_eq(a.c1, b.c1); }
 
 // ---- constants -------------------------------------------------------------
 struct Consts {
@@ -403,6 +351,64 @@ G1a g1_mul(const G1a& p, const uint32_t k[8]) {
 
 }  // namespace
 
+// Constants and final exponentiation for the device Miller loops (batch
+// verification): F12 values cross translation units as 12 Montgomery Fp
+// limbs in the order of the tower (c0.a0.c0, c0.a0.c1, ..., c1.a2.c1).
+void pairing_consts_raw(fp_t gamma[12], fp_t b2[2], uint64_t* ate_lo, uint64_t* ate_hi) {
+    const Consts& k = consts();
+    for (int i = 0; i < 6; i++) {
+        gamma[2 * i] = k.gamma[i].c0;
+        gamma[2 * i + 1] = k.gamma[i].c1;
+    }
+    b2[0] = k.b2.c0;
+    b2[1] = k.b2.c1;
+    *ate_lo = (uint64_t)k.ate;
+    *ate_hi = (uint64_t)(k.ate >> 64);
+}
+void final_exp_raw(const fp_t in[12], fp_t out[12]) {
+    F12 f;
+    static_assert(sizeof(F12) == 12 * sizeof(fp_t), "F12 is 12 Fp values");
+    memcpy(&f, in, sizeof f);
+    F12 r = final_exp(f);
+    memcpy(out, &r, sizeof r);
+}
+bool final_exp_is_one_raw(const fp_t in[12]) {
+    F12 f;
+    memcpy(&f, in, sizeof f);
+    return f12_eq(final_exp(f), f12_one());
+}
+// Parse a proof / verifying-key point to Montgomery affine coordinates
+// (infinity = zeros); false if not canonical or not on the curve.
+bool parse_g1_raw(const uint8_t b[64], fp_t out[2]) {
+    bool inf;
+    if (!read_g1(b, out[0], out[1], inf)) return false;
+    if (inf) out[0] = out[1] = fe_zero<FpCfg>();
+    return true;
+}
+bool parse_g2_raw(const uint8_t b[128], fp_t out[4]) {
+    G2a q;
+    if (!read_g2(b, q)) return false;
+    if (q.inf) q.x = q.y = f2_zero();
+    out[0] = q.x.c0;
+    out[1] = q.x.c1;
+    out[2] = q.y.c0;
+    out[3] = q.y.c1;
+    return true;
+}
+
+// Miller function by the projective loop (the device's), for tests
+bool miller_proj_raw(const fp_t& xp, const fp_t& yp, const fp_t q[4], fp_t out[12]) {
+    PairConsts k;
+    fp_t g[12], b[2];
+    pairing_consts_raw(g, b, &k.ate_lo, &k.ate_hi);
+    for (int i = 0; i < 6; i++) k.gamma[i] = {g[2 * i], g[2 * i + 1]};
+    k.b2 = {b[0], b[1]};
+    F12 f;
+    if (!miller_proj(xp, yp, {q[0], q[1]}, {q[2], q[3]}, k, f)) return false;
+    memcpy(out, &f, sizeof f);
+    return true;
+}
+
 // product of pairings e(P_i, Q_i) == 1 ?  (P, Q given in Montgomery affine)
 int pairing_product_is_one(int n, const fp_t* px, const fp_t* py, const bool* pinf, const G2a* q) {
     F12 acc = f12_one();
@@ -471,12 +477,26 @@ int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t 
 // Diagnostic: e(P, Q) as 12 canonical Fp limbs-triples, tower order
 // (c0.a0, c0.a1, c0.a2, c1.a0, c1.a1, c1.a2; each Fp2 as c0, c1).
 int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]) {
+    return ace_debug_pairing_form(0, g1, g2, out);
+}
+
+// form 0: affine Miller loop (the single verifier's); form 1: projective
+// Miller loop (the batch verifier's device loop, run here on the host)
+int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]) {
     fp_t x, y;
     bool inf;
     G2a q;
+    if (form < 0 || form > 1) return ACE_E_ARG;
     if (!read_g1(g1, x, y, inf) || !read_g2(g2, q)) return ACE_E_NOT_ON_CURVE;
     F12 f = f12_one();
-    if (!inf && !q.inf && !miller(x, y, q, f)) return ACE_E_ARG;
+    if (!inf && !q.inf) {
+        if (form == 0 && !miller(x, y, q, f)) return ACE_E_ARG;
+        if (form == 1) {
+            fp_t qq[4] = {q.x.c0, q.x.c1, q.y.c0, q.y.c1}, raw[12];
+            if (!miller_proj_raw(x, y, qq, raw)) return ACE_E_ARG;
+            memcpy(&f, raw, sizeof f);
+        }
+    }
     f = final_exp(f);
     const F2* c[6] = {&f.c0.a0, &f.c0.a1, &f.c0.a2, &f.c1.a0, &f.c1.a1, &f.c1.a2};
     for (int i = 0; i < 6; i++) {

@@ -131,3 +131,24 @@ def test_host_pairing_bilinear(lib):
     lhs = e(O.g1_mul(g1, a), O.g2_mul(g2, b))
     assert lhs == e(O.g1_mul(g1, a * b % Y.R), g2) == e(g1, O.g2_mul(g2, a * b % Y.R))
     assert e(O.g1_mul(g1, Y.R - 1), g2) != base
+
+
+def test_projective_miller_loop_matches_affine(lib):
+    """The batch verifier's projective Miller loop (run here on the host) and
+    the single verifier's affine one give the same pairing values."""
+    import random
+    f = lib.ace_debug_pairing_form
+    f.restype = ctypes.c_int
+    rng = random.Random(5)
+    g1, g2 = O.g1_generator(), O.g2_generator()
+    for _ in range(3):
+        P = O.g1_mul(g1, rng.randrange(1, Y.R))
+        Q = O.g2_mul(g2, rng.randrange(1, Y.R))
+        a, b = ctypes.create_string_buffer(384), ctypes.create_string_buffer(384)
+        assert f(0, P, Q, a) == 0 and f(1, P, Q, b) == 0
+        assert a.raw == b.raw
+    # bilinearity through the projective loop: e(2P, Q) = e(P, 2Q)
+    P, Q = O.g1_mul(g1, 77), O.g2_mul(g2, 99)
+    a, b = ctypes.create_string_buffer(384), ctypes.create_string_buffer(384)
+    assert f(1, O.g1_mul(P, 2), Q, a) == 0 and f(1, P, O.g2_mul(Q, 2), b) == 0
+    assert a.raw == b.raw

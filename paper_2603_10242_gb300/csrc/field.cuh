@@ -28,6 +28,7 @@ struct FpCfg {
     static constexpr uint32_t M0 = 0xd87cfd47u, M1 = 0x3c208c16u, M2 = 0x6871ca8du, M3 = 0x97816a91u,
                               M4 = 0x8181585du, M5 = 0xb85045b6u, M6 = 0xe131a029u, M7 = 0x30644e72u;
     static constexpr uint32_t INV = 0xe4866389u;  // -p^{-1} mod 2^32
+    static constexpr uint64_t INV64 = 0x87d20782e4866389ull;  // -p^{-1} mod 2^64
     static constexpr uint32_t ONE0 = 0xc58f0d9du, ONE1 = 0xd35d438du, ONE2 = 0xf5c70b3du, ONE3 = 0x0a78eb28u,
                               ONE4 = 0x7879462cu, ONE5 = 0x666ea36fu, ONE6 = 0x9a07df2fu, ONE7 = 0x0e0a77c1u;
     static constexpr uint32_t RR0 = 0x538afa89u, RR1 = 0xf32cfc5bu, RR2 = 0xd44501fbu, RR3 = 0xb5e71911u,
@@ -38,6 +39,7 @@ struct FrCfg {
     static constexpr uint32_t M0 = 0xf0000001u, M1 = 0x43e1f593u, M2 = 0x79b97091u, M3 = 0x2833e848u,
                               M4 = 0x8181585du, M5 = 0xb85045b6u, M6 = 0xe131a029u, M7 = 0x30644e72u;
     static constexpr uint32_t INV = 0xefffffffu;  // -r^{-1} mod 2^32
+    static constexpr uint64_t INV64 = 0xc2e1f593efffffffull;  // -r^{-1} mod 2^64
     static constexpr uint32_t ONE0 = 0x4ffffffbu, ONE1 = 0xac96341cu, ONE2 = 0x9f60cd29u, ONE3 = 0x36fc7695u,
                               ONE4 = 0x7879462eu, ONE5 = 0x666ea36fu, ONE6 = 0x9a07df2fu, ONE7 = 0x0e0a77c1u;
     static constexpr uint32_t RR0 = 0xae216da7u, RR1 = 0x1bb8e645u, RR2 = 0xe35c59e3u, RR3 = 0x53fe3ab1u,
@@ -149,40 +151,53 @@ inline void h_sub(uint32_t* r, const uint32_t* a, const uint32_t* b) {
     }
     for (int i = 0; i < 8; i++) r[i] = d[i];
 }
+// CIOS over four 64-bit limbs with 128-bit products (host compilers on both
+// x86-64 and AArch64 provide unsigned __int128)
 template <class C>
 inline void h_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
-    uint32_t t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < 8; i++) {
-        uint64_t c = 0;
-        for (int j = 0; j < 8; j++) {
-            c += (uint64_t)t[j] + (uint64_t)a[j] * b[i];
-            t[j] = (uint32_t)c;
-            c >>= 32;
-        }
-        c += t[8];
-        t[8] = (uint32_t)c;
-        t[9] = (uint32_t)(c >> 32);
-        uint32_t m = t[0] * C::INV;
-        c = (uint64_t)t[0] + (uint64_t)m * mod_limb<C>(0);
-        c >>= 32;
-        for (int j = 1; j < 8; j++) {
-            c += (uint64_t)t[j] + (uint64_t)m * mod_limb<C>(j);
-            t[j - 1] = (uint32_t)c;
-            c >>= 32;
-        }
-        c += t[8];
-        t[7] = (uint32_t)c;
-        t[8] = t[9] + (uint32_t)(c >> 32);
+    typedef unsigned __int128 u128;
+    uint64_t A[4], B[4], M[4], t[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 4; i++) {
+        A[i] = (uint64_t)a[2 * i] | ((uint64_t)a[2 * i + 1] << 32);
+        B[i] = (uint64_t)b[2 * i] | ((uint64_t)b[2 * i + 1] << 32);
+        M[i] = (uint64_t)mod_limb<C>(2 * i) | ((uint64_t)mod_limb<C>(2 * i + 1) << 32);
     }
-    uint32_t d[8];
-    int64_t br = 0;
-    for (int i = 0; i < 8; i++) {
-        int64_t x = (int64_t)t[i] - mod_limb<C>(i) + br;
-        d[i] = (uint32_t)x;
-        br = x < 0 ? -1 : 0;
+    for (int i = 0; i < 4; i++) {
+        u128 c = 0;
+        for (int j = 0; j < 4; j++) {
+            c += (u128)t[j] + (u128)A[j] * B[i];
+            t[j] = (uint64_t)c;
+            c >>= 64;
+        }
+        c += t[4];
+        t[4] = (uint64_t)c;
+        t[5] = (uint64_t)(c >> 64);
+        uint64_t m = t[0] * C::INV64;
+        c = (u128)t[0] + (u128)m * M[0];
+        c >>= 64;
+        for (int j = 1; j < 4; j++) {
+            c += (u128)t[j] + (u128)m * M[j];
+            t[j - 1] = (uint64_t)c;
+            c >>= 64;
+        }
+        c += t[4];
+        t[3] = (uint64_t)c;
+        t[4] = t[5] + (uint64_t)(c >> 64);
     }
-    bool keep = (t[8] == 0) && br != 0;
-    for (int i = 0; i < 8; i++) r[i] = keep ? t[i] : d[i];
+    // t < 2m: one conditional subtraction
+    uint64_t d[4];
+    u128 br = 0;
+    for (int i = 0; i < 4; i++) {
+        u128 x = (u128)t[i] - M[i] - br;
+        d[i] = (uint64_t)x;
+        br = (x >> 127) & 1;  // borrow
+    }
+    bool keep = (t[4] == 0) && br != 0;
+    for (int i = 0; i < 4; i++) {
+        uint64_t v = keep ? t[i] : d[i];
+        r[2 * i] = (uint32_t)v;
+        r[2 * i + 1] = (uint32_t)(v >> 32);
+    }
 }
 
 // ---------------------------------------------------------------------------

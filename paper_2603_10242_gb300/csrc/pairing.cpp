@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ace.h"
+#include "curve.cuh"
 #include "field.cuh"
 #include "pairing.cuh"
 
@@ -190,7 +191,7 @@ F12 frobenius(const F12& a) {
 F12 f12_pow(const F12& a, const Big& e) {
     F12 acc = f12_one();
     for (int i = (int)e.size() * 32 - 1; i >= 0; i--) {
-        acc = acc * acc;
+        acc = f12_sqr(acc);
         if ((e[i >> 5] >> (i & 31)) & 1u) acc = acc * a;
     }
     return acc;
@@ -278,47 +279,13 @@ bool read_g2(const uint8_t* b, G2a& q) {
     return fe_eq(fe_sqr(q.y), fe_sqr(q.x) * q.x + consts().b2);
 }
 
-// r Q == O on the twist (subgroup membership), affine double-and-add
+// r Q == O on the twist (subgroup membership): XYZZ double-and-add
 bool g2_in_subgroup(const G2a& q) {
     if (q.inf) return true;
     uint32_t rl[8];
     for (int i = 0; i < 8; i++) rl[i] = mod_limb<FrCfg>(i);
-    G2a acc = {f2_zero(), f2_zero(), true};
-    for (int i = 253; i >= 0; i--) {
-        // acc = 2 acc
-        if (!acc.inf) {
-            if (fe_is_zero(acc.y)) {
-                acc.inf = true;
-            } else {
-                F2 xx = fe_sqr(acc.x);
-                F2 lam = (xx + xx + xx) * fe_inv(acc.y + acc.y);
-                F2 x3 = fe_sqr(lam) - acc.x - acc.x;
-                acc.y = lam * (acc.x - x3) - acc.y;
-                acc.x = x3;
-            }
-        }
-        if ((rl[i >> 5] >> (i & 31)) & 1u) {
-            if (acc.inf) {
-                acc = q;
-            } else if (fe_eq(acc.x, q.x)) {
-                if (fe_eq(acc.y, q.y)) {
-                    F2 xx = fe_sqr(acc.x);
-                    F2 lam = (xx + xx + xx) * fe_inv(acc.y + acc.y);
-                    F2 x3 = fe_sqr(lam) - acc.x - acc.x;
-                    acc.y = lam * (acc.x - x3) - acc.y;
-                    acc.x = x3;
-                } else {
-                    acc.inf = true;
-                }
-            } else {
-                F2 lam = (q.y - acc.y) * fe_inv(q.x - acc.x);
-                F2 x3 = fe_sqr(lam) - acc.x - q.x;
-                acc.y = lam * (acc.x - x3) - acc.y;
-                acc.x = x3;
-            }
-        }
-    }
-    return acc.inf;
+    g2_aff a = {q.x, q.y};
+    return xyzz_is_inf(xyzz_mul_aff(a, rl));
 }
 
 // affine G1 helpers for the input term ic0 + x ic1
@@ -326,29 +293,6 @@ struct G1a {
     fp_t x, y;
     bool inf;
 };
-G1a g1_add(const G1a& a, const G1a& b) {
-    if (a.inf) return b;
-    if (b.inf) return a;
-    fp_t lam;
-    if (fe_eq(a.x, b.x)) {
-        if (!fe_eq(a.y, b.y) || fe_is_zero(a.y)) return {fe_zero<FpCfg>(), fe_zero<FpCfg>(), true};
-        fp_t xx = fe_sqr(a.x);
-        lam = (xx + xx + xx) * fe_inv(a.y + a.y);
-    } else {
-        lam = (b.y - a.y) * fe_inv(b.x - a.x);
-    }
-    fp_t x3 = fe_sqr(lam) - a.x - b.x;
-    return {x3, lam * (a.x - x3) - a.y, false};
-}
-G1a g1_mul(const G1a& p, const uint32_t k[8]) {
-    G1a acc = {fe_zero<FpCfg>(), fe_zero<FpCfg>(), true};
-    for (int i = 255; i >= 0; i--) {
-        acc = g1_add(acc, acc);
-        if ((k[i >> 5] >> (i & 31)) & 1u) acc = g1_add(acc, p);
-    }
-    return acc;
-}
-
 }  // namespace
 
 // Constants and final exponentiation for the device Miller loops (batch
@@ -411,11 +355,19 @@ bool miller_proj_raw(const fp_t& xp, const fp_t& yp, const fp_t q[4], fp_t out[1
 
 // product of pairings e(P_i, Q_i) == 1 ?  (P, Q given in Montgomery affine)
 int pairing_product_is_one(int n, const fp_t* px, const fp_t* py, const bool* pinf, const G2a* q) {
+    static const PairConsts pc = [] {
+        PairConsts k;
+        fp_t g[12], b[2];
+        pairing_consts_raw(g, b, &k.ate_lo, &k.ate_hi);
+        for (int i = 0; i < 6; i++) k.gamma[i] = {g[2 * i], g[2 * i + 1]};
+        k.b2 = {b[0], b[1]};
+        return k;
+    }();
     F12 acc = f12_one();
     for (int i = 0; i < n; i++) {
         if (pinf[i] || q[i].inf) continue;
         F12 f;
-        if (!miller(px[i], py[i], q[i], f)) return -1;
+        if (!miller_proj(px[i], py[i], q[i].x, q[i].y, pc, f)) return -1;
         acc = acc * f;
     }
     return f12_eq(final_exp(acc), f12_one()) ? 1 : 0;
@@ -460,7 +412,10 @@ int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t 
         set_error("ace_verify: verifying key point not on the curve");
         return ACE_E_NOT_ON_CURVE;
     }
-    G1a ic = g1_add({i0x, i0y, i0inf}, g1_mul({i1x, i1y, i1inf}, x.v));
+    g1_xyzz icx = xyzz_mul_aff(g1_aff{i1x, i1y}, x.v);
+    if (!i0inf) icx = xyzz_add_aff(icx, g1_aff{i0x, i0y});
+    g1_aff ica = xyzz_to_aff(icx);
+    G1a ic = {ica.x, ica.y, xyzz_is_inf(icx)};
     // e(-A, B) e(alpha, beta) e(IC, gamma) e(C, delta) == 1
     fp_t px[4] = {ax, alx, ic.x, cx};
     fp_t py[4] = {fe_neg(ay), aly, ic.y, cy};

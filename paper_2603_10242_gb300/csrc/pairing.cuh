@@ -9,8 +9,8 @@
 // Miller loop in homogeneous projective coordinates (x = X/Z, y = Y/Z), no
 // inversions.  Lines are scaled by factors in Fp2, which the final
 // exponentiation removes.
-//   doubling (tangent at T, scaled by 2 y Z^2 ... i.e. by 2YZ after clearing
-//   denominators): with B = Y^2, E = 3 b' Z^2
+//   doubling (the affine tangent line at T times 2 y Z^2 = 2 Y Z): with
+//   B = Y^2, E = 3 b' Z^2
 //     line = 2YZ yP  -  3X^2 xP w  +  (B - E) w^3
 //     X3 = 2XY (B - 3E),  Y3 = (B + 3E)^2 - 12 E^2,  Z3 = 8 B YZ
 //   mixed addition T + Q (Q affine): theta = y2 Z - Y, eta = x2 Z - X
@@ -73,6 +73,12 @@ ACE_HD F12 operator*(const F12& a, const F12& b) {
     F6 t0 = a.c0 * b.c0, t1 = a.c1 * b.c1;
     F6 t2 = (a.c0 + a.c1) * (b.c0 + b.c1);
     return {t0 + mul_v(t1), t2 - t0 - t1};
+}
+// (a0 + a1 w)^2 = (a0 + a1)(a0 + v a1) - a0 a1 - v a0 a1 + 2 a0 a1 w: two Fp6 products
+ACE_HD F12 f12_sqr(const F12& a) {
+    F6 t = a.c0 * a.c1;
+    F6 u = (a.c0 + a.c1) * (a.c0 + mul_v(a.c1));
+    return {u - t - mul_v(t), t + t};
 }
 ACE_HD F12 f12_conj(const F12& a) { return {a.c0, f6_neg(a.c1)}; }
 ACE_HD F12 f12_inv(const F12& a) {
@@ -158,7 +164,7 @@ ACE_HD bool miller_proj(const fp_t& xp, const fp_t& yp, const F2& qx, const F2& 
     int top = 64;
     while (top > 0 && !(top >= 64 ? (k.ate_hi >> (top - 64)) & 1u : (k.ate_lo >> top) & 1u)) top--;
     for (int i = top - 1; i >= 0; i--) {
-        f = f * f;
+        f = f12_sqr(f);
         miller_dbl(f, T, xp, yp, k);
         const uint64_t bit = i >= 64 ? (k.ate_hi >> (i - 64)) & 1u : (k.ate_lo >> i) & 1u;
         if (bit && !miller_add(f, T, qx, qy, xp, yp)) return false;

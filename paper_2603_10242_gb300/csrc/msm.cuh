@@ -8,8 +8,10 @@
 //   2. counting sort of (bucket, point) pairs: histogram, exclusive scan,
 //      scatter;
 //   3. one mixed XYZZ addition per entry into its bucket;
-//   4. per window sum_b b S_b: running sums over segments of L buckets, then a
-//      binary tree over segments whose right child is weighted by 2^level L;
+//   4. per window sum_b b S_b: running sums over segments of L = 16 buckets
+//      give W_j (weights 1..L inside segment j) and S_j; one thread per
+//      segment adds j L S_j to W_j (at most c - 1 doublings), and block-wide
+//      trees sum the M segments of every window (256 to 1 per pass);
 //   5. Horner over windows (c doublings each) plus the ones-window total.
 // With precomputed window tables of the bases (the proving key's queries),
 // every window's digits share one bucket set and step 5 is a single sum.

@@ -68,7 +68,7 @@ static MsmPlan plan_for(size_t n, int c, bool tabled) {
     p.c = c;
     p.K = (255 + p.c - 1) / p.c;
     p.B = 1u << (p.c - 1);
-    p.lambda = p.c - 1 < 5 ? p.c - 1 : 5;
+    p.lambda = p.c - 1 < 4 ? p.c - 1 : 4;  // segments of 16 buckets
     p.L = 1u << p.lambda;
     p.M = p.B / p.L;
     p.tabled = tabled;

@@ -66,6 +66,9 @@ size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont) {
 // (ACE_BUCKET_MIN_BLOCKS: resident blocks of 128 threads per SM the compiler
 // must allow, which caps the registers per thread)
 // ---------------------------------------------------------------------------
+#ifndef ACE_MADD_PAIRS
+#define ACE_MADD_PAIRS 0  // 1: G1 mixed additions as five calls of paired products
+#endif
 #ifndef ACE_BUCKET_MIN_BLOCKS
 #define ACE_BUCKET_MIN_BLOCKS 1
 #endif
@@ -84,7 +87,12 @@ __global__ void __launch_bounds__(128, ACE_BUCKET_MIN_BLOCKS) k_bucket_acc(const
         uint32_t v = __ldg(entries + t);
         Affine<F> p = ld_vec(bases + (v & 0x7fffffffu));
         if (v >> 31) p.y = fe_neg(p.y);
+#if ACE_MADD_PAIRS
+        if constexpr (sizeof(F) == sizeof(fp_t)) acc = xyzz_add_aff_pairs(acc, p);
+        else acc = xyzz_add_aff(acc, p);
+#else
         acc = xyzz_add_aff(acc, p);
+#endif
     }
     st_vec(buckets + key, acc);
 }
@@ -109,48 +117,69 @@ __global__ void __launch_bounds__(128) k_seg_reduce(const Xyzz<F>* __restrict__ 
     st_vec(segS + t, run);
 }
 
-// level: combine slots (j 2^(lev+1)) and (j 2^(lev+1) + 2^lev) of every window:
-// W = W_l + W_r + 2^(lev + lambda) S_r, S = S_l + S_r
+// weighted segment values: bucket b of a window carries weight b + 1, so
+// segment j (buckets jL .. jL + L - 1) contributes W_j + j L S_j; the ones
+// window contributes its plain sum S_j.  P_j overwrites W_j.  One thread per
+// segment: j L S_j by double-and-add (at most c - 1 doublings).
 template <class F>
-__global__ void __launch_bounds__(128) k_tree_level(Xyzz<F>* W, Xyzz<F>* S, uint32_t windows, uint32_t M,
-                                                    int lev, int lambda) {
-    uint32_t pairs = M >> (lev + 1);
+__global__ void __launch_bounds__(128) k_seg_weight(Xyzz<F>* W, const Xyzz<F>* __restrict__ S, uint32_t nseg,
+                                                    uint32_t M, int lambda, uint32_t windows, uint32_t ones) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= windows * pairs) return;
-    uint32_t w = t / pairs, j = t % pairs;
-    size_t l = (size_t)w * M + ((size_t)j << (lev + 1));
-    size_t r = l + ((size_t)1 << lev);
-    Xyzz<F> sr = ld_plain(S + r);
-    Xyzz<F> sh = sr;
-    for (int k = 0; k < lev + lambda; k++) sh = xyzz_dbl(sh);
-    Xyzz<F> wl = ld_plain(W + l);
-    wl = xyzz_add(wl, ld_plain(W + r));
-    wl = xyzz_add(wl, sh);
-    st_vec(W + l, wl);
-    st_vec(S + l, xyzz_add(ld_plain(S + l), sr));
+    if (t >= nseg) return;
+    const uint32_t w = t / M, j = t % M;
+    Xyzz<F> s = ld_plain(S + t);
+    if (w % windows == ones) {
+        st_vec(W + t, s);
+        return;
+    }
+    Xyzz<F> acc = ld_plain(W + t);
+    if (j != 0) {
+        Xyzz<F> m = xyzz_inf<F>();
+        for (int b = 31 - __clz(j); b >= 0; b--) {
+            m = xyzz_dbl(m);
+            if ((j >> b) & 1u) m = xyzz_add(m, s);
+        }
+        for (int k = 0; k < lambda; k++) m = xyzz_dbl(m);
+        acc = xyzz_add(acc, m);
+    }
+    st_vec(W + t, acc);
 }
 
-// Horner over the K digit windows, plus the ones-window total; one thread
-// per MSM of a batch (its windows follow the previous MSM's: K + 1 of them)
+// out[g nb + b] = sum of in[g n + 256 b .. g n + 256 b + 255] (within n),
+// nb = ceil(n / 256): block (b, g), 128 threads, a tree in shared memory
 template <class F>
-__global__ void k_msm_final(const Xyzz<F>* W, const Xyzz<F>* S, uint32_t K, uint32_t M, int c, uint32_t batch,
-                            Xyzz<F>* res, Affine<F>* out) {
+__global__ void __launch_bounds__(128) k_group_sum(const Xyzz<F>* __restrict__ in, uint32_t n, Xyzz<F>* out) {
+    __shared__ Xyzz<F> sh[128];
+    const uint32_t g = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+    const uint32_t i0 = 256 * b + threadIdx.x, i1 = i0 + 128;
+    Xyzz<F> v = i0 < n ? ld_plain(in + (size_t)g * n + i0) : xyzz_inf<F>();
+    if (i1 < n) v = xyzz_add(v, ld_plain(in + (size_t)g * n + i1));
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (uint32_t h = 64; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] = xyzz_add(sh[threadIdx.x], sh[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st_vec(out + (size_t)g * nb + b, sh[0]);
+}
+
+// Horner over the K digit windows' totals, plus the ones-window total; one
+// thread per MSM of a batch (T holds K + 1 totals per MSM)
+template <class F>
+__global__ void k_msm_final(const Xyzz<F>* T, uint32_t K, int c, uint32_t batch, Xyzz<F>* res, Affine<F>* out) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= batch) return;
-    W += (size_t)q * (K + 1) * M;
-    S += (size_t)q * (K + 1) * M;
-    if (res) res += q;
-    if (out) out += q;
-    Xyzz<F> acc = ld_plain(W + (size_t)(K - 1) * M);
+    T += (size_t)q * (K + 1);
+    Xyzz<F> acc = ld_plain(T + (K - 1));
     for (int w = (int)K - 2; w >= 0; w--) {
         for (int k = 0; k < c; k++) acc = xyzz_dbl(acc);
-        acc = xyzz_add(acc, ld_plain(W + (size_t)w * M));
+        acc = xyzz_add(acc, ld_plain(T + w));
     }
-    acc = xyzz_add(acc, ld_plain(S + (size_t)K * M));
-    if (res) st_vec(res, acc);
+    acc = xyzz_add(acc, ld_plain(T + K));
+    if (res) st_vec(res + q, acc);
     if (out) {
         Affine<F> a = aff_from_mont(xyzz_to_aff(acc));
-        st_vec(out, a);
+        st_vec(out + q, a);
     }
 }
 
@@ -230,14 +259,21 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     uint32_t nseg = plan.all_windows() * plan.M;
     int prof_red = prof_begin(PROF_REDUCE, st);
     k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS); ::ace::note_launch();
-    for (int lev = 0; (1u << lev) < plan.M; lev++) {
-        uint32_t pairs = plan.all_windows() * (plan.M >> (lev + 1));
-        k_tree_level<F><<<(pairs + 127) / 128, 128, 0, st>>>(b.segW, b.segS, plan.all_windows(), plan.M, lev,
-                                                             plan.lambda); ::ace::note_launch();
+    k_seg_weight<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.segW, b.segS, nseg, plan.M, plan.lambda, plan.windows(),
+                                                        plan.bucket_windows()); ::ace::note_launch();
+    // sum each window's M weighted segments: 256 to 1 per pass, ping-pong
+    // between the two segment arrays
+    Xyzz<F>*src = b.segW, *dst = b.segS;
+    for (uint32_t n = plan.M; n > 1;) {
+        uint32_t nb = (n + 255) / 256;
+        k_group_sum<F><<<dim3(nb, plan.all_windows()), 128, 0, st>>>(src, n, dst); ::ace::note_launch();
+        Xyzz<F>* t = src;
+        src = dst;
+        dst = t;
+        n = nb;
     }
-    k_msm_final<F><<<(plan.batch + 31) / 32, 32, 0, st>>>(b.segW, b.segS, plan.bucket_windows(), plan.M, plan.c,
-                                                           plan.batch, d_res, d_out); ::ace::note_launch();
-    prof_end(prof_red, st, nullptr, (uint64_t)plan.windows() * plan.B);
+    k_msm_final<F><<<(plan.batch + 31) / 32, 32, 0, st>>>(src, plan.bucket_windows(), plan.c, plan.batch, d_res, d_out); ::ace::note_launch();
+    prof_end(prof_red, st, nullptr, (uint64_t)plan.keys());
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

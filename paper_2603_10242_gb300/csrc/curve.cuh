@@ -124,33 +124,6 @@ ACE_HD Xyzz<F> xyzz_add_aff(const Xyzz<F>& p, const Affine<F>& q) {
     return r;
 }
 
-#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
-// The same mixed addition on G1 with its ten products issued as five calls
-// of two independent products each: (U2, S2), (P^2, R^2), (P PP, X1 PP),
-// (R (Q - X3), Y1 PPP), (ZZ1 PP, ZZZ1 PPP).
-__device__ __forceinline__ g1_xyzz xyzz_add_aff_pairs(const g1_xyzz& p, const g1_aff& q) {
-    if (aff_is_inf(q)) return p;
-    if (xyzz_is_inf(p)) return xyzz_from_aff(q);
-    FePair<FpCfg> u = d_mul2_call<FpCfg>(q.x, p.ZZ, q.y, p.ZZZ);
-    fp_t P = u.a - p.X;
-    fp_t R = u.b - p.Y;
-    if (fe_is_zero(P)) {
-        if (fe_is_zero(R)) return xyzz_dbl_aff(q);
-        return xyzz_inf<fp_t>();
-    }
-    FePair<FpCfg> sq = d_sqr2_call<FpCfg>(P, R);  // PP, R^2
-    FePair<FpCfg> t = d_mul2_call<FpCfg>(P, sq.a, p.X, sq.a);  // PPP, Q
-    g1_xyzz r;
-    r.X = sq.b - t.a - fe_dbl(t.b);
-    FePair<FpCfg> v = d_mul2_call<FpCfg>(R, t.b - r.X, p.Y, t.a);
-    r.Y = v.a - v.b;
-    FePair<FpCfg> w = d_mul2_call<FpCfg>(p.ZZ, sq.a, p.ZZZ, t.a);
-    r.ZZ = w.a;
-    r.ZZZ = w.b;
-    return r;
-}
-#endif
-
 // P + Q (add-2008-s)
 template <class F>
 ACE_HD Xyzz<F> xyzz_add(const Xyzz<F>& p, const Xyzz<F>& q) {

@@ -932,32 +932,6 @@ __device__ __noinline__ Fe<C> d_mul_call(const Fe<C> a, const Fe<C> b) {
 }
 #endif
 
-#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
-// Two independent products (or squares) in one out-of-line call: the two
-// instruction streams interleave, doubling the work a warp has in flight.
-template <class C>
-struct FePair {
-    Fe<C> a, b;
-};
-template <class C>
-__device__ __noinline__ FePair<C> d_mul2_call(const Fe<C> a1, const Fe<C> b1, const Fe<C> a2, const Fe<C> b2) {
-    FePair<C> r;
-    d_mul_form<C>(r.a.v, a1.v, b1.v);
-    d_mul_form<C>(r.b.v, a2.v, b2.v);
-    return r;
-}
-template <class C>
-__device__ __noinline__ FePair<C> d_sqr2_call(const Fe<C> a1, const Fe<C> a2) {
-    FePair<C> r;
-    uint32_t t1[16], t2[16];
-    d_sqr512(t1, a1.v);
-    d_sqr512(t2, a2.v);
-    d_redc512<C>(r.a.v, t1);
-    d_redc512<C>(r.b.v, t2);
-    return r;
-}
-#endif
-
 template <class C>
 ACE_HD Fe<C> operator*(const Fe<C>& a, const Fe<C>& b) {
 #if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)

@@ -66,9 +66,6 @@ size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont) {
 // (ACE_BUCKET_MIN_BLOCKS: resident blocks of 128 threads per SM the compiler
 // must allow, which caps the registers per thread)
 // ---------------------------------------------------------------------------
-#ifndef ACE_MADD_PAIRS
-#define ACE_MADD_PAIRS 0  // 1: G1 mixed additions as five calls of paired products
-#endif
 #ifndef ACE_BUCKET_MIN_BLOCKS
 #define ACE_BUCKET_MIN_BLOCKS 1
 #endif
@@ -87,12 +84,7 @@ __global__ void __launch_bounds__(128, ACE_BUCKET_MIN_BLOCKS) k_bucket_acc(const
         uint32_t v = __ldg(entries + t);
         Affine<F> p = ld_vec(bases + (v & 0x7fffffffu));
         if (v >> 31) p.y = fe_neg(p.y);
-#if ACE_MADD_PAIRS
-        if constexpr (sizeof(F) == sizeof(fp_t)) acc = xyzz_add_aff_pairs(acc, p);
-        else acc = xyzz_add_aff(acc, p);
-#else
         acc = xyzz_add_aff(acc, p);
-#endif
     }
     st_vec(buckets + key, acc);
 }

@@ -483,6 +483,10 @@ def run_batch_workload(args):
     rss = [ace.rs_from_seed(base + i) for i in range(k)]
     rs = b"".join(r for r, _ in rss)
     ss = b"".join(s_ for _, s_ in rss)
+    # proving slots from the autotuner, timed on the median-size proof
+    mid = sorted(range(k), key=lambda i: sizes[i][1])[k // 2]
+    slot_ms = ctx.autotune_batch_slots(pks[mid], dzs[mid], 8, 4)
+    slots = 1 + min(range(len(slot_ms)), key=lambda q: slot_ms[q])
     ctx.prove_batch(pks, dzs, rs, ss)            # warm-up (sizes the slots)
     for i in range(k):
         ctx.prove(pks[i], dzs[i], *rss[i])
@@ -503,7 +507,7 @@ def run_batch_workload(args):
                       "log_n_hist": {str(l): sum(1 for p in sizes if p[0] == l) for l in range(12, 19)},
                       "batched_proofs_per_s": k / best_b, "plain_proofs_per_s": k / best_p,
                       "batched_constraints_per_s": rows / best_b, "setup_s": setup_s, "verified": ok,
-                      "batch_slots": 2}))
+                      "batch_slots": slots}))
 
 
 # per-transaction circuit: 5 permutations (the commitment and key-derivation

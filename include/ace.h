@@ -341,10 +341,11 @@ int ace_server_destroy(ace_server* srv);
  * with the given arrival time, run time and memory on `slots` slots and a
  * memory budget; returns each job's start / finish time and status (0, -2
  * never fits, -6 timed out) and peaks[0] = most jobs running at once,
- * peaks[1] = most memory admitted at once. */
+ * peaks[1] = most memory admitted at once; prio_out (optional): each job's
+ * stream-priority level (jobs already running when it started). */
 int ace_debug_scheduler_sim(int slots, size_t budget, size_t n, const double* arrival, const double* duration,
                             const size_t* mem, double max_wait, double* start_out, double* finish_out,
-                            int32_t* status_out, uint64_t* peaks);
+                            int32_t* status_out, uint64_t* peaks, int32_t* prio_out);
 
 /* Witnesses of k instances of circuit c on the device, instance q from input
  * seed seeds[q] (host array): the same values, in the same order, as

@@ -93,7 +93,7 @@ def lib():
             "ace_server_stats": (i32, [vp, ctypes.POINTER(u64)]),
             "ace_server_destroy": (i32, [vp]),
             "ace_debug_scheduler_sim": (i32, [i32, sz, sz, vp, vp, vp, ctypes.c_double, vp, vp, vp,
-                                              ctypes.POINTER(u64)]),
+                                              ctypes.POINTER(u64), vp]),
             "ace_debug_imad_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "ace_debug_chain_latency": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
             "ace_debug_mul_rate": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -485,5 +485,6 @@ def scheduler_sim(slots: int, budget: int, arrival, duration, mem, max_wait: flo
     st, fi = (ctypes.c_double * n)(), (ctypes.c_double * n)()
     status = (ctypes.c_int32 * n)()
     peaks = (ctypes.c_uint64 * 2)()
-    check(lib().ace_debug_scheduler_sim(slots, budget, n, A, D, M, max_wait, st, fi, status, peaks))
-    return list(st), list(fi), list(status), (int(peaks[0]), int(peaks[1]))
+    prio = (ctypes.c_int32 * n)()
+    check(lib().ace_debug_scheduler_sim(slots, budget, n, A, D, M, max_wait, st, fi, status, peaks, prio))
+    return list(st), list(fi), list(status), (int(peaks[0]), int(peaks[1])), list(prio)

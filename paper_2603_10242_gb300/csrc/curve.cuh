@@ -76,7 +76,7 @@ ACE_HD Xyzz<F> xyzz_dbl_aff(const Affine<F>& p) {
     F M = fe_dbl(xx) + xx;
     Xyzz<F> r;
     r.X = fe_sqr(M) - fe_dbl(S);
-    r.Y = M * (S - r.X) - W * p.y;
+    r.Y = fe_mul_sub(M, S - r.X, W, p.y);
     r.ZZ = V;
     r.ZZZ = W;
     return r;
@@ -94,7 +94,7 @@ ACE_HD Xyzz<F> xyzz_dbl(const Xyzz<F>& p) {
     F M = fe_dbl(xx) + xx;
     Xyzz<F> r;
     r.X = fe_sqr(M) - fe_dbl(S);
-    r.Y = M * (S - r.X) - W * p.Y;
+    r.Y = fe_mul_sub(M, S - r.X, W, p.Y);
     r.ZZ = V * p.ZZ;
     r.ZZZ = W * p.ZZZ;
     return r;
@@ -118,7 +118,7 @@ ACE_HD Xyzz<F> xyzz_add_aff(const Xyzz<F>& p, const Affine<F>& q) {
     F Q = p.X * PP;
     Xyzz<F> r;
     r.X = fe_sqr(R) - PPP - fe_dbl(Q);
-    r.Y = R * (Q - r.X) - p.Y * PPP;
+    r.Y = fe_mul_sub(R, Q - r.X, p.Y, PPP);
     r.ZZ = p.ZZ * PP;
     r.ZZZ = p.ZZZ * PPP;
     return r;
@@ -144,7 +144,7 @@ ACE_HD Xyzz<F> xyzz_add(const Xyzz<F>& p, const Xyzz<F>& q) {
     F Q = U1 * PP;
     Xyzz<F> r;
     r.X = fe_sqr(R) - PPP - fe_dbl(Q);
-    r.Y = R * (Q - r.X) - S1 * PPP;
+    r.Y = fe_mul_sub(R, Q - r.X, S1, PPP);
     r.ZZ = p.ZZ * q.ZZ * PP;
     r.ZZZ = p.ZZZ * q.ZZZ * PPP;
     return r;

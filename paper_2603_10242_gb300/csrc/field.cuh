@@ -846,6 +846,29 @@ ACE_DEV uint32_t d_sub512(uint32_t (&a)[16], const uint32_t (&b)[16]) {
           "r"(b[9]), "r"(b[10]), "r"(b[11]), "r"(b[12]), "r"(b[13]), "r"(b[14]), "r"(b[15]));
     return br;
 }
+// a += b over 16 limbs (modulo 2^512)
+ACE_DEV void d_add512(uint32_t (&a)[16], const uint32_t (&b)[16]) {
+    asm("add.cc.u32 %0, %0, %16;\n\t"
+        "addc.cc.u32 %1, %1, %17;\n\t"
+        "addc.cc.u32 %2, %2, %18;\n\t"
+        "addc.cc.u32 %3, %3, %19;\n\t"
+        "addc.cc.u32 %4, %4, %20;\n\t"
+        "addc.cc.u32 %5, %5, %21;\n\t"
+        "addc.cc.u32 %6, %6, %22;\n\t"
+        "addc.cc.u32 %7, %7, %23;\n\t"
+        "addc.cc.u32 %8, %8, %24;\n\t"
+        "addc.cc.u32 %9, %9, %25;\n\t"
+        "addc.cc.u32 %10, %10, %26;\n\t"
+        "addc.cc.u32 %11, %11, %27;\n\t"
+        "addc.cc.u32 %12, %12, %28;\n\t"
+        "addc.cc.u32 %13, %13, %29;\n\t"
+        "addc.cc.u32 %14, %14, %30;\n\t"
+        "addc.u32 %15, %15, %31;\n\t"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+          "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]),
+          "r"(b[9]), "r"(b[10]), "r"(b[11]), "r"(b[12]), "r"(b[13]), "r"(b[14]), "r"(b[15]));
+}
 // a[8..15] += m & mask (adds m 2^256 when mask is all ones)
 template <class C>
 ACE_DEV void d_add_hi_mod(uint32_t (&a)[16], uint32_t mask) {
@@ -976,6 +999,40 @@ ACE_HD Fe<C> fe_sqr(const Fe<C>& a) {
     return a * a;
 #endif
 }
+// a b - c d with a single Montgomery reduction on the device: both products
+// stay at 512 bits, their difference (in (-m^2, m^2)) is made non-negative by
+// adding m 2^256 when it borrows, and one reduction gives the result.
+#if defined(__CUDA_ARCH__)
+template <class C>
+ACE_DEV void d_mul_sub(uint32_t* r, const uint32_t* a, const uint32_t* b, const uint32_t* c, const uint32_t* d) {
+    uint32_t t1[16], t2[16];
+    d_mul512(t1, a, b);
+    d_mul512(t2, c, d);
+    uint32_t br = d_sub512(t1, t2);
+    d_add_hi_mod<C>(t1, br);
+    d_redc512<C>(r, t1);
+}
+#if defined(ACE_FIELD_MUL_CALL)
+template <class C>
+__device__ __noinline__ Fe<C> d_mul_sub_call(const Fe<C> a, const Fe<C> b, const Fe<C> c, const Fe<C> d) {
+    Fe<C> r;
+    d_mul_sub<C>(r.v, a.v, b.v, c.v, d.v);
+    return r;
+}
+#endif
+#endif
+template <class C>
+ACE_HD Fe<C> fe_mul_sub(const Fe<C>& a, const Fe<C>& b, const Fe<C>& c, const Fe<C>& d) {
+#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
+    return d_mul_sub_call<C>(a, b, c, d);
+#elif defined(__CUDA_ARCH__)
+    Fe<C> r;
+    d_mul_sub<C>(r.v, a.v, b.v, c.v, d.v);
+    return r;
+#else
+    return a * b - c * d;
+#endif
+}
 template <class C>
 ACE_HD Fe<C> fe_dbl(const Fe<C>& a) { return a + a; }
 template <class C>
@@ -1072,6 +1129,60 @@ ACE_HD fp2_t fe_sqr(const fp2_t& a) {
     // (a0 + a1)(a0 - a1) + 2 a0 a1 u
     fp_t t = a.c0 * a.c1;
     return {(a.c0 + a.c1) * (a.c0 - a.c1), t + t};
+}
+// a b - c d in Fp2 with two reductions (instead of four): each coefficient's
+// true value lies in (-2p^2, 2p^2), so the 512-bit two's-complement
+// combination of the six unreduced products is exact; a negative one gets
+// p 2^256 added (2 p^2 < p 2^256) before the reduction.
+#if defined(__CUDA_ARCH__)
+ACE_DEV void d_fp2_mul_sub(fp2_t& r, const fp2_t& a, const fp2_t& b, const fp2_t& c, const fp2_t& d) {
+    // products P0 = a0 b0, P1 = a1 b1, P2 = (a0 + a1)(b0 + b1), Q0, Q1, Q2 the
+    // same for c, d:  c0 = P0 - P1 - Q0 + Q1,  c1 = P2 - P0 - P1 - Q2 + Q0 + Q1
+    uint32_t x[16], y[16], t[16], sa[8], sb[8];
+    d_mul512(x, a.c0.v, b.c0.v);
+#pragma unroll
+    for (int i = 0; i < 16; i++) y[i] = 0;
+    d_sub512(y, x);
+    d_mul512(t, a.c1.v, b.c1.v);
+    d_sub512(x, t);
+    d_sub512(y, t);
+    d_add_raw(sa, a.c0.v, a.c1.v);
+    d_add_raw(sb, b.c0.v, b.c1.v);
+    d_mul512(t, sa, sb);
+    d_add512(y, t);
+    d_mul512(t, c.c0.v, d.c0.v);
+    d_sub512(x, t);
+    d_add512(y, t);
+    d_mul512(t, c.c1.v, d.c1.v);
+    d_add512(x, t);
+    d_add512(y, t);
+    d_add_raw(sa, c.c0.v, c.c1.v);
+    d_add_raw(sb, d.c0.v, d.c1.v);
+    d_mul512(t, sa, sb);
+    d_sub512(y, t);
+    d_add_hi_mod<FpCfg>(x, 0u - (x[15] >> 31));
+    d_add_hi_mod<FpCfg>(y, 0u - (y[15] >> 31));
+    d_redc512<FpCfg>(r.c0.v, x);
+    d_redc512<FpCfg>(r.c1.v, y);
+}
+#if defined(ACE_FIELD_MUL_CALL)
+static __device__ __noinline__ fp2_t d_fp2_mul_sub_call(const fp2_t a, const fp2_t b, const fp2_t c, const fp2_t d) {
+    fp2_t r;
+    d_fp2_mul_sub(r, a, b, c, d);
+    return r;
+}
+#endif
+#endif
+ACE_HD fp2_t fe_mul_sub(const fp2_t& a, const fp2_t& b, const fp2_t& c, const fp2_t& d) {
+#if defined(__CUDA_ARCH__) && defined(ACE_FIELD_MUL_CALL)
+    return d_fp2_mul_sub_call(a, b, c, d);
+#elif defined(__CUDA_ARCH__)
+    fp2_t r;
+    d_fp2_mul_sub(r, a, b, c, d);
+    return r;
+#else
+    return a * b - c * d;
+#endif
 }
 ACE_HD fp2_t fe_dbl(const fp2_t& a) { return {a.c0 + a.c0, a.c1 + a.c1}; }
 ACE_HD fp2_t fe_neg(const fp2_t& a) { return {fe_neg(a.c0), fe_neg(a.c1)}; }

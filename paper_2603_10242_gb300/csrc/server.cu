@@ -332,7 +332,7 @@ struct SimExecutor {
 
 extern "C" int ace_debug_scheduler_sim(int slots, size_t budget, size_t n, const double* arrival,
                                        const double* duration, const size_t* mem, double max_wait, double* start_out,
-                                       double* finish_out, int32_t* status_out, uint64_t* peaks) {
+                                       double* finish_out, int32_t* status_out, uint64_t* peaks, int32_t* prio_out) {
     if (slots < 1 || !arrival || !duration || !mem || !start_out || !finish_out || !status_out || !peaks)
         return ACE_E_ARG;
     SimClock clock;
@@ -370,6 +370,7 @@ extern "C" int ace_debug_scheduler_sim(int slots, size_t budget, size_t n, const
         start_out[i] = jobs[i].start;
         finish_out[i] = jobs[i].finish;
         status_out[i] = jobs[i].status;
+        if (prio_out) prio_out[i] = jobs[i].prio;
     }
     peaks[0] = (uint64_t)sched.peak_running();
     peaks[1] = sched.peak_used();

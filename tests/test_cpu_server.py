@@ -16,7 +16,7 @@ def _lib():
 
 def test_fifo_and_slot_cap():
     n = 10
-    st, fi, status, peaks = ace.scheduler_sim(2, 10**12, [0.0] * n, [1.0] * n, [1] * n)
+    st, fi, status, peaks, _ = ace.scheduler_sim(2, 10**12, [0.0] * n, [1.0] * n, [1] * n)
     assert status == [0] * n
     assert st == [0, 0, 1, 1, 2, 2, 3, 3, 4, 4]
     assert fi == [s + 1 for s in st]
@@ -25,13 +25,13 @@ def test_fifo_and_slot_cap():
 
 def test_memory_budget_limits_concurrency():
     n = 6
-    st, fi, status, peaks = ace.scheduler_sim(3, 10, [0.0] * n, [1.0] * n, [6] * n)
+    st, fi, status, peaks, _ = ace.scheduler_sim(3, 10, [0.0] * n, [1.0] * n, [6] * n)
     assert status == [0] * n and peaks[0] == 1 and peaks[1] == 6
     assert st == [0, 1, 2, 3, 4, 5]
 
 
 def test_queue_deadline_and_never_fits():
-    st, fi, status, _ = ace.scheduler_sim(1, 100, [0.0, 0.0, 0.1, 5.0], [1.0, 1.0, 1.0, 1.0], [10, 10, 10, 500],
+    st, fi, status, _, _ = ace.scheduler_sim(1, 100, [0.0, 0.0, 0.1, 5.0], [1.0, 1.0, 1.0, 1.0], [10, 10, 10, 500],
                                           max_wait=0.5)
     assert status[0] == 0 and st[0] == 0
     assert status[1] == -6 and status[2] == -6          # could not start within 0.5 s
@@ -48,7 +48,7 @@ def test_random_load_invariants():
         arr.append(t)
         dur.append(rng.uniform(0.05, 1.2))
         mem.append(rng.randint(10, 60))
-    st, fi, status, peaks = ace.scheduler_sim(slots, budget, arr, dur, mem, max_wait=3.0)
+    st, fi, status, peaks, prio = ace.scheduler_sim(slots, budget, arr, dur, mem, max_wait=3.0)
     ran = [i for i in range(n) if status[i] == 0]
     assert len(ran) > n // 2
     for i in ran:
@@ -63,3 +63,19 @@ def test_random_load_invariants():
         assert len(live) <= slots
         assert sum(mem[j] for j in live) <= budget
     assert peaks[0] <= slots and peaks[1] <= budget
+    # a job's stream-priority level is the number of jobs running when it
+    # started (jobs started at the same instant count if admitted before it)
+    for i in ran:
+        running = [j for j in ran if (st[j] < st[i] or (st[j] == st[i] and j < i)) and st[i] < fi[j]]
+        assert prio[i] == len(running)
+
+
+def test_priority_levels_follow_admission_order():
+    # three overlapping jobs on three slots get levels 0, 1, 2; a job that
+    # starts on an idle device gets level 0 again
+    st, fi, status, _, prio = ace.scheduler_sim(3, 10**12, [0.0, 0.1, 0.2, 5.0], [1.0, 1.0, 1.0, 1.0], [1, 1, 1, 1])
+    assert status == [0, 0, 0, 0]
+    assert prio == [0, 1, 2, 0]
+    # the first job finishes before the fourth of a busy stream starts: two running
+    st, fi, status, _, prio = ace.scheduler_sim(3, 10**12, [0.0, 0.1, 0.2, 1.05], [1.0, 1.0, 1.0, 1.0], [1] * 4)
+    assert prio == [0, 1, 2, 2]

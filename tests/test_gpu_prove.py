@@ -142,6 +142,12 @@ def test_block_scale_proof_in_the_exponent(log_n):
     opk = O.ProvingKey(oc, 2, with_points=False)
     assert proof == opk.expected_proof(z, r, s)
     assert opk.verify(int.from_bytes(z[32:64], "little"), proof) == 1
+    # the bench's launch configuration: proofs pipelined over proving slots
+    dz = gu.dev(z)
+    rss = [ace.rs_from_seed(50 + i) for i in range(3)] + [(r, s)]
+    proofs, status = ctx.prove_batch([pk] * 4, [dz] * 4, b"".join(a for a, _ in rss), b"".join(b for _, b in rss))
+    assert status == [0] * 4 and proofs[3] == proof
+    assert proofs[1] == opk.expected_proof(z, *rss[1])
     # sampled setup points at full size
     g1 = O.g1_generator()
     for j in (2, lc.m // 3, lc.m - 1):

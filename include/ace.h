@@ -269,6 +269,11 @@ int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[3
  * (homogeneous projective, the loop the batch verifier runs on the device),
  * computed on the host. */
 int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
+/* Host: the GLV split the prover uses for s S_A + r S_B1: k = k1 + k2 lambda
+ * (mod r), lambda = 0xb3c4d79d41a917585bfc41088d8daaa78b17ea66b99c90dd, a
+ * cube root of unity with (beta x, y) = lambda (x, y) on G1.  out[0..3] = |k1|,
+ * out[4] = 1 if k1 < 0, out[5..8] = |k2|, out[9] = 1 if k2 < 0 (|k_i| < 2^128). */
+int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]);
 /* Measured 32-bit multiply-add throughput of the device (operations/s):
  * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs, 3 mad.wide.u32
  * (one 32 x 32 -> 64-bit limb product with 64-bit accumulate per operation). */

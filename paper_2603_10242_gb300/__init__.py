@@ -81,6 +81,7 @@ def lib():
             "ace_witness_many": (i32, [vp, vp, sz, vp, vp, vp]),
             "ace_verify_batch": (i32, [vp, vp, sz, cp, cp, u64]),
             "ace_debug_pairing_form": (i32, [i32, cp, cp, cp]),
+            "ace_debug_glv_split": (i32, [cp, vp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
             "ace_autotune_batch_slots": (i32, [vp, vp, vp, i32, i32, vp]),

@@ -40,6 +40,8 @@ struct MsmPlan {
     // scalars (scalars and results laid out one MSM after another) and its
     // own bucket sets; every reduction step runs over all of them at once
     uint32_t batch = 1;
+    // most threads one bucket's entries may be split among (1: no split)
+    uint32_t max_split = 16;
     uint32_t bucket_windows() const { return tabled ? 1u : (uint32_t)K; }
     uint32_t windows() const { return bucket_windows() + 1; }  // + ones window
     uint32_t keys_per() const { return windows() * B; }         // keys of one MSM
@@ -66,6 +68,7 @@ struct MsmBufs {
     uint32_t* order;     // keys, bucket keys by decreasing size
     uint32_t* size_bins; // SIZE_BINS + 1
     Xyzz<F>* buckets;    // keys
+    Xyzz<F>* partial;    // keys x split (split parts per bucket), or buckets itself
     Xyzz<F>* segW;       // windows M
     Xyzz<F>* segS;       // windows M
     Affine<F>* conv;     // n (only when bases arrive canonical)

@@ -35,6 +35,9 @@ __device__ __forceinline__ T ld_plain(const T* p) {
     return r;
 }
 
+template <class F>
+uint32_t bucket_split(const MsmPlan& p);
+
 template <class F, class A>
 template <class Alloc>
 bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
@@ -46,10 +49,12 @@ bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
     order = (uint32_t*)a.take(keys * 4);
     size_bins = (uint32_t*)a.take((SIZE_BINS + 1) * 4);
     buckets = (Xyzz<F>*)a.take(keys * sizeof(Xyzz<F>));
+    const uint32_t split = bucket_split<F>(p);
+    partial = split > 1 ? (Xyzz<F>*)a.take(keys * split * sizeof(Xyzz<F>)) : buckets;
     segW = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
     segS = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
     conv = need_conv ? (Affine<F>*)a.take(p.n * sizeof(Affine<F>)) : nullptr;
-    return offsets && cursor && scan_tmp && entries && order && size_bins && buckets && segW && segS &&
+    return offsets && cursor && scan_tmp && entries && order && size_bins && buckets && partial && segW && segS &&
            (!need_conv || conv);
 }
 
@@ -74,19 +79,57 @@ __global__ void __launch_bounds__(128, ACE_BUCKET_MIN_BLOCKS) k_bucket_acc(const
                                                     const uint32_t* __restrict__ entries,
                                                     const uint32_t* __restrict__ offsets,
                                                     const uint32_t* __restrict__ order, uint32_t nkeys,
-                                                    Xyzz<F>* buckets) {
+                                                    uint32_t split, Xyzz<F>* out) {
+    // thread t adds part t % split of bucket order[t / split]; with split > 1
+    // the partial sums go to out[key split + part] (combined below)
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nkeys) return;
-    uint32_t key = __ldg(order + t);
-    uint32_t b = offsets[key], e = offsets[key + 1];
+    if (t >= nkeys * split) return;
+    const uint32_t rank = t / split, part = t - rank * split;
+    uint32_t key = __ldg(order + rank);
+    uint32_t b0 = offsets[key], e0 = offsets[key + 1];
+    uint32_t len = e0 - b0;
+    uint32_t b = b0 + (uint32_t)(((uint64_t)len * part) / split);
+    uint32_t e = b0 + (uint32_t)(((uint64_t)len * (part + 1)) / split);
     Xyzz<F> acc = xyzz_inf<F>();
-    for (uint32_t t = b; t < e; t++) {
-        uint32_t v = __ldg(entries + t);
+    for (uint32_t i = b; i < e; i++) {
+        uint32_t v = __ldg(entries + i);
         Affine<F> p = ld_vec(bases + (v & 0x7fffffffu));
         if (v >> 31) p.y = fe_neg(p.y);
         acc = xyzz_add_aff(acc, p);
     }
-    st_vec(buckets + key, acc);
+    st_vec(out + (size_t)key * split + part, acc);
+}
+
+// bucket = sum of its split partial sums (one thread per bucket)
+template <class F>
+__global__ void __launch_bounds__(128) k_bucket_combine(const Xyzz<F>* __restrict__ partial, uint32_t nkeys,
+                                                        uint32_t split, Xyzz<F>* buckets) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    Xyzz<F> acc = ld_plain(partial + (size_t)k * split);
+    for (uint32_t p = 1; p < split; p++) acc = xyzz_add(acc, ld_plain(partial + (size_t)k * split + p));
+    st_vec(buckets + k, acc);
+}
+
+// Parts per bucket: when the keys are too few to fill the GPU (fewer than 4
+// resident waves of the accumulation kernel) and the buckets are long, each
+// bucket's entries are split among 2..16 threads (at least ~8 entries each)
+// whose partial sums are then combined.  Entries per digit bucket are taken
+// as n K / 2^(c-1) (tabled) or n / 2^(c-1) (one set per window).
+template <class F>
+uint32_t bucket_split(const MsmPlan& p) {
+    static const double res = [] {
+        int dev = 0, sms = 0, nb = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bucket_acc<F>, 128, 0);
+        return (double)sms * (nb > 0 ? nb : 1) * 128.0;
+    }();
+    const double keys = (double)p.keys();
+    const double load = (double)p.n * (p.tabled ? p.K : 1) / (double)p.B;
+    uint32_t S = 1;
+    while (S < 16 && 2 * S <= p.max_split && keys * S < 4.0 * res && load / (2.0 * S) >= 8.0) S *= 2;
+    return S;
 }
 
 // ---------------------------------------------------------------------------
@@ -246,8 +289,13 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     ACE_TRY(bucket_order(b.offsets, keys, b.size_bins, b.scan_tmp, b.order, st));
     prof_end(prof_sort, st, nullptr, n);
     int prof = prof_begin(sizeof(F) == sizeof(fp_t) ? PROF_G1_BUCKET : PROF_G2_BUCKET, st);
-    k_bucket_acc<F><<<(keys + 127) / 128, 128, 0, st>>>(bases, b.entries, b.offsets, b.order, keys, b.buckets); ::ace::note_launch();
+    const uint32_t split = bucket_split<F>(plan);
+    k_bucket_acc<F><<<(unsigned)(((uint64_t)keys * split + 127) / 128), 128, 0, st>>>(bases, b.entries, b.offsets, b.order,
+                                                                              keys, split, b.partial); ::ace::note_launch();
     prof_end(prof, st, b.offsets + keys, 0);
+    if (split > 1) {
+        k_bucket_combine<F><<<(keys + 127) / 128, 128, 0, st>>>(b.partial, keys, split, b.buckets); ::ace::note_launch();
+    }
     uint32_t nseg = plan.all_windows() * plan.M;
     int prof_red = prof_begin(PROF_REDUCE, st);
     k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS); ::ace::note_launch();

@@ -754,6 +754,14 @@ int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_
     return ACE_OK;
 }
 
+int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]) {
+    if (!k || !out) return ACE_E_ARG;
+    fr_t x;
+    memcpy(x.v, k->l, 32);
+    if (fe_geq_mod(x)) return ACE_E_ARG;
+    return glv_split(x, out, &out[4], out + 5, &out[9]) ? ACE_OK : ACE_E_ARG;
+}
+
 int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, const ace_fr* rs, const ace_fr* ss,
                    uint8_t* proofs, int32_t* status) {
     clear_error();

@@ -152,3 +152,25 @@ def test_projective_miller_loop_matches_affine(lib):
     a, b = ctypes.create_string_buffer(384), ctypes.create_string_buffer(384)
     assert f(1, O.g1_mul(P, 2), Q, a) == 0 and f(1, P, O.g2_mul(Q, 2), b) == 0
     assert a.raw == b.raw
+
+
+def test_glv_split(lib):
+    """k = k1 + k2 lambda (mod r) with |k1|, |k2| < 2^128, and (beta x, y) =
+    lambda (x, y) on G1 for the constants the prover's split assumes."""
+    import random
+    lam = 0xb3c4d79d41a917585bfc41088d8daaa78b17ea66b99c90dd
+    beta = 0x59e26bcea0d48bacd4f263f1acdb5c4f5763473177fffffe
+    assert pow(lam, 3, Y.R) == 1 and lam != 1
+    assert pow(beta, 3, Y.P) == 1 and beta != 1
+    g = Y.g1_mul(Y.G1, 12345)
+    assert Y.g1_mul(g, lam) == ((beta * g[0]) % Y.P, g[1])
+    f = lib.ace_debug_glv_split
+    f.restype = ctypes.c_int
+    rng = random.Random(9)
+    for k in [0, 1, 2, Y.R - 1, Y.R // 2, lam, (1 << 253) + 17] + [rng.randrange(Y.R) for _ in range(200)]:
+        out = (ctypes.c_uint32 * 10)()
+        assert f(k.to_bytes(32, "little"), out) == 0
+        k1 = sum(out[i] << (32 * i) for i in range(4)) * (-1 if out[4] else 1)
+        k2 = sum(out[5 + i] << (32 * i) for i in range(4)) * (-1 if out[9] else 1)
+        assert abs(k1) < 1 << 128 and abs(k2) < 1 << 128
+        assert (k1 + k2 * lam - k) % Y.R == 0

@@ -292,17 +292,37 @@ __device__ __forceinline__ uint32_t size_bin(const uint32_t* off, uint32_t key) 
     return SIZE_BINS - 1 - s;  // bin 0 holds the largest buckets
 }
 
-__global__ void k_size_hist(const uint32_t* __restrict__ off, uint32_t keys, uint32_t* bins) {
+// Bucket sizes cluster around the mean, so a few bins take most keys: both
+// passes count in shared memory first and touch each global bin once per
+// block (blocks of 256 threads).
+__global__ void __launch_bounds__(256) k_size_hist(const uint32_t* __restrict__ off, uint32_t keys, uint32_t* bins) {
+    __shared__ uint32_t cnt[SIZE_BINS];
+    for (uint32_t j = threadIdx.x; j < SIZE_BINS; j += blockDim.x) cnt[j] = 0;
+    __syncthreads();
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= keys) return;
-    atomicAdd(&bins[size_bin(off, k)], 1u);
+    if (k < keys) atomicAdd(&cnt[size_bin(off, k)], 1u);
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < SIZE_BINS; j += blockDim.x)
+        if (cnt[j]) atomicAdd(&bins[j], cnt[j]);
 }
 
-__global__ void k_size_scatter(const uint32_t* __restrict__ off, uint32_t keys, uint32_t* bins, uint32_t* order) {
+// bins holds each bin's first position (exclusive scan of the histogram)
+__global__ void __launch_bounds__(256) k_size_scatter(const uint32_t* __restrict__ off, uint32_t keys, uint32_t* bins,
+                                                      uint32_t* order) {
+    __shared__ uint32_t cnt[SIZE_BINS], base[SIZE_BINS];
+    for (uint32_t j = threadIdx.x; j < SIZE_BINS; j += blockDim.x) cnt[j] = 0;
+    __syncthreads();
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= keys) return;
-    uint32_t pos = atomicAdd(&bins[size_bin(off, k)], 1u);
-    order[pos] = k;
+    uint32_t bin = 0, rank = 0;
+    if (k < keys) {
+        bin = size_bin(off, k);
+        rank = atomicAdd(&cnt[bin], 1u);
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < SIZE_BINS; j += blockDim.x)
+        if (cnt[j]) base[j] = atomicAdd(&bins[j], cnt[j]);
+    __syncthreads();
+    if (k < keys) order[base[bin] + rank] = k;
 }
 
 int bucket_order(const uint32_t* offsets, uint32_t keys, uint32_t* bins, uint32_t* scan_tmp, uint32_t* order,

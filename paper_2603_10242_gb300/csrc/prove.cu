@@ -53,20 +53,36 @@ struct CsrDev {
 // Montgomery coefficient and a canonical z_j is the canonical product, so the
 // row sums are canonical and one multiplication by R^2 mod r returns them to
 // Montgomery form.
+// row i of one matrix times z, two non-zeros at a time (their loads and
+// products are independent), back in Montgomery form
+__device__ __forceinline__ fr_t row_dot(const CsrDev& m, int k, const fr_t* __restrict__ z, uint32_t i) {
+    const uint32_t* __restrict__ col = m.col[k];
+    const fr_t* __restrict__ val = m.val[k];
+    fr_t acc0 = fe_zero<FrCfg>(), acc1 = fe_zero<FrCfg>();
+    uint32_t t = m.rp[k][i];
+    const uint32_t e = m.rp[k][i + 1];
+    for (; t + 2 <= e; t += 2) {
+        const uint32_t c0 = __ldg(col + t), c1 = __ldg(col + t + 1);
+        const fr_t v0 = ldg_fr(val + t), v1 = ldg_fr(val + t + 1);
+        const fr_t z0 = ldg_fr(z + c0), z1 = ldg_fr(z + c1);
+        acc0 = acc0 + v0 * z0;
+        acc1 = acc1 + v1 * z1;
+    }
+    if (t < e) acc0 = acc0 + ldg_fr(val + t) * ldg_fr(z + __ldg(col + t));
+    return (acc0 + acc1) * fe_rr<FrCfg>();
+}
+
 __global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const fr_t* __restrict__ z, uint32_t N, fr_t* abc,
                                                int32_t* status) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    fr_t v[3];
-#pragma unroll 1
-    for (int k = 0; k < 3; k++) {
-        fr_t acc = fe_zero<FrCfg>();
-        uint32_t b = m.rp[k][i], e = m.rp[k][i + 1];
-        for (uint32_t t = b; t < e; t++) acc = acc + ldg_fr(m.val[k] + t) * ldg_fr(z + __ldg(m.col[k] + t));
-        v[k] = acc * fe_rr<FrCfg>();
-        st_fr2(abc + (size_t)k * N + i, v[k]);
-    }
-    if (!fe_eq(v[0] * v[1], v[2])) atomicOr(status, 1);
+    const fr_t a = row_dot(m, 0, z, i);
+    st_fr2(abc + i, a);
+    const fr_t b = row_dot(m, 1, z, i);
+    st_fr2(abc + (size_t)N + i, b);
+    const fr_t c = row_dot(m, 2, z, i);
+    st_fr2(abc + 2 * (size_t)N + i, c);
+    if (!fe_eq(a * b, c)) atomicOr(status, 1);
 }
 
 // q_i = (a_i b_i - c_i) * zinv, written over a
@@ -263,16 +279,13 @@ __global__ void __launch_bounds__(256) k_spmv3_many(CsrDev m, const fr_t* __rest
     const uint32_t q = blockIdx.y;
     z += (size_t)q * wit;
     abc += (size_t)q * 3 * N;
-    fr_t v[3];
-#pragma unroll 1
-    for (int k = 0; k < 3; k++) {
-        fr_t acc = fe_zero<FrCfg>();
-        uint32_t b = m.rp[k][i], e = m.rp[k][i + 1];
-        for (uint32_t t = b; t < e; t++) acc = acc + ldg_fr(m.val[k] + t) * ldg_fr(z + __ldg(m.col[k] + t));
-        v[k] = acc * fe_rr<FrCfg>();
-        st_fr2(abc + (size_t)k * N + i, v[k]);
-    }
-    if (!fe_eq(v[0] * v[1], v[2])) atomicOr(status + q, 1);
+    const fr_t a = row_dot(m, 0, z, i);
+    st_fr2(abc + i, a);
+    const fr_t b = row_dot(m, 1, z, i);
+    st_fr2(abc + (size_t)N + i, b);
+    const fr_t c = row_dot(m, 2, z, i);
+    st_fr2(abc + 2 * (size_t)N + i, c);
+    if (!fe_eq(a * b, c)) atomicOr(status + q, 1);
 }
 
 __global__ void k_quotient_many(const fr_t* abc, uint32_t N, fr_t zinv, fr_t* h) {

@@ -367,7 +367,8 @@ int ace_witness_many(ace_ctx* ctx, const ace_circuit* c, size_t k, const uint64_
  * ParallelMap over the block's transactions).  Every stage runs once for
  * all k proofs (one sparse-product launch, NTT launches over 3k arrays, MSMs
  * whose k bucket sets share the key's point tables), in chunks that keep the
- * scratch within 24 GB.  d_z: k witnesses of pk's m values each, contiguous
+ * scratch within 24 GB (the environment variable ACE_MANY_MAX_CHUNK caps the
+ * proofs per chunk further).  d_z: k witnesses of pk's m values each, contiguous
  * (k x m ace_fr, canonical, 16-byte aligned, device); rs, ss: k canonical
  * values each (host); proofs (host, k x 256 bytes) and status (host, k: 0 ok,
  * 1 the witness does not satisfy the R1CS).  Synchronous; each proof equals

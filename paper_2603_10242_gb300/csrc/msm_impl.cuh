@@ -74,8 +74,12 @@ size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont) {
 #ifndef ACE_BUCKET_MIN_BLOCKS
 #define ACE_BUCKET_MIN_BLOCKS 1
 #endif
+#ifndef ACE_BUCKET_MIN_BLOCKS_G2
+#define ACE_BUCKET_MIN_BLOCKS_G2 1
+#endif
 template <class F>
-__global__ void __launch_bounds__(128, ACE_BUCKET_MIN_BLOCKS) k_bucket_acc(const Affine<F>* __restrict__ bases,
+__global__ void __launch_bounds__(128, sizeof(F) == sizeof(fp_t) ? ACE_BUCKET_MIN_BLOCKS : ACE_BUCKET_MIN_BLOCKS_G2)
+    k_bucket_acc(const Affine<F>* __restrict__ bases,
                                                     const uint32_t* __restrict__ entries,
                                                     const uint32_t* __restrict__ offsets,
                                                     const uint32_t* __restrict__ order, uint32_t nkeys,
@@ -137,16 +141,20 @@ uint32_t bucket_split(const MsmPlan& p) {
 // ---------------------------------------------------------------------------
 template <class F>
 __global__ void __launch_bounds__(128) k_seg_reduce(const Xyzz<F>* __restrict__ buckets, uint32_t nseg,
-                                                    uint32_t B, uint32_t L, uint32_t M, Xyzz<F>* segW,
-                                                    Xyzz<F>* segS) {
+                                                    uint32_t B, uint32_t L, uint32_t M, uint32_t windows,
+                                                    uint32_t ones, Xyzz<F>* segW, Xyzz<F>* segS) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nseg) return;
     uint32_t w = t / M, j = t % M;
     const Xyzz<F>* bk = buckets + (size_t)w * B + (size_t)j * L;
     Xyzz<F> run = xyzz_inf<F>(), acc = xyzz_inf<F>();
-    for (int b = (int)L - 1; b >= 0; b--) {
-        run = xyzz_add(run, ld_plain(bk + b));
-        acc = xyzz_add(acc, run);
+    if (w % windows == ones) {  // the ones window needs only its plain sum
+        for (int b = (int)L - 1; b >= 0; b--) run = xyzz_add(run, ld_plain(bk + b));
+    } else {
+        for (int b = (int)L - 1; b >= 0; b--) {
+            run = xyzz_add(run, ld_plain(bk + b));
+            acc = xyzz_add(acc, run);
+        }
     }
     st_vec(segW + t, acc);
     st_vec(segS + t, run);
@@ -298,7 +306,8 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     }
     uint32_t nseg = plan.all_windows() * plan.M;
     int prof_red = prof_begin(PROF_REDUCE, st);
-    k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, b.segW, b.segS); ::ace::note_launch();
+    k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, plan.windows(),
+                                                        plan.bucket_windows(), b.segW, b.segS); ::ace::note_launch();
     k_seg_weight<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.segW, b.segS, nseg, plan.M, plan.lambda, plan.windows(),
                                                         plan.bucket_windows()); ::ace::note_launch();
     // sum each window's M weighted segments: 256 to 1 per pass, ping-pong

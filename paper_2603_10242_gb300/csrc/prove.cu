@@ -17,6 +17,7 @@
 //      the fixed-base terms come from the key's window tables at the start,
 //      s S_A + r S_B1 (one joint double-and-add) as soon as the A and B1
 //      MSMs are done, and the last kernel only adds and converts to affine.
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -815,6 +816,12 @@ int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, 
     if (chunk > ((size_t)1 << 31) / keys) chunk = ((size_t)1 << 31) / keys;
     if (chunk < 1) chunk = 1;
     if (chunk > 21845) chunk = 21845;
+    // ACE_MANY_MAX_CHUNK (environment): a smaller cap, e.g. to bound latency
+    // per chunk or to exercise the chunk loop
+    if (const char* env = getenv("ACE_MANY_MAX_CHUNK")) {
+        long v = strtol(env, nullptr, 10);
+        if (v >= 1 && (size_t)v < chunk) chunk = (size_t)v;
+    }
     if (chunk > k) chunk = k;
     ACE_TRY(arena_ensure(ctx, 3, chunk * (256 + sizeof(int32_t)) + 1024));
     ctx->scratch[3].reset();

@@ -66,3 +66,19 @@ def test_prove_many_rejects_bad_arguments():
     with pytest.raises(ace.AceError):
         ctx.prove_many(pk, gu.dev(z), 1, bad_r, s)
     assert ctx.prove_many(pk, gu.dev(z), 0, b"", b"") == ([], [])
+
+
+def test_prove_many_in_chunks(monkeypatch):
+    """Proofs split into chunks of 3 (3 + 3 + 1) equal the proofs of one pass."""
+    ctx = gu.ctx()
+    c = ace.Circuit(*CIRCUITS[2], seed=27)
+    pk = ace.ProvingKey(ctx, c, toxic_seed=28)
+    k = 7
+    zs, rs = _inputs(c, k, 500)
+    dz = gu.dev(b"".join(zs))
+    r_all, s_all = b"".join(r for r, _ in rs), b"".join(s for _, s in rs)
+    whole, st1 = ctx.prove_many(pk, dz, k, r_all, s_all)
+    monkeypatch.setenv("ACE_MANY_MAX_CHUNK", "3")
+    chunked, st2 = ctx.prove_many(pk, dz, k, r_all, s_all)
+    assert st1 == st2 == [0] * k and chunked == whole
+    assert chunked[6] == ctx.prove(pk, gu.dev(zs[6]), *rs[6])

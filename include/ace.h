@@ -227,7 +227,8 @@ int ace_verify(const ace_vk* vk, const ace_fr* pub, size_t n_pub, const uint8_t 
  * except with probability about k 2^-128), negative on malformed input.
  * rho_i are 128-bit values drawn from SplitMix64(seed, purpose 12): a
  * verifier facing adversarial provers must pass a seed they cannot predict.
- * pubs: k public inputs (host, canonical); proofs: k x 256 bytes (host).
+ * pubs: k public inputs (host, canonical); proofs: k x 256 bytes (host);
+ * k <= 2^20 per call (about 1.5 KB of device scratch per proof).
  * The per-proof work (subgroup check, rho_i A_i, rho_i C_i, Miller loop) runs
  * on the device, the final exponentiation on the host. */
 int ace_verify_batch(ace_ctx* ctx, const ace_vk* vk, size_t k, const ace_fr* pubs, const uint8_t* proofs,
@@ -267,7 +268,9 @@ int ace_debug_curve_op(int group, int op, const void* d_a, const void* d_b, cons
 int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
 /* The same pairing by Miller-loop form 0 (affine, the single verifier's) or 1
  * (homogeneous projective, the loop the batch verifier runs on the device),
- * computed on the host. */
+ * or form 2 (affine, with the final exponentiation's hard part by plain
+ * square-and-multiply instead of the base-p joint exponentiation), computed
+ * on the host. */
 int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]);
 /* Host: the GLV split the prover uses for s S_A + r S_B1: k = k1 + k2 lambda
  * (mod r), lambda = 0xb3c4d79d41a917585bfc41088d8daaa78b17ea66b99c90dd, a

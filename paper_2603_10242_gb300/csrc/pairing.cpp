@@ -34,6 +34,7 @@ struct Consts {
     F2 gamma[6];                 // xi^(k (p-1)/6): Frobenius of w^k
     F2 b2;                       // twist coefficient 3/xi
     std::vector<uint32_t> hard;  // (p^4 - p^2 + 1) / r
+    uint32_t hard_p[4][8];       // its digits in base p: hard = sum_i hard_p[i] p^i
     unsigned __int128 ate = 0;   // 6x + 2 (a 65-bit value)
 };
 
@@ -117,6 +118,40 @@ bool big_div_exact(const Big& a, const uint32_t d[8], Big& q) {
     return true;
 }
 
+// q = a / d, r = a mod d for the 254-bit modulus d (bit-serial long division)
+void big_divmod(const Big& a, const uint32_t d[8], Big& q, Big& r) {
+    q.assign(a.size(), 0);
+    Big rem(9, 0);
+    for (int bit = (int)a.size() * 32 - 1; bit >= 0; bit--) {
+        uint32_t carry = (a[bit >> 5] >> (bit & 31)) & 1u;
+        for (int i = 0; i < 9; i++) {
+            uint32_t nc = rem[i] >> 31;
+            rem[i] = (rem[i] << 1) | carry;
+            carry = nc;
+        }
+        bool ge = rem[8] != 0;
+        if (!ge) {
+            ge = true;
+            for (int i = 7; i >= 0; i--) {
+                if (rem[i] != d[i]) {
+                    ge = rem[i] > d[i];
+                    break;
+                }
+            }
+        }
+        if (ge) {
+            int64_t br = 0;
+            for (int i = 0; i < 9; i++) {
+                int64_t x = (int64_t)rem[i] - (i < 8 ? d[i] : 0) + br;
+                rem[i] = (uint32_t)x;
+                br = x < 0 ? -1 : 0;
+            }
+            q[bit >> 5] |= 1u << (bit & 31);
+        }
+    }
+    r.assign(rem.begin(), rem.begin() + 8);
+}
+
 F2 f2_pow(const F2& a, const Big& e) {
     F2 acc = f2_one();
     for (int i = (int)e.size() * 32 - 1; i >= 0; i--) {
@@ -164,6 +199,14 @@ Consts make_consts() {
     big_div_exact(num, rl, q);
     while (q.size() > 1 && q.back() == 0) q.pop_back();
     c.hard = q;
+    // base-p digits of the hard exponent (it has four: (p^4 - p^2 + 1)/r < p^4)
+    Big rest = q;
+    for (int i = 0; i < 4; i++) {
+        Big quo, rem;
+        big_divmod(rest, pl, quo, rem);
+        for (int l = 0; l < 8; l++) c.hard_p[i][l] = l < (int)rem.size() ? rem[l] : 0;
+        rest = quo;
+    }
     c.ate = (unsigned __int128)6 * 4965661367192848881ull + 2u;
     return c;
 }
@@ -197,10 +240,43 @@ F12 f12_pow(const F12& a, const Big& e) {
     return acc;
 }
 
+// t^hard with hard = d0 + d1 p + d2 p^2 + d3 p^3: t^(d_i p^i) = frob^i(t)^d_i,
+// so one joint square-and-multiply over the 254-bit digits with the 15
+// products of the four Frobenius images (254 squarings instead of 761)
+F12 hard_part(const F12& t) {
+    const Consts& k = consts();
+    F12 b[4];
+    b[0] = t;
+    for (int i = 1; i < 4; i++) b[i] = frobenius(b[i - 1]);
+    F12 tab[16];
+    tab[0] = f12_one();
+    for (int m = 1; m < 16; m++) {
+        int low = m & -m, i = 0;
+        while ((1 << i) != low) i++;
+        tab[m] = (m == low) ? b[i] : tab[m ^ low] * b[i];
+    }
+    F12 acc = f12_one();
+    for (int bit = 253; bit >= 0; bit--) {
+        acc = f12_sqr(acc);
+        int m = 0;
+        for (int i = 0; i < 4; i++) m |= (int)((k.hard_p[i][bit >> 5] >> (bit & 31)) & 1u) << i;
+        if (m) acc = acc * tab[m];
+    }
+    return acc;
+}
+
 F12 final_exp(const F12& f) {
     F12 t = f12_conj(f) * f12_inv(f);          // f^(p^6 - 1)
     t = frobenius(frobenius(t)) * t;           // ^(p^2 + 1)
-    return f12_pow(t, consts().hard);          // ^((p^4 - p^2 + 1)/r)
+    return hard_part(t);                       // ^((p^4 - p^2 + 1)/r)
+}
+
+// the same power by plain square-and-multiply over the 761-bit exponent (for
+// tests of hard_part)
+F12 final_exp_plain(const F12& f) {
+    F12 t = f12_conj(f) * f12_inv(f);
+    t = frobenius(frobenius(t)) * t;
+    return f12_pow(t, consts().hard);
 }
 
 struct G2a {
@@ -436,23 +512,25 @@ int ace_debug_pairing(const uint8_t g1[64], const uint8_t g2[128], uint8_t out[3
 }
 
 // form 0: affine Miller loop (the single verifier's); form 1: projective
-// Miller loop (the batch verifier's device loop, run here on the host)
+// Miller loop (the batch verifier's device loop, run here on the host);
+// form 2: affine Miller loop and the final exponentiation's hard part by
+// plain square-and-multiply over its 761-bit exponent
 int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128], uint8_t out[384]) {
     fp_t x, y;
     bool inf;
     G2a q;
-    if (form < 0 || form > 1) return ACE_E_ARG;
+    if (form < 0 || form > 2) return ACE_E_ARG;
     if (!read_g1(g1, x, y, inf) || !read_g2(g2, q)) return ACE_E_NOT_ON_CURVE;
     F12 f = f12_one();
     if (!inf && !q.inf) {
-        if (form == 0 && !miller(x, y, q, f)) return ACE_E_ARG;
+        if (form != 1 && !miller(x, y, q, f)) return ACE_E_ARG;
         if (form == 1) {
             fp_t qq[4] = {q.x.c0, q.x.c1, q.y.c0, q.y.c1}, raw[12];
             if (!miller_proj_raw(x, y, qq, raw)) return ACE_E_ARG;
             memcpy(&f, raw, sizeof f);
         }
     }
-    f = final_exp(f);
+    f = form == 2 ? final_exp_plain(f) : final_exp(f);
     const F2* c[6] = {&f.c0.a0, &f.c0.a1, &f.c0.a2, &f.c1.a0, &f.c1.a1, &f.c1.a2};
     for (int i = 0; i < 6; i++) {
         fp_t a = fe_from_mont(c[i]->c0), b = fe_from_mont(c[i]->c1);

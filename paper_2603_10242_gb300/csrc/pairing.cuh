@@ -50,10 +50,22 @@ ACE_HD F6 f6_one() { return {f2_one(), f2_zero(), f2_zero()}; }
 ACE_HD F6 operator+(const F6& a, const F6& b) { return {a.a0 + b.a0, a.a1 + b.a1, a.a2 + b.a2}; }
 ACE_HD F6 operator-(const F6& a, const F6& b) { return {a.a0 - b.a0, a.a1 - b.a1, a.a2 - b.a2}; }
 ACE_HD F6 f6_neg(const F6& a) { return {fe_neg(a.a0), fe_neg(a.a1), fe_neg(a.a2)}; }
+// Karatsuba over Fp2 (6 products): with v_i = a_i b_i,
+// c0 = v0 + xi ((a1 + a2)(b1 + b2) - v1 - v2), c1 = (a0 + a1)(b0 + b1) - v0 - v1 + xi v2,
+// c2 = (a0 + a2)(b0 + b2) - v0 - v2 + v1
 ACE_HD F6 operator*(const F6& a, const F6& b) {
-    F2 c0 = a.a0 * b.a0 + mul_xi(a.a1 * b.a2 + a.a2 * b.a1);
-    F2 c1 = a.a0 * b.a1 + a.a1 * b.a0 + mul_xi(a.a2 * b.a2);
-    F2 c2 = a.a0 * b.a2 + a.a1 * b.a1 + a.a2 * b.a0;
+    F2 v0 = a.a0 * b.a0, v1 = a.a1 * b.a1, v2 = a.a2 * b.a2;
+    F2 c0 = v0 + mul_xi((a.a1 + a.a2) * (b.a1 + b.a2) - v1 - v2);
+    F2 c1 = (a.a0 + a.a1) * (b.a0 + b.a1) - v0 - v1 + mul_xi(v2);
+    F2 c2 = (a.a0 + a.a2) * (b.a0 + b.a2) - v0 - v2 + v1;
+    return {c0, c1, c2};
+}
+// a (x0 + x1 v): the Fp6 product with a factor of zero v^2 coefficient
+ACE_HD F6 f6_mul_01(const F6& a, const F2& x0, const F2& x1) {
+    F2 v0 = a.a0 * x0, v1 = a.a1 * x1;
+    F2 c0 = v0 + mul_xi((a.a1 + a.a2) * x1 - v1);
+    F2 c1 = (a.a0 + a.a1) * (x0 + x1) - v0 - v1;
+    F2 c2 = a.a2 * x0 + v1;
     return {c0, c1, c2};
 }
 ACE_HD F6 mul_v(const F6& a) { return {mul_xi(a.a2), a.a0, a.a1}; }
@@ -88,13 +100,14 @@ ACE_HD F12 f12_inv(const F12& a) {
 }
 ACE_HD bool f12_eq(const F12& a, const F12& b) { return f6_eq(a.c0, b.c0) && f6_eq(a.c1, b.c1); }
 
-// f times a line value with only the w^0 (Fp), w^1 and w^3 (Fp2) coefficients:
-// l = l0 + l1 w + l3 w^3 = (l0 + 0 v + 0 v^2) + (l1 + l3 v + 0 v^2) w
+// f times a line value with only the w^0, w^1 and w^3 coefficients:
+// l = l0 + l1 w + l3 w^3 = (l0 + 0 v + 0 v^2) + (l1 + l3 v + 0 v^2) w, so
+// f0 l0 + v (f1 (l1 + l3 v)) + ((f0 + f1)(l0 + l1 + l3 v) - f0 l0 - f1 (l1 + l3 v)) w
 ACE_HD F12 f12_mul_line(const F12& f, const F2& l0, const F2& l1, const F2& l3) {
-    F12 l;
-    l.c0 = {l0, f2_zero(), f2_zero()};
-    l.c1 = {l1, l3, f2_zero()};
-    return f * l;
+    F6 t0 = {f.c0.a0 * l0, f.c0.a1 * l0, f.c0.a2 * l0};
+    F6 t1 = f6_mul_01(f.c1, l1, l3);
+    F6 t2 = f6_mul_01(f.c0 + f.c1, l0 + l1, l3);
+    return {t0 + mul_v(t1), t2 - t0 - t1};
 }
 
 // constants of the Miller loop (built on the host)

@@ -138,8 +138,8 @@ int ace_verify_batch(ace_ctx* ctx, const ace_vk* vk, size_t k, const ace_fr* pub
         return ACE_E_ARG;
     }
     if (k == 0) return 1;
-    if (k > (1u << 24)) {
-        set_error("ace_verify_batch: k = %zu proofs (at most 2^24)", k);
+    if (k > (1u << 20)) {  // scratch: about 1.5 KB of device memory per proof
+        set_error("ace_verify_batch: k = %zu proofs (at most 2^20 per call)", k);
         return ACE_E_ARG;
     }
     // host: parse and validate every point, draw rho

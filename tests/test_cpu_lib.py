@@ -144,9 +144,9 @@ def test_projective_miller_loop_matches_affine(lib):
     for _ in range(3):
         P = O.g1_mul(g1, rng.randrange(1, Y.R))
         Q = O.g2_mul(g2, rng.randrange(1, Y.R))
-        a, b = ctypes.create_string_buffer(384), ctypes.create_string_buffer(384)
-        assert f(0, P, Q, a) == 0 and f(1, P, Q, b) == 0
-        assert a.raw == b.raw
+        a, b, c = (ctypes.create_string_buffer(384) for _ in range(3))
+        assert f(0, P, Q, a) == 0 and f(1, P, Q, b) == 0 and f(2, P, Q, c) == 0
+        assert a.raw == b.raw == c.raw
     # bilinearity through the projective loop: e(2P, Q) = e(P, 2Q)
     P, Q = O.g1_mul(g1, 77), O.g2_mul(g2, 99)
     a, b = ctypes.create_string_buffer(384), ctypes.create_string_buffer(384)

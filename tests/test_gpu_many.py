@@ -12,6 +12,7 @@ torch = gu.torch
 ace = gu.ace
 
 CIRCUITS = [(10, 1024, 4, 0, 0), (11, 1400, 5, 0, 0), (12, 4000, 8, 8, 172)]
+TINY = [(2, 4, 0, 0, 0), (3, 6, 0, 1, 3)]  # chain only; a packing row and a ragged tail
 
 
 def _inputs(c, k, seed):
@@ -82,3 +83,17 @@ def test_prove_many_in_chunks(monkeypatch):
     chunked, st2 = ctx.prove_many(pk, dz, k, r_all, s_all)
     assert st1 == st2 == [0] * k and chunked == whole
     assert chunked[6] == ctx.prove(pk, gu.dev(zs[6]), *rs[6])
+
+
+@pytest.mark.parametrize("params", TINY)
+def test_prove_many_tiny_circuits(params):
+    ctx = gu.ctx()
+    c = ace.Circuit(*params, seed=29)
+    pk = ace.ProvingKey(ctx, c, toxic_seed=30)
+    k = 5
+    zs, rs = _inputs(c, k, 600)
+    proofs, status = ctx.prove_many(pk, gu.dev(b"".join(zs)), k, b"".join(r for r, _ in rs),
+                                    b"".join(s for _, s in rs))
+    assert status == [0] * k
+    for i in range(k):
+        assert proofs[i] == ctx.prove(pk, gu.dev(zs[i]), *rs[i])

@@ -41,11 +41,24 @@ def sources():
 
 
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every csrc/ translation unit (in parallel) and link libace.so."""
+    """Compile every csrc/ translation unit (in parallel) and link libace.so.
+    Processes that build at the same time (e.g. the ranks of one job) take
+    turns on a lock file, so only the first one compiles."""
+    import fcntl
+
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, jobs)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, jobs: int | None) -> str:
     from concurrent.futures import ThreadPoolExecutor
 
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
     # ACE_NVCC_FLAGS: extra compile flags (e.g. -DACE_MUL_FORM=2); a change of
     # them rebuilds everything
     extra = os.environ.get("ACE_NVCC_FLAGS", "").split()

@@ -271,6 +271,7 @@ def run_ours(args):
     launches = ace.launch_count() - launches0
     total_ms = eb0.elapsed_time(eb1)
     prof = {k: ace.profile_read(k) for k in range(7)}
+    g1_sum_ms = ace.profile_read_sum(ace.PROF_G1_BUCKET)
     ace.profile_enable(False)
     if sampler:
         sampler.terminate()
@@ -367,7 +368,13 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (G1 bucket accumulation) ----
     ms, nl, units = prof[ace.PROF_G1_BUCKET]
     peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = units * IMAD_PER_G1_MADD / (ms / 1000.0) / 1e12 if ms > 0 else None
+    # algorithmic multiply-adds per launch / average launch duration (the
+    # launches of the batched proofs overlap other kernels and one another)
+    achieved = units * IMAD_PER_G1_MADD / (g1_sum_ms / 1000.0) / 1e12 if g1_sum_ms > 0 else None
+    union = {"achieved": units * IMAD_PER_G1_MADD / (ms / 1000.0) / 1e12 if ms > 0 else None, "ms": ms,
+             "how": "the same work over the union of the launch intervals (time during which at least one "
+                    "launch of the kernel was running)"}
+    union["frac"] = union["achieved"] / peak if union["achieved"] else None
     measured_peak = {k: ace.imad_rate(ctx, mode) / 1e12 for k, mode in (("mad_lo", 0), ("mad_hi", 1),
                                                                        ("mad_lo_hi_chain", 2))}
     # one mad.wide is one limb product = two 32-bit multiply-adds (lo and hi)
@@ -395,12 +402,13 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": "k_bucket_acc<G1>", "achieved": achieved, "peak": peak,
                 "unit": "T IMAD/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "algorithmic_per_unit": f"{IMAD_PER_G1_MADD} IMAD per mixed addition (10 Fp mul x 272)",
-                "units_per_launch": units / nl if nl else None, "launches": nl, "ms_union": ms,
+                "units_per_launch": units / nl if nl else None, "launches": nl,
+                "avg_launch_ms": g1_sum_ms / nl if nl else None,
                 "peak_source": "152 SMs x 64 IMAD/clk/SM x 2070 MHz (nominal unit counts and max clock)",
                 "peak_measured_T_per_s": measured_peak,
-                "measured": "union of the kernel's launch intervals inside the timed proofs (other kernels "
-                            "share the SMs meanwhile)",
-                "isolated": isolated, "whole_step": step_alu}
+                "measured": "CUDA events around every launch inside the timed proofs; up to four proofs run "
+                            "at once, so each launch shares the SMs with other kernels",
+                "union": union, "isolated": isolated, "whole_step": step_alu}
     stages = {
         "g1_bucket_ms_per_proof": ms / args.steps,
         "g2_bucket_ms_per_proof": prof[ace.PROF_G2_BUCKET][0] / args.steps,

@@ -307,6 +307,10 @@ int ace_launch_count(uint64_t* out);
  * A bracket of kinds 4 and 5 spans several kernels of one MSM. */
 int ace_profile_enable(int on);
 int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
+/* The total length of the same intervals (ms): launches that overlap one
+ * another count once each, so sum_ms / launches is the average launch
+ * duration. */
+int ace_profile_read_sum(int kind, double* sum_ms);
 
 /* ---- batching and serving ------------------------------------------------ */
 

@@ -103,6 +103,7 @@ def lib():
             "ace_profile_enable": (i32, [i32]),
             "ace_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
                                        ctypes.POINTER(u64)]),
+            "ace_profile_read_sum": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name, None)
@@ -386,6 +387,13 @@ def launch_count() -> int:
 
 def profile_enable(on: bool = True):
     check(lib().ace_profile_enable(1 if on else 0))
+
+
+def profile_read_sum(kind: int) -> float:
+    """Total length (ms) of one kind's launch intervals since enabling."""
+    v = ctypes.c_double()
+    check(lib().ace_profile_read_sum(kind, ctypes.byref(v)))
+    return v.value
 
 
 def profile_read(kind: int):

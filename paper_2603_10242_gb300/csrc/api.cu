@@ -389,6 +389,17 @@ int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units) 
     return prof_read(kind, ms, launches, units);
 }
 
+int ace_profile_read_sum(int kind, double* sum_ms) {
+    clear_error();
+    if (kind < 0 || kind >= PROF_KINDS || !sum_ms) {
+        set_error("ace_profile_read_sum: bad argument");
+        return ACE_E_ARG;
+    }
+    double ms = 0;
+    uint64_t n = 0, u = 0;
+    return prof_read(kind, &ms, &n, &u, sum_ms);
+}
+
 }  // extern "C"
 
 namespace ace {

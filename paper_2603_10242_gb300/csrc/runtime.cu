@@ -162,7 +162,7 @@ void prof_end(int slot, cudaStream_t st, const uint32_t* device_units, uint64_t 
     }
 }
 
-int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units) {
+int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units, double* sum_ms) {
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     ACE_TRY_CUDA(cudaDeviceSynchronize());
@@ -183,6 +183,11 @@ int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units) {
         iv.push_back({a, b});
         n++;
         u += r.host_units + (r.dev_units ? du[i] : 0);
+    }
+    if (sum_ms) {
+        double total = 0;
+        for (auto& x : iv) total += x.second - x.first;
+        *sum_ms = total;
     }
     std::sort(iv.begin(), iv.end());
     double t = 0, cs = 0, ce = -1e300;

@@ -149,5 +149,6 @@ int prof_begin(int kind, cudaStream_t st);  // returns a record slot, or -1 when
 // host_units is added to it
 void prof_end(int slot, cudaStream_t st, const uint32_t* device_units, uint64_t host_units);
 void prof_enable(bool on);
-int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
+// ms: length of the union of the intervals; sum_ms (optional): their total length
+int prof_read(int kind, double* ms, uint64_t* launches, uint64_t* units, double* sum_ms = nullptr);
 }  // namespace ace

@@ -54,23 +54,14 @@ struct CsrDev {
 // Montgomery coefficient and a canonical z_j is the canonical product, so the
 // row sums are canonical and one multiplication by R^2 mod r returns them to
 // Montgomery form.
-// row i of one matrix times z, two non-zeros at a time (their loads and
-// products are independent), back in Montgomery form
+// row i of one matrix times z, back in Montgomery form
 __device__ __forceinline__ fr_t row_dot(const CsrDev& m, int k, const fr_t* __restrict__ z, uint32_t i) {
     const uint32_t* __restrict__ col = m.col[k];
     const fr_t* __restrict__ val = m.val[k];
-    fr_t acc0 = fe_zero<FrCfg>(), acc1 = fe_zero<FrCfg>();
-    uint32_t t = m.rp[k][i];
+    fr_t acc = fe_zero<FrCfg>();
     const uint32_t e = m.rp[k][i + 1];
-    for (; t + 2 <= e; t += 2) {
-        const uint32_t c0 = __ldg(col + t), c1 = __ldg(col + t + 1);
-        const fr_t v0 = ldg_fr(val + t), v1 = ldg_fr(val + t + 1);
-        const fr_t z0 = ldg_fr(z + c0), z1 = ldg_fr(z + c1);
-        acc0 = acc0 + v0 * z0;
-        acc1 = acc1 + v1 * z1;
-    }
-    if (t < e) acc0 = acc0 + ldg_fr(val + t) * ldg_fr(z + __ldg(col + t));
-    return (acc0 + acc1) * fe_rr<FrCfg>();
+    for (uint32_t t = m.rp[k][i]; t < e; t++) acc = acc + ldg_fr(val + t) * ldg_fr(z + __ldg(col + t));
+    return acc * fe_rr<FrCfg>();
 }
 
 __global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const fr_t* __restrict__ z, uint32_t N, fr_t* abc,

@@ -39,6 +39,7 @@ struct ace_pk {
     uint32_t* d_col[3] = {};
     ace::fr_t* d_val[3] = {};
     uint64_t nnz[3] = {};
+    uint32_t* d_row_order = nullptr;  // N rows by decreasing total length (sparse-product schedule)
     ace::Query<ace::fp_t> A, B1, L;
     ace::Query<ace::fp2_t> B2;   // same indices as B1
     ace::g1_aff* d_H = nullptr;  // window table of N points: d_H[p] = H_{bitrev(p)}, H_{N-1} = infinity
@@ -58,6 +59,11 @@ struct ace_pk {
 
 namespace ace {
 int pk_alloc(ace_pk* pk, void** p, size_t bytes);
+// rows 0..N-1 ordered by decreasing number of non-zeros in A, B and C
+// together (ties: by the A length, then the B length, then the row), uploaded to
+// pk->d_row_order: the sparse product takes rows in this order so that the
+// lanes of a warp have equal work
+int pk_row_order(ace_pk* pk, const Csr mat[3]);
 // window tables of the fixed points (after d_fixed is set)
 int pk_build_tables(ace_pk* pk, const PkFixed& f);
 // allocate the window table of a query of `count` points (window 0 to be

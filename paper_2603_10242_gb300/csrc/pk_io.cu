@@ -222,6 +222,7 @@ int ace_pk_load(ace_ctx* ctx, const char* path, ace_pk** pk_out, ace_vk* vk_out)
         if (rc == ACE_OK) rc = host_to_dev(pk, c->mat[k].col, &pk->d_col[k]);
         if (rc == ACE_OK) rc = host_to_dev(pk, c->mat[k].val, &pk->d_val[k]);
     }
+    if (rc == ACE_OK) rc = pk_row_order(pk, c->mat);
     pk->A.count = (uint32_t)ia.size();
     pk->A.h_idx = ia;
     pk->B1.count = pk->B2.count = (uint32_t)ib.size();

@@ -53,26 +53,48 @@ struct CsrDev {
 // a, b, c (Montgomery) for every row; z canonical.  The product of a
 // Montgomery coefficient and a canonical z_j is the canonical product, so the
 // row sums are canonical and one multiplication by R^2 mod r returns them to
-// Montgomery form.
-// row i of one matrix times z, back in Montgomery form
-__device__ __forceinline__ fr_t row_dot(const CsrDev& m, int k, const fr_t* __restrict__ z, uint32_t i) {
-    const uint32_t* __restrict__ col = m.col[k];
-    const fr_t* __restrict__ val = m.val[k];
-    fr_t acc = fe_zero<FrCfg>();
-    const uint32_t e = m.rp[k][i + 1];
-    for (uint32_t t = m.rp[k][i]; t < e; t++) acc = acc + ldg_fr(val + t) * ldg_fr(z + __ldg(col + t));
-    return acc * fe_rr<FrCfg>();
+// Montgomery form.  Row lengths vary from 1 to a few hundred terms (S-box
+// inputs are long linear combinations, packing rows carry one term per bit),
+// so thread t takes row order[t] (rows by decreasing total length) and runs
+// over the row's A, B and C terms in one loop: the lanes of a warp then do
+// equal numbers of products whatever the split of their totals among A, B, C.
+// The R1CS check a b = c is made on the way.
+__device__ __forceinline__ void rows_abc(const CsrDev& m, const fr_t* __restrict__ z, uint32_t i, fr_t& a, fr_t& b,
+                                         fr_t& c) {
+    fr_t acc = fe_zero<FrCfg>(), sa = acc, sb = acc;
+    int k = 0;
+    const uint32_t* __restrict__ col = m.col[0];
+    const fr_t* __restrict__ val = m.val[0];
+    uint32_t t = __ldg(m.rp[0] + i), e = __ldg(m.rp[0] + i + 1);
+    for (;;) {
+        while (t == e) {  // matrix k done: keep its sum, go to the next
+            if (k == 0) sa = acc;
+            else if (k == 1) sb = acc;
+            if (++k == 3) break;
+            acc = fe_zero<FrCfg>();
+            col = k == 1 ? m.col[1] : m.col[2];
+            val = k == 1 ? m.val[1] : m.val[2];
+            t = __ldg((k == 1 ? m.rp[1] : m.rp[2]) + i);
+            e = __ldg((k == 1 ? m.rp[1] : m.rp[2]) + i + 1);
+        }
+        if (k == 3) break;
+        acc = acc + ldg_fr(val + t) * ldg_fr(z + __ldg(col + t));
+        t++;
+    }
+    a = sa * fe_rr<FrCfg>();
+    b = sb * fe_rr<FrCfg>();
+    c = acc * fe_rr<FrCfg>();
 }
 
-__global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const fr_t* __restrict__ z, uint32_t N, fr_t* abc,
-                                               int32_t* status) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const fr_t a = row_dot(m, 0, z, i);
+__global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const uint32_t* __restrict__ order,
+                                               const fr_t* __restrict__ z, uint32_t N, fr_t* abc, int32_t* status) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const uint32_t i = __ldg(order + t);
+    fr_t a, b, c;
+    rows_abc(m, z, i, a, b, c);
     st_fr2(abc + i, a);
-    const fr_t b = row_dot(m, 1, z, i);
     st_fr2(abc + (size_t)N + i, b);
-    const fr_t c = row_dot(m, 2, z, i);
     st_fr2(abc + 2 * (size_t)N + i, c);
     if (!fe_eq(a * b, c)) atomicOr(status, 1);
 }
@@ -264,18 +286,18 @@ __global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz
 // its quotient h + q N; every kernel covers all proofs (blockIdx.y or one
 // thread per proof).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_spmv3_many(CsrDev m, const fr_t* __restrict__ z, uint64_t wit, uint32_t N,
-                                                    fr_t* abc, int32_t* status) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const uint32_t q = blockIdx.y;
+__global__ void __launch_bounds__(256) k_spmv3_many(CsrDev m, const uint32_t* __restrict__ order,
+                                                    const fr_t* __restrict__ z, uint64_t wit, uint32_t N, fr_t* abc,
+                                                    int32_t* status) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const uint32_t q = blockIdx.y, i = __ldg(order + t);
     z += (size_t)q * wit;
     abc += (size_t)q * 3 * N;
-    const fr_t a = row_dot(m, 0, z, i);
+    fr_t a, b, c;
+    rows_abc(m, z, i, a, b, c);
     st_fr2(abc + i, a);
-    const fr_t b = row_dot(m, 1, z, i);
     st_fr2(abc + (size_t)N + i, b);
-    const fr_t c = row_dot(m, 2, z, i);
     st_fr2(abc + 2 * (size_t)N + i, c);
     if (!fe_eq(a * b, c)) atomicOr(status + q, 1);
 }
@@ -376,7 +398,7 @@ int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t*
     ACE_TRY(ntt_get_plan(ctx, pk->log_n, &plan));
     const uint32_t N = (uint32_t)pk->N;
     int prof = prof_begin(PROF_SPMV, st);
-    k_spmv3<<<(N + 255) / 256, 256, 0, st>>>(csr_of(pk), d_z, N, abc, d_status); ::ace::note_launch();
+    k_spmv3<<<(N + 255) / 256, 256, 0, st>>>(csr_of(pk), pk->d_row_order, d_z, N, abc, d_status); ::ace::note_launch();
     prof_end(prof, st, nullptr, pk->nnz[0] + pk->nnz[1] + pk->nnz[2]);
     NttScale none, cos, icos;
     cos.hi = plan->cos_hi;
@@ -612,7 +634,8 @@ static int prove_many_run(ace_ctx* ctx, const ace_pk* pk, uint32_t count, const 
     icos.h = plan->h;
     icos.brev = 1;
     int prof = prof_begin(PROF_SPMV, ss.main);
-    k_spmv3_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(csr_of(pk), d_z, wit, N, abc, d_status);
+    k_spmv3_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(csr_of(pk), pk->d_row_order, d_z, wit, N, abc,
+                                                                      d_status);
     ::ace::note_launch();
     prof_end(prof, ss.main, nullptr, (pk->nnz[0] + pk->nnz[1] + pk->nnz[2]) * count);
     ACE_TRY(ntt_run(*plan, abc, 3 * (int)count, true, true, none, cos, ss.main));

@@ -81,6 +81,21 @@ static int upload(ace_pk* pk, const void* src, size_t bytes, F** out) {
     return ACE_OK;
 }
 
+int pk_row_order(ace_pk* pk, const Csr mat[3]) {
+    const uint64_t N = mat[0].rp.size() - 1;
+    std::vector<uint64_t> key(N);
+    for (uint64_t i = 0; i < N; i++) {
+        const uint64_t a = mat[0].rp[i + 1] - mat[0].rp[i], b = mat[1].rp[i + 1] - mat[1].rp[i],
+                       c = mat[2].rp[i + 1] - mat[2].rp[i];
+        // 21 bits per length (rows are far shorter than 2^21 terms)
+        key[i] = ((a + b + c) << 42) | (std::min<uint64_t>(a, (1u << 21) - 1) << 21) | std::min<uint64_t>(b, (1u << 21) - 1);
+    }
+    std::vector<uint32_t> order(N);
+    for (uint64_t i = 0; i < N; i++) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return key[x] > key[y]; });
+    return upload(pk, order.data(), N * 4, &pk->d_row_order);
+}
+
 // columns of one matrix: col_sum[j] = sum_i M_ij L_i, threads over column ranges
 static void column_sums(const Csr& M, uint64_t N, uint64_t m, const std::vector<fr_t>& Lt, std::vector<fr_t>& out) {
     std::vector<uint32_t> cnt(m + 1, 0);
@@ -248,6 +263,7 @@ int ace_setup_toy(ace_ctx* ctx, const ace_circuit* c, uint64_t toxic_seed, ace_p
         SETUP_TRY(upload(pk, M.col.data(), M.col.size() * 4, &pk->d_col[k]));
         SETUP_TRY(upload(pk, M.val.data(), M.val.size() * sizeof(fr_t), &pk->d_val[k]));
     }
+    SETUP_TRY(pk_row_order(pk, c->mat));
     // queries
     SETUP_TRY(build_query<fp_t>(pk, u, 0, pk->A, st));
     SETUP_TRY(build_query<fp_t>(pk, v, 0, pk->B1, st));

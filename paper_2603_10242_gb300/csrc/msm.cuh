@@ -2,9 +2,9 @@
 //
 // sum_i k_i P_i for affine P_i (Montgomery form) and canonical Fr scalars k_i:
 //   1. signed c-bit digits of every scalar; scalars 0 contribute nothing and
-//      scalars 1 go to an extra "ones" window of B virtual buckets (their sum
-//      is that window's plain total), so the frequent {0,1} witness values
-//      neither cost K additions nor pile onto one bucket;
+//      scalars 1 go to an extra "ones" window of up to B virtual buckets
+//      (their sum is that window's plain total), so the frequent {0,1}
+//      witness values neither cost K additions nor pile onto one bucket;
 //   2. counting sort of (bucket, point) pairs: histogram, exclusive scan,
 //      scatter;
 //   3. one mixed XYZZ addition per entry into its bucket;
@@ -42,6 +42,12 @@ struct MsmPlan {
     uint32_t batch = 1;
     // most threads one bucket's entries may be split among (1: no split)
     uint32_t max_split = 16;
+    // virtual buckets the ones window uses (a power of two <= B, about n / 64):
+    // scalar 1 of point i goes to bucket i mod B1.  Enough buckets to spread
+    // the additions over many threads, few enough that the window's plain sum
+    // in the reduction stays short (its other buckets are empty)
+    uint32_t B1 = 0;
+    uint32_t ones_mask() const { return (B1 ? B1 : B) - 1u; }
     uint32_t bucket_windows() const { return tabled ? 1u : (uint32_t)K; }
     uint32_t windows() const { return bucket_windows() + 1; }  // + ones window
     uint32_t keys_per() const { return windows() * B; }         // keys of one MSM

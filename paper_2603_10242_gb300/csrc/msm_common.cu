@@ -72,6 +72,8 @@ static MsmPlan plan_for(size_t n, int c, bool tabled) {
     p.L = 1u << p.lambda;
     p.M = p.B / p.L;
     p.tabled = tabled;
+    p.B1 = 1;
+    while (p.B1 < p.B && (size_t)p.B1 * 64 < n) p.B1 *= 2;
     return p;
 }
 
@@ -212,7 +214,7 @@ __device__ __forceinline__ int scalar_kind(const uint32_t s[8]) {
 // multiplies point t mod n; each MSM has its own keys_per keys.
 template <int C, bool SCATTER, bool TAB>
 __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t total, size_t n, uint32_t keys_per,
-                             uint32_t* cnt, uint32_t* entries) {
+                             uint32_t ones_mask, uint32_t* cnt, uint32_t* entries) {
     constexpr int K = (255 + C - 1) / C;
     constexpr uint32_t B = 1u << (C - 1);
     constexpr uint32_t BW = TAB ? 1u : (uint32_t)K;
@@ -226,7 +228,7 @@ __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t total, size
     const size_t i = t - q * n;               // which point
     cnt += q * keys_per;
     if (kind == 1) {
-        uint32_t key = BW * B + (uint32_t)(i & (B - 1));
+        uint32_t key = BW * B + ((uint32_t)i & ones_mask);
         if (SCATTER) {
             uint32_t pos = atomicAdd(&cnt[key], 1u);
             entries[pos] = (uint32_t)i;
@@ -265,12 +267,12 @@ __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t total, size
 template <bool SCATTER>
 void launch_digits(const MsmPlan& plan, const uint32_t* sc, uint32_t* cnt, uint32_t* entries, cudaStream_t st) {
     const size_t total = plan.scalars(), n = plan.n;
-    const uint32_t kp = plan.keys_per();
+    const uint32_t kp = plan.keys_per(), om = plan.ones_mask();
     unsigned grid = (unsigned)((total + 255) / 256);
     switch (plan.c * 2 + (plan.tabled ? 1 : 0)) {
 #define ACE_DIGITS_CASE(CC)                                                                                        \
-    case 2 * CC: k_msm_digits<CC, SCATTER, false><<<grid, 256, 0, st>>>(sc, total, n, kp, cnt, entries); break; \
-    case 2 * CC + 1: k_msm_digits<CC, SCATTER, true><<<grid, 256, 0, st>>>(sc, total, n, kp, cnt, entries); break;
+    case 2 * CC: k_msm_digits<CC, SCATTER, false><<<grid, 256, 0, st>>>(sc, total, n, kp, om, cnt, entries); break; \
+    case 2 * CC + 1: k_msm_digits<CC, SCATTER, true><<<grid, 256, 0, st>>>(sc, total, n, kp, om, cnt, entries); break;
         ACE_DIGITS_CASE(6) ACE_DIGITS_CASE(7) ACE_DIGITS_CASE(8) ACE_DIGITS_CASE(9) ACE_DIGITS_CASE(10)
         ACE_DIGITS_CASE(11) ACE_DIGITS_CASE(12) ACE_DIGITS_CASE(13) ACE_DIGITS_CASE(14) ACE_DIGITS_CASE(15)
         ACE_DIGITS_CASE(16) ACE_DIGITS_CASE(17) ACE_DIGITS_CASE(18) ACE_DIGITS_CASE(19) ACE_DIGITS_CASE(20)

@@ -1065,13 +1065,141 @@ ACE_HD Fe<C> fe_pow(const Fe<C>& a, const uint32_t* e) {
     }
     return acc;
 }
-// inverse by Fermat (a^{m-2}); inverse of 0 is 0
+#if defined(__CUDA_ARCH__)
+// Inverse on the device by the binary extended Euclidean algorithm (Hankerson,
+// Menezes and Vanstone, Guide to Elliptic Curve Cryptography, Algorithm 2.22)
+// applied to the stored residue x = a R: with u = x, v = m and invariants
+// x1 x = u, x2 x = v (mod m), halve whichever of u, v is even (halving x1 or
+// x2 mod m alongside) and subtract the smaller from the larger until one of
+// them is 1; its x1 or x2 is then (a R)^-1 = a^-1 R^-1, and two Montgomery
+// products with R^2 give a^-1 R.  About 2 x 254 halvings and 254
+// subtractions of 8-limb values instead of Fermat's ~380 sequential
+// products.  Variable time: the device inverts public values only (affine
+// forms of results, proof elements and key points).
+namespace detail {
+ACE_DEV bool inv_is_one(const uint32_t* x) {
+    uint32_t o = x[0] ^ 1u;
+#pragma unroll
+    for (int i = 1; i < 8; i++) o |= x[i];
+    return o == 0;
+}
+ACE_DEV void inv_shr1(uint32_t* x) {
+#pragma unroll
+    for (int i = 0; i < 7; i++) x[i] = (x[i] >> 1) | (x[i + 1] << 31);
+    x[7] >>= 1;
+}
+// x = x / 2 mod m (x < m, m odd and < 2^255: x + m does not overflow)
+template <class C>
+ACE_DEV void inv_half(uint32_t* x) {
+    if (x[0] & 1u) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            c += (uint64_t)x[i] + mod_limb<C>(i);
+            x[i] = (uint32_t)c;
+            c >>= 32;
+        }
+    }
+    inv_shr1(x);
+}
+// x = x - y (plain, x >= y)
+ACE_DEV void inv_sub(uint32_t* x, const uint32_t* y) {
+    int64_t b = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        b += (int64_t)x[i] - y[i];
+        x[i] = (uint32_t)b;
+        b >>= 32;
+    }
+}
+// x = x - y mod m (x, y < m)
+template <class C>
+ACE_DEV void inv_sub_mod(uint32_t* x, const uint32_t* y) {
+    int64_t b = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        b += (int64_t)x[i] - y[i];
+        x[i] = (uint32_t)b;
+        b >>= 32;
+    }
+    if (b) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            c += (uint64_t)x[i] + mod_limb<C>(i);
+            x[i] = (uint32_t)c;
+            c >>= 32;
+        }
+    }
+}
+ACE_DEV bool inv_geq(const uint32_t* x, const uint32_t* y) {
+    bool gt = false, eq = true;
+#pragma unroll
+    for (int i = 7; i >= 0; i--) {
+        gt = gt || (eq && x[i] > y[i]);
+        eq = eq && x[i] == y[i];
+    }
+    return gt || eq;
+}
+ACE_DEV bool inv_is_zero(const uint32_t* x) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) o |= x[i];
+    return o == 0;
+}
+}  // namespace detail
+
+template <class C>
+__device__ __noinline__ Fe<C> d_inv_binary(Fe<C> a) {
+    if (fe_is_zero(a)) return a;
+    uint32_t u[8], v[8], x1[8], x2[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        u[i] = a.v[i];
+        v[i] = mod_limb<C>(i);
+        x1[i] = i == 0 ? 1u : 0u;
+        x2[i] = 0u;
+    }
+    // the loop ends within 2 x 256 halvings and 256 subtractions; the bound
+    // and the zero tests only guard it against a non-canonical input (a
+    // multiple of m would drive u to 0)
+    for (int it = 0; it < 1024 && !detail::inv_is_one(u) && !detail::inv_is_one(v); it++) {
+        if (detail::inv_is_zero(u) || detail::inv_is_zero(v)) break;
+        while (!(u[0] & 1u)) {
+            detail::inv_shr1(u);
+            detail::inv_half<C>(x1);
+        }
+        while (!(v[0] & 1u)) {
+            detail::inv_shr1(v);
+            detail::inv_half<C>(x2);
+        }
+        if (detail::inv_geq(u, v)) {
+            detail::inv_sub(u, v);
+            detail::inv_sub_mod<C>(x1, x2);
+        } else {
+            detail::inv_sub(v, u);
+            detail::inv_sub_mod<C>(x2, x1);
+        }
+    }
+    Fe<C> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = detail::inv_is_one(u) ? x1[i] : x2[i];
+    return r * fe_rr<C>() * fe_rr<C>();
+}
+#endif
+
+// inverse of a (Montgomery form); inverse of 0 is 0.  Host: Fermat (a^{m-2});
+// device: the binary algorithm above
 template <class C>
 ACE_HD Fe<C> fe_inv(const Fe<C>& a) {
+#if defined(__CUDA_ARCH__)
+    return d_inv_binary<C>(a);
+#else
     uint32_t e[8];
     for (int i = 0; i < 8; i++) e[i] = mod_limb<C>(i);
     e[0] -= 2;  // m is odd and > 2: no borrow
     return fe_pow(a, e);
+#endif
 }
 
 // ---------------------------------------------------------------------------

@@ -39,7 +39,8 @@ def test_field_ops_vs_oracle(field, mod):
     for op, name in ((0, "add"), (1, "sub"), (2, "mul"), (3, None), (4, "inv")):
         ace.debug_field_op(field, op, da, db, out, n)
         got = gu.bytes_ints(gu.host(out))
-        for i in range(0, n, 7):
+        # every inverse (the device inversion's path depends on the value)
+        for i in range(0, n, 1 if name == "inv" else 7):
             if name == "inv":
                 want = O.field_op(which, "inv", a[i]) if a[i] else 0
             elif name is None:
@@ -64,7 +65,7 @@ def test_fp2_ops_vs_python():
         assert (got[2 * i], got[2 * i + 1]) == ((a0 * b0 - a1 * b1) % P, (a0 * b1 + a1 * b0) % P)
     ace.debug_field_op(2, 4, da, db, out, n)
     got = gu.bytes_ints(gu.host(out))
-    for i in range(1, n, 5):
+    for i in range(1, n):
         a0, a1 = a[i]
         x0, x1 = got[2 * i], got[2 * i + 1]
         assert ((a0 * x0 - a1 * x1) % P, (a0 * x1 + a1 * x0) % P) == (1, 0)

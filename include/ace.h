@@ -148,8 +148,10 @@ int ace_pk_info(const ace_pk* pk, uint64_t info[ACE_INFO_LEN]);
 /* Copy one proving-key point to host memory (affine, canonical).
  * query: 0 A_j = [u_j(tau)]1, 1 B1_j = [v_j(tau)]1, 2 B2_j = [v_j(tau)]2 (out is
  * an ace_g2_affine), 3 L_j = [(beta u_j + alpha v_j + w_j)(tau)/delta]1 (j > 1),
- * 4 H_i = [tau^i Z(tau)/delta]1 (i <= N-2); j indexes the witness, i the
- * domain.  Infinity is returned as zeros. */
+ * 4 H_i = [L'_i(tau) Z(tau)/delta]1 (i < N), L'_i the Lagrange basis of the
+ * coset g H = {5 omega^i} (the prover multiplies it by the quotient's values
+ * on that coset); j indexes the witness, i the domain.  Infinity is returned
+ * as zeros. */
 int ace_pk_point(const ace_pk* pk, int query, size_t index, void* out);
 
 /* ---- hot path ----------------------------------------------------------- */

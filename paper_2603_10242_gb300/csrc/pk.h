@@ -42,7 +42,7 @@ struct ace_pk {
     uint32_t* d_row_order = nullptr;  // N rows by decreasing total length (sparse-product schedule)
     ace::Query<ace::fp_t> A, B1, L;
     ace::Query<ace::fp2_t> B2;   // same indices as B1
-    ace::g1_aff* d_H = nullptr;  // window table of N points: d_H[p] = H_{bitrev(p)}, H_{N-1} = infinity
+    ace::g1_aff* d_H = nullptr;  // window table of N points: H_i = [L'_i(tau) Z(tau)/delta]_1, coset Lagrange basis
     ace::MsmPlan H_plan;         // tabled plan of the H query
     ace::PkFixed* d_fixed = nullptr;
     // 8-bit window tables (32 x 255 points) of alpha1, beta1, delta1 and delta2

@@ -1,11 +1,12 @@
 // pk_io.cu -- persistence of a proving key: setup at 2^20 and above is the
 // expensive step, so a serving process reloads the key instead of redoing it.
 //
-// File layout (little-endian): "ACEPK001" | u32 version (1) | u32 header
+// File layout (little-endian): "ACEPK001" | u32 version (2) | u32 header
 // words | header (params, N, m, nnz[3], query counts) | circuit (CSR of A, B,
 // C; round constants; MDS; chain constants) | queries (indices, Montgomery
-// affine points) | H query | fixed points | verifying key.  Each array is
-// preceded by its byte count (u64).
+// affine points) | H query (coset Lagrange basis; version 1 files held the
+// monomial basis and are refused) | fixed points | verifying key.  Each array
+// is preceded by its byte count (u64).
 #include <stdio.h>
 #include <string.h>
 
@@ -15,7 +16,7 @@ namespace ace {
 namespace {
 
 const char MAGIC[8] = {'A', 'C', 'E', 'P', 'K', '0', '0', '1'};
-const uint32_t VERSION = 1;
+const uint32_t VERSION = 2;
 
 struct Writer {
     FILE* f;

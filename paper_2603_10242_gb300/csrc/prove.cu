@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const uint32_t* __restr
     if (!fe_eq(a * b, c)) atomicOr(status, 1);
 }
 
-// q_i = (a_i b_i - c_i) * zinv, written over a
+// q_i = (a_i b_i - c_i) * zinv, written over a (zinv in Montgomery form keeps
+// q in Montgomery form; its plain value gives the canonical q)
 __global__ void k_quotient(fr_t* abc, uint32_t N, fr_t zinv) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -392,8 +393,12 @@ static CsrDev csr_of(const ace_pk* pk) {
     return m;
 }
 
-// steps 1-2: leaves canonical h in bit-reversed order in abc[0..N)
-int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t* d_status, cudaStream_t st) {
+// steps 1-2.  coset = true (proving): leaves the canonical values h(g omega^i)
+// in natural order in abc[0..N), the scalars of the H query in the coset
+// Lagrange basis; coset = false: the canonical coefficients of h in
+// bit-reversed order (one more inverse transform)
+int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t* d_status, cudaStream_t st,
+            bool coset) {
     NttPlan* plan = nullptr;
     ACE_TRY(ntt_get_plan(ctx, pk->log_n, &plan));
     const uint32_t N = (uint32_t)pk->N;
@@ -411,8 +416,14 @@ int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t*
     icos.brev = 1;
     ACE_TRY(ntt_run(*plan, abc, 3, true, true, none, cos, st));
     ACE_TRY(ntt_run(*plan, abc, 3, false, false, none, none, st));
-    k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, plan->zinv); ::ace::note_launch();
-    ACE_TRY(ntt_run(*plan, abc, 1, true, true, none, icos, st));
+    if (coset) {
+        // (a b - c) is in Montgomery form; a product with the plain value of
+        // (g^N - 1)^-1 leaves Montgomery form: canonical h(g omega^i)
+        k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, fe_from_mont(plan->zinv)); ::ace::note_launch();
+    } else {
+        k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, plan->zinv); ::ace::note_launch();
+        ACE_TRY(ntt_run(*plan, abc, 1, true, true, none, icos, st));
+    }
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }
@@ -520,7 +531,7 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     }
     ::ace::note_launch();
     prof_end(pv, ss.aux[4], nullptr, 1);
-    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, ss.main));
+    ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, ss.main, true));
     ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, ss.main));
     for (int k = 0; k < 5; k++) {
         ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], ss.aux[k]));
@@ -624,15 +635,11 @@ static int prove_many_run(ace_ctx* ctx, const ace_pk* pk, uint32_t count, const 
     k_prove_var_many<<<(count + 63) / 64, 64, 0, ss.aux[4]>>>(res1 + count, res1 + 2 * (size_t)count, rsv, count,
                                                               vterm); ::ace::note_launch();
     // QAP of every proof, then the H MSM, on the main stream
-    NttScale none, cos, icos;
+    NttScale none, cos;
     cos.hi = plan->cos_hi;
     cos.lo = plan->cos_lo;
     cos.h = plan->h;
     cos.brev = 1;
-    icos.hi = plan->icos_hi;
-    icos.lo = plan->icos_lo;
-    icos.h = plan->h;
-    icos.brev = 1;
     int prof = prof_begin(PROF_SPMV, ss.main);
     k_spmv3_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(csr_of(pk), pk->d_row_order, d_z, wit, N, abc,
                                                                       d_status);
@@ -640,8 +647,9 @@ static int prove_many_run(ace_ctx* ctx, const ace_pk* pk, uint32_t count, const 
     prof_end(prof, ss.main, nullptr, (pk->nnz[0] + pk->nnz[1] + pk->nnz[2]) * count);
     ACE_TRY(ntt_run(*plan, abc, 3 * (int)count, true, true, none, cos, ss.main));
     ACE_TRY(ntt_run(*plan, abc, 3 * (int)count, false, false, none, none, ss.main));
-    k_quotient_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(abc, N, plan->zinv, h); ::ace::note_launch();
-    ACE_TRY(ntt_run(*plan, h, (int)count, true, true, none, icos, ss.main));
+    // canonical h(g omega^i) of every proof (see qap_run)
+    k_quotient_many<<<dim3((N + 255) / 256, count), 256, 0, ss.main>>>(abc, N, fe_from_mont(plan->zinv), h);
+    ::ace::note_launch();
     ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)h, a0, res1, nullptr, ss.main));
     for (int k = 0; k < 5; k++) {
         ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], ss.aux[k]));
@@ -679,7 +687,7 @@ int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out
     fr_t* abc = (fr_t*)ctx->scratch[0].take(3 * pk->N * sizeof(fr_t));
     int32_t* status = (int32_t*)ctx->scratch[0].take(16);
     ACE_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-    ACE_TRY(qap_run(ctx, pk, (const fr_t*)d_z, abc, status, st));
+    ACE_TRY(qap_run(ctx, pk, (const fr_t*)d_z, abc, status, st, false));
     return fr_bitrev_copy(abc, (fr_t*)d_h_out, pk->log_n, 1, st);
 }
 

@@ -4,12 +4,23 @@
 // Scalars (host):  L_i(tau) = (tau^N - 1) omega^i / (N (tau - omega^i)) by
 // batch inversion; u_j, v_j, w_j = sum_i {A,B,C}_ij L_i(tau) over the
 // columns; L-query (beta u_j + alpha v_j + w_j)/delta (j > 1) and the
-// verifying-key inputs with /gamma (j <= 1); H-query tau^i Z(tau)/delta.
+// verifying-key inputs with /gamma (j <= 1); H-query in the Lagrange basis
+// of the coset g H (see below).
 // Points (device): fixed-base multiplication of the generators, stored in
-// Montgomery affine form; zero scalars are compacted out of the queries, and
-// the H query is stored in bit-reversed order to match the quotient the QAP
-// step leaves in bit-reversed order.  Every query is kept with its MSM window
-// table (window w holds 2^(c w) times the points).
+// Montgomery affine form; zero scalars are compacted out of the queries.
+// Every query is kept with its MSM window table (window w holds 2^(c w) times
+// the points).
+//
+// H query.  The quotient h = (A B - C) / Z has degree at most N - 2, so its N
+// values on the coset g H = {x_i = g omega^i} determine it:
+//   h(tau) = sum_i h(x_i) L'_i(tau),
+//   L'_i(tau) = x_i (tau^N - g^N) / (N g^N (tau - x_i))
+// (the Lagrange basis of g H, whose vanishing polynomial is X^N - g^N).  The
+// key stores H_i = [L'_i(tau) Z(tau) / delta]_1 for i < N in natural order,
+// so the prover feeds the coset values of h, which the QAP step produces
+// anyway, straight into the H MSM: sum_i h(x_i) H_i = [h(tau) Z(tau) /
+// delta]_1, the same point as sum_e h_e [tau^e Z(tau) / delta]_1 over the
+// coefficients, without the last inverse transform.
 #include <string.h>
 
 #include <algorithm>
@@ -50,15 +61,6 @@ int pk_alloc(ace_pk* pk, void** p, size_t bytes) {
     pk->allocs.push_back({*p, bytes});
     pk->bytes += bytes;
     return ACE_OK;
-}
-
-static uint32_t h_brev(uint32_t x, int bits) {
-    uint32_t r = 0;
-    for (int i = 0; i < bits; i++) {
-        r = (r << 1) | (x & 1u);
-        x >>= 1;
-    }
-    return r;
 }
 
 static fr_t pow_u64(fr_t a, uint64_t e) {
@@ -274,16 +276,37 @@ int ace_setup_toy(ace_ctx* ctx, const ace_circuit* c, uint64_t toxic_seed, ace_p
         lq2[1] = fe_zero<FrCfg>();
         SETUP_TRY(build_query<fp_t>(pk, lq2, 0, pk->L, st));
     }
-    // H query, bit-reversed: position p holds tau^e Z(tau)/delta with e = bitrev(p), e <= N-2
+    // H query in the Lagrange basis of the coset g H (natural order):
+    // H_i = K x_i / (tau - x_i) with K = (tau^N - g^N) Z(tau) / (N g^N delta),
+    // or, when tau lies on the coset (tau = x_k), H_i = [i = k] Z(tau)/delta
     {
         std::vector<fr_t> hs(N);
-        fr_t zd = zt * dinv, t = one;
-        std::vector<fr_t> hq(N);
+        const fr_t gc = fe_from_u32<FrCfg>(5), gn = pow_u64(gc, N), tn = pow_u64(tau, N);
+        std::vector<fr_t> xs(N), dx(N), pre2(N);
+        fr_t x = gc, acc = one;
+        bool on_coset = false;
         for (uint64_t i = 0; i < N; i++) {
-            hq[i] = (i + 1 < N) ? t * zd : fe_zero<FrCfg>();
-            t = t * tau;
+            xs[i] = x;
+            dx[i] = tau - x;
+            if (fe_is_zero(dx[i])) on_coset = true;
+            x = x * omega;
         }
-        for (uint64_t p = 0; p < N; p++) hs[p] = fe_from_mont(hq[h_brev((uint32_t)p, log_n)]);
+        if (on_coset) {
+            for (uint64_t i = 0; i < N; i++) hs[i] = fe_is_zero(dx[i]) ? fe_from_mont(zt * dinv) : fe_zero<FrCfg>();
+        } else {
+            for (uint64_t i = 0; i < N; i++) {
+                pre2[i] = acc;
+                acc = acc * dx[i];
+            }
+            acc = fe_inv(acc);
+            for (uint64_t i = N; i-- > 0;) {
+                fr_t inv_i = acc * pre2[i];
+                acc = acc * dx[i];
+                dx[i] = inv_i;
+            }
+            const fr_t K = (tn - gn) * zt * ninv * fe_inv(gn) * dinv;
+            for (uint64_t i = 0; i < N; i++) hs[i] = fe_from_mont(K * xs[i] * dx[i]);
+        }
         fr_t* d_sc = nullptr;
         SETUP_TRY(upload(pk, hs.data(), N * sizeof(fr_t), &d_sc));
         SETUP_TRY(pk_alloc_table<fp_t>(pk, (uint32_t)N, &pk->H_plan, &pk->d_H));
@@ -371,13 +394,12 @@ int ace_pk_point(const ace_pk* pk, int query, size_t index, void* out) {
     }
     ACE_TRY_CUDA(cudaSetDevice(pk->ctx->device));
     if (query == 4) {
-        if (index + 1 >= pk->N) {
+        if (index >= pk->N) {
             set_error("ace_pk_point: H index %zu out of range", index);
             return ACE_E_ARG;
         }
         g1_aff p;
-        uint32_t pos = h_brev((uint32_t)index, pk->log_n);
-        ACE_TRY_CUDA(cudaMemcpy(&p, pk->d_H + pos, sizeof p, cudaMemcpyDeviceToHost));
+        ACE_TRY_CUDA(cudaMemcpy(&p, pk->d_H + index, sizeof p, cudaMemcpyDeviceToHost));
         canon_point<fp_t>(p, out);
         return ACE_OK;
     }

@@ -1,7 +1,8 @@
 """GPU parity of the full Groth16 path against the CPU oracle.
 
 Circuit and witness (host, byte-identical to the oracle's), setup points
-(sampled, against scalar multiples of the oracle's setup scalars), the QAP
+(sampled, against scalar multiples of the oracle's setup scalars; the H query
+in the coset Lagrange basis from its product definition), the QAP
 quotient (bit-exact), and whole proofs: bit-exact against the oracle's own
 prover at small sizes and against the in-the-exponent proof (no NTT, no MSM
 on the oracle side) up to the 2^20 block-scale circuit, plus the oracle's
@@ -24,6 +25,27 @@ SMALL = [
     (10, 1024, 4, 0, 0),      # the 2^10 single-proof circuit
     (12, 4000, 8, 8, 172),    # packing rows, zero rows 4000..4095
 ]
+
+
+def _coset_h_scalar(opk, log_n, i):
+    """Scalar of H query point i: L'_i(tau) Z(tau)/delta, L'_i the Lagrange
+    basis of the coset g H (g = 5) by its product definition
+    prod_{j != i} (tau - x_j) / (x_i - x_j), x_j = g omega^j, at
+    tau = h_1 / h_0 from the oracle's monomial scalars h_e = tau^e Z(tau)/delta."""
+    R = gu.R
+    h0, h1 = opk.scalar("h", 0), opk.scalar("h", 1)
+    tau = h1 * pow(h0, -1, R) % R
+    n = 1 << log_n
+    w = O.fr_root_of_unity(log_n)
+    xi = 5 * pow(w, i, R) % R
+    num = den = 1
+    x = 5
+    for j in range(n):
+        if j != i:
+            num = num * (tau - x) % R
+            den = den * (xi - x) % R
+        x = x * w % R
+    return num * pow(den, -1, R) * h0 % R
 
 
 def _pair(params, seed=1):
@@ -54,8 +76,8 @@ def test_setup_points_match_oracle_scalars(params):
         assert pk.point("B2", j) == O.g2_mul(g2, opk.scalar("v", j))
         if j > 1:
             assert pk.point("L", j) == O.g1_mul(g1, opk.scalar("l", j))
-    for i in sorted({0, 1, lc.N // 2, lc.N - 2}):
-        assert pk.point("H", i) == O.g1_mul(g1, opk.scalar("h", i))
+    for i in sorted({0, 1, lc.N // 2, lc.N - 2, lc.N - 1}):
+        assert pk.point("H", i) == O.g1_mul(g1, _coset_h_scalar(opk, params[0], i)), i
     # verifying key
     vk = bytes(pk.vk)
     assert vk[0:64] == opk.point("fixed", 0)
@@ -152,8 +174,8 @@ def test_block_scale_proof_in_the_exponent(log_n):
     g1 = O.g1_generator()
     for j in (2, lc.m // 3, lc.m - 1):
         assert pk.point("A", j) == O.g1_mul(g1, opk.scalar("u", j))
-    for i in (0, lc.N - 2):
-        assert pk.point("H", i) == O.g1_mul(g1, opk.scalar("h", i))
+    for i in (0, lc.N - 1):
+        assert pk.point("H", i) == O.g1_mul(g1, _coset_h_scalar(opk, log_n, i))
 
 
 def test_pk_save_load_roundtrip(tmp_path):

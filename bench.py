@@ -51,10 +51,10 @@ SM_COUNT = 152
 IMAD_PER_CLK_PER_SM = 64
 SM_MAX_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the G1 bucket
-# accumulation kernel inside the 2^20 proofs, per mixed addition: 1.830 GB on
+# accumulation kernel inside the 2^20 proofs, per mixed addition: 1.828 GB on
 # average over the 16 launches of four proofs (ncu capture summarised in
 # profiles/g1_bucket_acc_msm_2p20.md) for 13.62 M additions per launch.
-G1_BUCKET_DRAM_BYTES_PER_MADD = 1.830e9 / 13.619e6
+G1_BUCKET_DRAM_BYTES_PER_MADD = 1.828e9 / 13.619e6
 
 
 def _dist_env():

@@ -112,6 +112,7 @@ void ctx_destroy_now(ace_ctx* c) {
         cudaEventDestroy(sl.ev_start);
         cudaEventDestroy(sl.ev_done);
         for (auto e : sl.ev_aux) cudaEventDestroy(e);
+        if (sl.ev_sort) cudaEventDestroy(sl.ev_sort);
     }
     ntt_release_plans(c);
     if (c->g1_fixed_tab) dev_free(c, c->g1_fixed_tab, 32 * 255 * sizeof(g1_aff));

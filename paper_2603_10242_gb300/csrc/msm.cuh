@@ -82,14 +82,28 @@ struct MsmBufs {
     bool carve(Alloc& a, const MsmPlan& p, bool need_conv);
 };
 
+// The sorted (bucket, point) entries of one MSM: bucket offsets (keys + 1),
+// entries, bucket order.  A second MSM with the same scalars and plan over
+// other bases (the B query on G1 and on G2) reuses them instead of sorting.
+struct MsmSorted {
+    const uint32_t* offsets = nullptr;
+    const uint32_t* entries = nullptr;
+    const uint32_t* order = nullptr;
+};
+
 // Run one MSM (plan.batch of them over the same bases).  d_bases: n affine
 // points; base_mont says whether they are in Montgomery form.  Writes the
 // XYZZ results (Montgomery, plan.batch of them) to d_res if non-null and the
 // canonical affine results to d_out if non-null.  Scratch comes from `ar`
 // (size it with msm_scratch_bytes).  Asynchronous on st.
+// pre: sorted entries of an earlier MSM with the same scalars and plan (then
+// d_scalars is not read; the caller orders st after that sort).  sorted /
+// sorted_ev: hand out this run's sorted entries, and record sorted_ev on st
+// when they are complete; they stay valid while `ar` is not reused.
 template <class F>
 int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
-            Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st);
+            Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st, const MsmSorted* pre = nullptr,
+            MsmSorted* sorted = nullptr, cudaEvent_t sorted_ev = nullptr);
 template <class F>
 size_t msm_scratch_bytes(const MsmPlan& plan, bool base_mont);
 

@@ -4,7 +4,7 @@
 
 namespace ace {
 template int msm_run<fp_t>(const MsmPlan&, const Affine<fp_t>*, bool, const uint32_t*, Arena&, Xyzz<fp_t>*,
-                           Affine<fp_t>*, cudaStream_t);
+                           Affine<fp_t>*, cudaStream_t, const MsmSorted*, MsmSorted*, cudaEvent_t);
 template size_t msm_scratch_bytes<fp_t>(const MsmPlan&, bool);
 template int msm_build_table<fp_t>(const MsmPlan&, const Affine<fp_t>*, Affine<fp_t>*, cudaStream_t);
 }  // namespace ace

@@ -270,7 +270,8 @@ int msm_build_table(const MsmPlan& plan, const Affine<F>* pts, Affine<F>* tab, c
 
 template <class F>
 int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const uint32_t* d_scalars,
-            Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st) {
+            Arena& ar, Xyzz<F>* d_res, Affine<F>* d_out, cudaStream_t st, const MsmSorted* pre,
+            MsmSorted* sorted, cudaEvent_t sorted_ev) {
     if (plan.n == 0) {
         k_msm_empty<F><<<(plan.batch + 31) / 32, 32, 0, st>>>(plan.batch, d_res, d_out); ::ace::note_launch();
         ACE_TRY_CUDA(cudaGetLastError());
@@ -288,19 +289,32 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
         k_bases_to_mont<F><<<(unsigned)((plan.n + 127) / 128), 128, 0, st>>>(d_bases, plan.n, b.conv); ::ace::note_launch();
         bases = b.conv;
     }
-    int prof_sort = prof_begin(PROF_SORT, st);
-    ACE_TRY_CUDA(cudaMemsetAsync(b.offsets, 0, (keys + 1) * sizeof(uint32_t), st));
-    launch_digits<false>(plan, d_scalars, b.offsets, nullptr, st);
-    ACE_TRY(scan_exclusive_u32(b.offsets, keys + 1, b.scan_tmp, st));
-    ACE_TRY_CUDA(cudaMemcpyAsync(b.cursor, b.offsets, keys * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    launch_digits<true>(plan, d_scalars, b.cursor, b.entries, st);
-    ACE_TRY(bucket_order(b.offsets, keys, b.size_bins, b.scan_tmp, b.order, st));
-    prof_end(prof_sort, st, nullptr, n);
+    const uint32_t *offsets = b.offsets, *entries = b.entries, *order = b.order;
+    if (pre) {
+        offsets = pre->offsets;
+        entries = pre->entries;
+        order = pre->order;
+    } else {
+        int prof_sort = prof_begin(PROF_SORT, st);
+        ACE_TRY_CUDA(cudaMemsetAsync(b.offsets, 0, (keys + 1) * sizeof(uint32_t), st));
+        launch_digits<false>(plan, d_scalars, b.offsets, nullptr, st);
+        ACE_TRY(scan_exclusive_u32(b.offsets, keys + 1, b.scan_tmp, st));
+        ACE_TRY_CUDA(cudaMemcpyAsync(b.cursor, b.offsets, keys * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        launch_digits<true>(plan, d_scalars, b.cursor, b.entries, st);
+        ACE_TRY(bucket_order(b.offsets, keys, b.size_bins, b.scan_tmp, b.order, st));
+        prof_end(prof_sort, st, nullptr, n);
+    }
+    if (sorted) {
+        sorted->offsets = offsets;
+        sorted->entries = entries;
+        sorted->order = order;
+    }
+    if (sorted_ev) ACE_TRY_CUDA(cudaEventRecord(sorted_ev, st));
     int prof = prof_begin(sizeof(F) == sizeof(fp_t) ? PROF_G1_BUCKET : PROF_G2_BUCKET, st);
     const uint32_t split = bucket_split<F>(plan);
-    k_bucket_acc<F><<<(unsigned)(((uint64_t)keys * split + 127) / 128), 128, 0, st>>>(bases, b.entries, b.offsets, b.order,
+    k_bucket_acc<F><<<(unsigned)(((uint64_t)keys * split + 127) / 128), 128, 0, st>>>(bases, entries, offsets, order,
                                                                               keys, split, b.partial); ::ace::note_launch();
-    prof_end(prof, st, b.offsets + keys, 0);
+    prof_end(prof, st, offsets + keys, 0);
     if (split > 1) {
         k_bucket_combine<F><<<(keys + 127) / 128, 128, 0, st>>>(b.partial, keys, split, b.buckets); ::ace::note_launch();
     }

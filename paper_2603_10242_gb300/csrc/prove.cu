@@ -452,7 +452,7 @@ size_t prove_slot_bytes(const ace_pk* pk, int arena) { return prove_plans(pk).sl
 
 template <class F>
 static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z, Arena& ar, Xyzz<F>* res,
-                        cudaStream_t s) {
+                        cudaStream_t s, MsmSorted* sorted = nullptr, cudaEvent_t sorted_ev = nullptr) {
     fr_t* zq = (fr_t*)ar.take((size_t)q.count * sizeof(fr_t) + 32);
     if (!zq) {
         set_error("prove: arena too small");
@@ -462,7 +462,7 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
         k_gather<<<(q.count + 255) / 256, 256, 0, s>>>(d_z, q.d_idx, q.count, zq);
         ::ace::note_launch();
     }
-    return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
+    return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s, nullptr, sorted, sorted_ev);
 }
 
 // Full proof on proving slot `slot`, on the slot's streams of priority level
@@ -508,8 +508,12 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     ACE_TRY_CUDA(cudaEventRecord(sl.ev_start, ss.main));
     for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[k], sl.ev_start, 0));
     ACE_TRY(gathered_msm<fp_t>(pl.A, pk->A, d_z, sl.ar[1], res1 + 1, ss.aux[0]));
-    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, sl.ar[2], res1 + 2, ss.aux[1]));
-    ACE_TRY(gathered_msm<fp2_t>(pl.B, pk->B2, d_z, sl.ar[3], res2, ss.aux[2]));
+    // B1 and B2 multiply the same witness values under one plan: B2 takes B1's
+    // sorted entries (B1's arena is not reused before this proof ends)
+    MsmSorted sortB;
+    ACE_TRY(gathered_msm<fp_t>(pl.B, pk->B1, d_z, sl.ar[2], res1 + 2, ss.aux[1], &sortB, sl.ev_sort));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[2], sl.ev_sort, 0));
+    ACE_TRY(msm_run<fp2_t>(pl.B, pk->B2.d_pts, true, nullptr, sl.ar[3], res2, nullptr, ss.aux[2], &sortB));
     ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, sl.ar[4], res1 + 3, ss.aux[3]));
     int pf = prof_begin(PROF_ASSEMBLY, ss.aux[4]);
     k_prove_fixed<<<1, 160, 0, ss.aux[4]>>>(tabs, r, s, rs, fx1, fx2); ::ace::note_launch();
@@ -572,7 +576,8 @@ static ManyPlans many_plans(const ace_pk* pk, uint32_t count) {
 
 template <class F>
 static int gathered_msm_many(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z, uint64_t wit, Arena& ar,
-                             Xyzz<F>* res, cudaStream_t s) {
+                             Xyzz<F>* res, cudaStream_t s, MsmSorted* sorted = nullptr,
+                             cudaEvent_t sorted_ev = nullptr) {
     fr_t* zq = (fr_t*)ar.take((size_t)q.count * plan.batch * sizeof(fr_t) + 32);
     if (!zq) {
         set_error("prove_many: arena too small");
@@ -583,7 +588,7 @@ static int gathered_msm_many(const MsmPlan& plan, const Query<F>& q, const fr_t*
         k_gather_many<<<grid, 256, 0, s>>>(d_z, wit, q.d_idx, q.count, zq);
         ::ace::note_launch();
     }
-    return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s);
+    return msm_run<F>(plan, q.d_pts, true, (const uint32_t*)zq, ar, res, nullptr, s, nullptr, sorted, sorted_ev);
 }
 
 // `count` proofs of pk on proving slot 0 (level 0 streams), after the work on
@@ -624,8 +629,11 @@ static int prove_many_run(ace_ctx* ctx, const ace_pk* pk, uint32_t count, const 
     for (int k = 0; k < 5; k++) ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[k], sl.ev_start, 0));
     // MSMs over the witness on the auxiliary streams
     ACE_TRY(gathered_msm_many<fp_t>(pl.A, pk->A, d_z, wit, sl.ar[1], res1 + count, ss.aux[0]));
-    ACE_TRY(gathered_msm_many<fp_t>(pl.B, pk->B1, d_z, wit, sl.ar[2], res1 + 2 * (size_t)count, ss.aux[1]));
-    ACE_TRY(gathered_msm_many<fp2_t>(pl.B, pk->B2, d_z, wit, sl.ar[3], res2, ss.aux[2]));
+    MsmSorted sortB;  // shared by B1 and B2, as in prove_run
+    ACE_TRY(gathered_msm_many<fp_t>(pl.B, pk->B1, d_z, wit, sl.ar[2], res1 + 2 * (size_t)count, ss.aux[1], &sortB,
+                                    sl.ev_sort));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[2], sl.ev_sort, 0));
+    ACE_TRY(msm_run<fp2_t>(pl.B, pk->B2.d_pts, true, nullptr, sl.ar[3], res2, nullptr, ss.aux[2], &sortB));
     ACE_TRY(gathered_msm_many<fp_t>(pl.L, pk->L, d_z, wit, sl.ar[4], res1 + 3 * (size_t)count, ss.aux[3]));
     k_prove_fixed_many<<<(5 * count + 127) / 128, 128, 0, ss.aux[4]>>>(tabs, rsv, count, fx1, fx2); ::ace::note_launch();
     ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[0], ss.aux[0]));

@@ -85,6 +85,7 @@ int slot_ready(ace_ctx* ctx, int s) {
     ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_start, cudaEventDisableTiming));
     ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));
     for (auto& e : sl.ev_aux) ACE_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ACE_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev_sort, cudaEventDisableTiming));
     sl.ready = true;
     return ACE_OK;
 }

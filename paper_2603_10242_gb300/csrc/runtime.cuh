@@ -83,6 +83,7 @@ struct ProveSlot {
     SlotStreams lv[PRIO_LEVELS];
     cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_aux[5] = {};
+    cudaEvent_t ev_sort = nullptr;  // the B query's entries are sorted (B2 reuses B1's)
 };
 
 }  // namespace ace

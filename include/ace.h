@@ -161,7 +161,8 @@ int ace_pk_point(const ace_pk* pk, int query, size_t index, void* out);
  * 3 inverse NTTs, 3 coset NTTs on g H (g = 5), pointwise (a b - c)/(g^N - 1),
  * coset inverse NTT.  d_z: m canonical Fr (device); d_h_out: N canonical Fr
  * (device), natural coefficient order, h_{N-1} = 0.  Asynchronous on stream.
- * Scratch is drawn from the context. */
+ * Scratch is drawn from the context.  (ace_prove stops before the last step:
+ * its H query is in the Lagrange basis of g H and takes the coset values.) */
 int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out, ace_stream stream);
 
 /* Multi-scalar multiplication sum_i k_i P_i over G1 (Pippenger: signed c-bit

@@ -2,21 +2,28 @@
 // Phase 2 (Section 3.1, Algorithm 1 ProveAsync; Section 3.3, Algorithm 3
 // Stage 1), producing the 256-byte proof of Section 3.3 / Appendix B.
 //
-//   1. a, b, c = Az, Bz, Cz (one thread per row, all three matrices), with
-//      the R1CS check a_i b_i = c_i folded in (status word on failure);
+//   1. a, b, c = Az, Bz, Cz (one thread per row, rows by decreasing length,
+//      all three matrices in one loop), with the R1CS check a_i b_i = c_i
+//      folded in (status word on failure);
 //   2. QAP quotient: inverse NTT of a, b, c (decimation in frequency, scaled
 //      by g^e / N on the way out: coset coefficients), forward NTT
-//      (decimation in time: values on g H), q = (a b - c)/(g^N - 1), inverse
-//      NTT scaled by g^-e / N leaving canonical h in bit-reversed order;
-//   3. five MSMs on their own streams: H (h, bit-reversed H query) on the
-//      main stream, A, B1 (G1), B2 (G2) and L on auxiliary streams, with the
-//      witness gathered per compacted query;
+//      (decimation in time: values on g H), q_i = (a b - c)/(g^N - 1) =
+//      h(g omega^i), canonical, natural order;
+//   3. five MSMs on their own streams: H (the q_i against the key's H query in
+//      the Lagrange basis of g H) on the main stream, A, B1 (G1), B2 (G2) and
+//      L on auxiliary streams, with the witness gathered per compacted query
+//      (B2 reuses B1's sorted entries);
 //   4. assembly: A = alpha + S_A + r delta, B = beta + S_B2 + s delta and
 //      C = S_L + S_H + s A + r B1 - r s delta with B1 = beta + S_B1 + s delta,
 //      i.e. C = S_L + S_H + s alpha + r beta + r s delta + s S_A + r S_B1:
 //      the fixed-base terms come from the key's window tables at the start,
-//      s S_A + r S_B1 (one joint double-and-add) as soon as the A and B1
-//      MSMs are done, and the last kernel only adds and converts to affine.
+//      s S_A + r S_B1 (GLV chains) as soon as the A and B1 MSMs are done, and
+//      the last kernel only adds and converts to affine.
+// The field product, square and difference of products are called out of
+// line: the single-thread chains of step 4 (hundreds of dependent curve
+// operations) run about twice as fast from one shared body as from inlined
+// copies that keep missing the instruction cache.
+#define ACE_FIELD_MUL_CALL 1
 #include <stdlib.h>
 #include <string.h>
 
@@ -59,6 +66,18 @@ struct CsrDev {
 // over the row's A, B and C terms in one loop: the lanes of a warp then do
 // equal numbers of products whatever the split of their totals among A, B, C.
 // The R1CS check a b = c is made on the way.
+// inlined Montgomery product for the sparse products (one product per loop
+// iteration: a short loop body that keeps 64 registers)
+__device__ __forceinline__ fr_t mul_inl(const fr_t& x, const fr_t& y) {
+#if defined(__CUDA_ARCH__)
+    fr_t r;
+    d_mul_form<FrCfg>(r.v, x.v, y.v);
+    return r;
+#else
+    return x * y;
+#endif
+}
+
 __device__ __forceinline__ void rows_abc(const CsrDev& m, const fr_t* __restrict__ z, uint32_t i, fr_t& a, fr_t& b,
                                          fr_t& c) {
     fr_t acc = fe_zero<FrCfg>(), sa = acc, sb = acc;
@@ -78,12 +97,12 @@ __device__ __forceinline__ void rows_abc(const CsrDev& m, const fr_t* __restrict
             e = __ldg((k == 1 ? m.rp[1] : m.rp[2]) + i + 1);
         }
         if (k == 3) break;
-        acc = acc + ldg_fr(val + t) * ldg_fr(z + __ldg(col + t));
+        acc = acc + mul_inl(ldg_fr(val + t), ldg_fr(z + __ldg(col + t)));
         t++;
     }
-    a = sa * fe_rr<FrCfg>();
-    b = sb * fe_rr<FrCfg>();
-    c = acc * fe_rr<FrCfg>();
+    a = mul_inl(sa, fe_rr<FrCfg>());
+    b = mul_inl(sb, fe_rr<FrCfg>());
+    c = mul_inl(acc, fe_rr<FrCfg>());
 }
 
 __global__ void __launch_bounds__(256) k_spmv3(CsrDev m, const uint32_t* __restrict__ order,

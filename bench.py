@@ -813,11 +813,117 @@ def run_case(args):
     print(json.dumps({"case": args.case, "steps": args.steps, "launches": ace.launch_count()}))
 
 
+def run_sweep(args):
+    """BASELINE config 3, the kernel sweep: G1 MSM at 2^16..2^24 points (bases
+    k_i G stored affine in Montgomery form, k_i seeded) in the uniform and the
+    70%-{0,1} scalar distributions, and the Fr NTT, inverse NTT and coset NTT
+    at 2^16..2^24 elements (uniform inputs).  Every timed call is bracketed by
+    CUDA events on the launching stream; a 256 MiB buffer (larger than the
+    129 MB L2) is written between timed calls, so no call starts with its
+    inputs in L2.  Sizes are prefixes of one seeded stream per distribution."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10242_gb300 as ace
+    from paper_2603_10242_gb300 import inputs
+
+    ace.build()
+    ctx = ace.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak_imad = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
+    hbm_peak = _measured_hbm_gbs()
+    reps = max(3, args.steps)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1000.0)
+        return statistics.median(ts)
+
+    logs = (16, 18, 20, 22, 24)
+    nmax = 1 << logs[-1]
+    kb = inputs.sample_fr(20, inputs.PURPOSE["bases"], nmax)
+    bases = torch.empty(64 * nmax, dtype=torch.uint8, device=dev)
+    ctx.g1_fixed_base(torch.from_numpy(kb.view(np.uint8).reshape(-1)).to(dev), nmax, bases, ace.FORM_MONT)
+    out = torch.empty(64, dtype=torch.uint8, device=dev)
+    msm_rows = []
+    for dist_name in ("uniform", "sparse"):
+        sc = torch.from_numpy(inputs.sample_scalars(24, nmax, dist_name).view(np.uint8).reshape(-1)).to(dev)
+        for lg in logs:
+            n = 1 << lg
+            t = timed(lambda: ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT))
+            # one more call under the launch profiler for the bucket kernel's work and time
+            ace.profile_enable(True)
+            ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT)
+            torch.cuda.synchronize()
+            ms, nl, adds = ace.profile_read(ace.PROF_G1_BUCKET)
+            sort_ms = ace.profile_read(ace.PROF_SORT)[0]
+            red_ms = ace.profile_read(ace.PROF_REDUCE)[0]
+            ace.profile_enable(False)
+            bucket_rate = adds * IMAD_PER_G1_MADD / (ms / 1000.0) if ms > 0 else None
+            msm_rows.append({
+                "log_n": lg, "scalars": dist_name, "ms": t * 1000.0, "points_per_s": n / t,
+                "bucket_additions": adds,
+                "stage_ms": {"sort": sort_ms, "bucket_acc": ms, "reduce_and_final": red_ms},
+                "bucket_kernel_frac": bucket_rate / peak_imad if bucket_rate else None,
+                "msm_frac": adds * IMAD_PER_G1_MADD / t / peak_imad,
+            })
+        del sc
+    del bases
+    torch.cuda.empty_cache()
+
+    ntt_rows = []
+    kinds = {0: "ntt", 1: "intt", 2: "coset_ntt", 3: "coset_intt"}
+    vals = torch.from_numpy(inputs.sample_fr(24, 7, 1 << 24).view(np.uint8).reshape(-1)).to(dev)
+    for lg in range(16, 25):
+        n = 1 << lg
+        d = vals[:32 * n].clone()
+        for kind, name in kinds.items():
+            t = timed(lambda: ctx.ntt(d, lg, kind))
+            # radix-2 count: (N/2) log2 N butterflies (one product each) plus the
+            # N scalings of the inverse and coset forms
+            muls = (n // 2) * lg + (n if kind else 0)
+            ntt_rows.append({
+                "log_n": lg, "kind": name, "ms": t * 1000.0, "elements_per_s": n / t,
+                "hbm_gbs_algorithmic": 64.0 * n / t / 1e9,
+                "hbm_frac": 64.0 * n / t / 1e9 / hbm_peak,
+                "imad_frac": muls * IMAD_PER_FP_MUL / t / peak_imad,
+            })
+        del d
+    print(json.dumps({
+        "workload": "kernel_sweep_msm_g1_ntt_2p16_2p24", "curve": "BN254", "reps": reps,
+        "timing": "median of reps, CUDA events per call, L2 flushed (256 MiB write) before each call",
+        "msm_g1": msm_rows, "ntt": ntt_rows,
+        "roofline": {"imad_peak_T_per_s": peak_imad / 1e12, "hbm_peak_gbs": hbm_peak,
+                     "msm": f"{IMAD_PER_G1_MADD} IMAD per bucket addition (algorithmic, bucket additions only)",
+                     "ntt": "64 B per element (read + write once) against HBM; "
+                            f"{IMAD_PER_FP_MUL} IMAD per butterfly product against the ALU"},
+    }))
+
+
+def _measured_hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=300, help="served workload: number of jobs")
     ap.add_argument("--serve-slots", type=int, default=3)
-    ap.add_argument("--workload", choices=["block2p20", "batch64", "serve", "pertx"], default="block2p20",
+    ap.add_argument("--workload", choices=["block2p20", "batch64", "serve", "pertx", "sweep"], default="block2p20",
                     help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
     ap.add_argument("--case", choices=["msm_g1", "msm_g2", "ntt", "prove16", "prove20"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
@@ -835,6 +941,8 @@ def main():
         run_serve(args)
     elif args.workload == "pertx":
         run_pertx(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

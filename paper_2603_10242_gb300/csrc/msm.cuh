@@ -56,7 +56,8 @@ struct MsmPlan {
     size_t scalars() const { return (size_t)batch * n; }
 };
 
-// c chosen by the cost model  n K madd + 2 K 2^(c-1) add  (force_c > 0 overrides)
+// c chosen by the cost model  max(n K madd + 2 K 2^(c-1) add, the top window's
+// longest bucket run in sequence)  (force_c > 0 overrides)
 MsmPlan msm_plan(size_t n, int force_c = 0);
 // plan for tabled bases: cost n K madd + 2 2^(c-1) add, c <= 20
 MsmPlan msm_plan_tabled(size_t n, int force_c = 0);

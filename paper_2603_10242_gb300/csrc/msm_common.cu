@@ -44,8 +44,12 @@ __device__ __forceinline__ T ld_plain(const T* p) {
 // 254 - c (K - 1) scalar bits (c = 18: 2, c = 19: 7), so its digits fall into
 // few buckets, and one thread adds each bucket's entries in sequence; one
 // sequential addition costs about MSM_SEQ_MADD additions of the whole GPU.
-// c is skipped when a top-window bucket gets more than MSM_TOP_LOAD entries
-// and that sequence would take more than half the throughput time.
+// Without window tables the top window has buckets of its own, and the time
+// is the longer of the throughput work and that sequence.  With window tables
+// the top window's digits share the low buckets with every other window,
+// whose long buckets are split among threads; there c is skipped when a
+// top-window bucket gets more than MSM_TOP_LOAD entries and that sequence
+// would take more than half the throughput time.
 static const double MSM_TOP_LOAD = 512.0;
 static const double MSM_SEQ_MADD = 2.0e4;
 static double msm_cost(size_t n, int c, bool tabled) {
@@ -56,6 +60,7 @@ static double msm_cost(size_t n, int c, bool tabled) {
     if (top_bits < 1) top_bits = 1;
     if (top_bits > c - 1) top_bits = c - 1;
     const double top_load = (double)n / (double)(1u << top_bits);
+    if (!tabled) return work > top_load * MSM_SEQ_MADD ? work : top_load * MSM_SEQ_MADD;
     if (top_load > MSM_TOP_LOAD && top_load * MSM_SEQ_MADD > 0.5 * work) return 1e300;
     return work;
 }

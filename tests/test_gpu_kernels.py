@@ -197,9 +197,12 @@ def test_msm_g1_every_window(c_bits):
     assert gu.host(out) == _msm_expected_dlog(ks, ss)
 
 
-@pytest.mark.parametrize("log_n,dist", [(16, "uniform"), (18, "sparse"), (20, "uniform"), (20, "sparse")])
+@pytest.mark.parametrize("log_n,dist", [(16, "uniform"), (18, "sparse"), (20, "uniform"), (20, "sparse"),
+                                        (22, "sparse"), (24, "uniform")])
 def test_msm_g1_large_dlog(log_n, dist):
-    """Bases from the fixed-base kernel; expected value from the seeds alone."""
+    """Bases from the fixed-base kernel; expected value from the seeds alone.
+    The sizes span the G1 MSM sweep (2^16 to 2^24 points) in both scalar
+    distributions, three points short of each power of two (a ragged tail)."""
     c = gu.ctx()
     n = (1 << log_n) - 3
     kb = inputs.sample_fr(log_n, inputs.PURPOSE["bases"], n)
@@ -246,13 +249,15 @@ def test_msm_g2_large_dlog():
     assert gu.host(out) == O.g2_mul(O.g2_generator(), s)
 
 
-@pytest.mark.parametrize("log_n", [1, 2, 5, 10, 11, 12, 16, 20, 23])
+@pytest.mark.parametrize("log_n", [1, 2, 5, 10, 11, 12, 16, 20, 23, 24])
 def test_ntt_kinds_vs_oracle(log_n):
+    """Every transform kind against the oracle's NTT, element by element; at
+    2^24 (the top of the NTT sweep) the forward transform only, whole."""
     c = gu.ctx()
     n = 1 << log_n
     vals = inputs.sample_fr(log_n, 7, n)
     raw = vals.tobytes()
-    kinds = (0, 1, 2, 3) if log_n <= 20 else (0, 3)
+    kinds = (0, 1, 2, 3) if log_n <= 20 else (0, 3) if log_n <= 23 else (0,)
     g = 5
     for kind in kinds:
         d = gu.dev(raw)

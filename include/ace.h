@@ -169,7 +169,12 @@ int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out
  * digits, bucket sort, bucket accumulation, bucket and window reduction).
  * d_bases: n affine points in base_form (ACE_FORM_CANONICAL or _MONT);
  * d_scalars: n canonical Fr; d_out: one affine canonical point (device).
- * n may be 0 (result is infinity).  Asynchronous on stream. */
+ * n may be 0 (result is infinity).  Asynchronous on stream.  For n < 2^30
+ * the G1 scalars are split by the GLV endomorphism, k = k1 + k2 lambda with
+ * 128-bit halves over P_i and (beta x_i, y_i), which halves the digit
+ * windows; any 256-bit scalar is then taken modulo r.  Scratch (buckets,
+ * sorted digits, 2n prepared points and scalar halves) is drawn from the
+ * context. */
 int ace_msm_g1(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
                size_t n, ace_g1_affine* d_out, ace_stream stream);
 /* Same over G2 (coordinates in Fp2): the B query of the proof. */
@@ -251,9 +256,14 @@ int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream s
 int ace_ntt_mont(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int count, int dif, int inverse,
                  ace_stream stream);
 
-/* ace_msm_g1 with the window size forced to c (6 <= c <= 20). */
+/* ace_msm_g1 with the window size forced to c (6 <= c <= 20), without the
+ * GLV split (full-width scalars, K = ceil(255 / c) windows). */
 int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
                       size_t n, int c, ace_g1_affine* d_out, ace_stream stream);
+/* ace_msm_g1 (GLV split, K = ceil(128 / c) windows over 2n points) with the
+ * window size forced to c (6 <= c <= 20); n < 2^30. */
+int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
+                          size_t n, int c, ace_g1_affine* d_out, ace_stream stream);
 
 /* ---- diagnostics and measurement ------------------------------------------- */
 

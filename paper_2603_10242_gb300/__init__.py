@@ -53,6 +53,7 @@ def lib():
             "ace_msm_g1": (i32, [vp, vp, i32, vp, sz, vp, vp]),
             "ace_msm_g2": (i32, [vp, vp, i32, vp, sz, vp, vp]),
             "ace_msm_g1_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
+            "ace_msm_g1_glv_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
             "ace_msm_g1_noalloc": (i32, [vp, i32, vp, sz, vp, vp]),
             "ace_g1_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
             "ace_g2_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
@@ -183,6 +184,10 @@ class Context:
     def msm_g1_window(self, bases, scalars, n: int, c: int, out, base_form: int = FORM_CANONICAL, stream=None):
         check(lib().ace_msm_g1_window(self.h, _ptr(bases), base_form, _ptr(scalars), n, c, _ptr(out),
                                       _stream(stream)))
+
+    def msm_g1_glv_window(self, bases, scalars, n: int, c: int, out, base_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_msm_g1_glv_window(self.h, _ptr(bases), base_form, _ptr(scalars), n, c, _ptr(out),
+                                          _stream(stream)))
 
     def g1_fixed_base(self, scalars, n: int, out, out_form: int = FORM_CANONICAL, stream=None):
         check(lib().ace_g1_fixed_base(self.h, _ptr(scalars), n, _ptr(out), out_form, _stream(stream)))

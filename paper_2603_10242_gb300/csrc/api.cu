@@ -35,7 +35,14 @@ static int msm_entry(ace_ctx* ctx, const void* d_bases, int base_form, const ace
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     int lg = 0;
     while (lg < 31 && ((size_t)1 << (lg + 1)) <= n) lg++;
-    MsmPlan plan = msm_plan(n, ctx->tuned_msm_c[lg]);
+    // G1: scalars split by the GLV endomorphism (half the windows; the 2 n
+    // virtual points need n < 2^30), with the autotuned window if any; G2:
+    // full-width scalars, window from the cost model
+    MsmPlan plan;
+    if (sizeof(F) == sizeof(fp_t) && n < (1ull << 30))
+        plan = msm_plan_glv(n, ctx->tuned_msm_c[lg]);
+    else
+        plan = msm_plan(n);
     bool mont = base_form == ACE_FORM_MONT;
     ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<F>(plan, mont)));
     return msm_run<F>(plan, (const Affine<F>*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
@@ -181,6 +188,24 @@ int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form,
     }
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     MsmPlan plan = msm_plan(n, c);
+    bool mont = base_form == ACE_FORM_MONT;
+    ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(plan, mont)));
+    return msm_run<fp_t>(plan, (const g1_aff*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
+                         (g1_aff*)d_out, pick_stream(ctx, stream));
+}
+
+// Diagnostic: the G1 MSM of ace_msm_g1 (GLV split) with an explicit window
+// size c (6..20).
+int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
+                          size_t n, int c, ace_g1_affine* d_out, ace_stream stream) {
+    clear_error();
+    if (!ctx || !d_out || (n && (!d_bases || !d_scalars)) || c < 6 || c > 20 || n >= (1ull << 30) ||
+        (base_form != ACE_FORM_CANONICAL && base_form != ACE_FORM_MONT)) {
+        set_error("ace_msm_g1_glv_window: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    MsmPlan plan = msm_plan_glv(n, c);
     bool mont = base_form == ACE_FORM_MONT;
     ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(plan, mont)));
     return msm_run<fp_t>(plan, (const g1_aff*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,

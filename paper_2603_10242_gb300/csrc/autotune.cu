@@ -89,12 +89,12 @@ int ace_autotune_msm(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* r
     int row = 0;
     for (uint32_t lg = log_min; lg <= log_max && rc == ACE_OK; lg++, row++) {
         size_t n = (size_t)1 << lg;
-        MsmPlan model = msm_plan(n);
+        MsmPlan model = msm_plan_glv(n);
         int best_c = model.c;
         float best = 1e30f, model_ms = 0;
         for (int c = model.c - 3; c <= model.c + 2 && rc == ACE_OK; c++) {
             if (c < 6 || c > 20) continue;
-            MsmPlan p = msm_plan(n, c);
+            MsmPlan p = msm_plan_glv(n, c);
             rc = arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(p, true));
             if (rc != ACE_OK) break;
             float t = 1e30f;

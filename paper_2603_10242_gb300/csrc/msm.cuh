@@ -42,6 +42,10 @@ struct MsmPlan {
     uint32_t batch = 1;
     // most threads one bucket's entries may be split among (1: no split)
     uint32_t max_split = 16;
+    // glv (G1 without window tables): n counts the points P_i and phi(P_i)
+    // of n / 2 input points, whose scalars are the 128-bit halves of the GLV
+    // split (glv.cuh); K = ceil(128 / c) windows
+    bool glv = false;
     // virtual buckets the ones window uses (a power of two <= B, about n / 64):
     // scalar 1 of point i goes to bucket i mod B1.  Enough buckets to spread
     // the additions over many threads, few enough that the window's plain sum
@@ -61,6 +65,14 @@ struct MsmPlan {
 MsmPlan msm_plan(size_t n, int force_c = 0);
 // plan for tabled bases: cost n K madd + 2 2^(c-1) add, c <= 20
 MsmPlan msm_plan_tabled(size_t n, int force_c = 0);
+// G1 plan over the GLV split of n points (2 n virtual points, 128-bit scalars)
+MsmPlan msm_plan_glv(size_t n, int force_c = 0);
+// GLV inputs of a G1 MSM: for i < n, out[i] = +-P_i and out[n + i] =
+// +-phi(P_i) (Montgomery affine), osc[i] = |k1|, osc[n + i] = |k2| (8 limbs,
+// canonical) with k_i mod r = k1 + k2 lambda and the signs moved onto the
+// points.  in: n affine points (Montgomery if in_mont); sc: n scalars < 2^256.
+int glv_prepare(const Affine<fp_t>* in, bool in_mont, const uint32_t* sc, size_t n, Affine<fp_t>* out,
+                uint32_t* osc, cudaStream_t st);
 // window table of n Montgomery affine points: tab[w n + i] = 2^(c w) pts[i]
 // for w < K (pts may be tab itself, i.e. window 0 already in place)
 template <class F>
@@ -78,7 +90,8 @@ struct MsmBufs {
     Xyzz<F>* partial;    // keys x split (split parts per bucket), or buckets itself
     Xyzz<F>* segW;       // windows M
     Xyzz<F>* segS;       // windows M
-    Affine<F>* conv;     // n (only when bases arrive canonical)
+    Affine<F>* conv;     // n (when bases arrive canonical, or the GLV points)
+    uint32_t* gsc;       // n x 8 (GLV scalar halves only)
     template <class Alloc>
     bool carve(Alloc& a, const MsmPlan& p, bool need_conv);
 };

@@ -52,11 +52,13 @@ __device__ __forceinline__ T ld_plain(const T* p) {
 // would take more than half the throughput time.
 static const double MSM_TOP_LOAD = 512.0;
 static const double MSM_SEQ_MADD = 2.0e4;
-static double msm_cost(size_t n, int c, bool tabled) {
-    const int K = (255 + c - 1) / c;
+// bits: 255 for full Fr scalars (254 bits and the top digit's carry), 128
+// for GLV halves (below 2^127).
+static double msm_cost(size_t n, int c, bool tabled, int bits = 255) {
+    const int K = (bits + c - 1) / c;
     const double B = (double)(1u << (c - 1));
     const double work = (double)n * K + (tabled ? 5.6 * B : 2.8 * K * B);
-    int top_bits = 254 - c * (K - 1);
+    int top_bits = (bits - 1) - c * (K - 1);
     if (top_bits < 1) top_bits = 1;
     if (top_bits > c - 1) top_bits = c - 1;
     const double top_load = (double)n / (double)(1u << top_bits);
@@ -65,13 +67,14 @@ static double msm_cost(size_t n, int c, bool tabled) {
     return work;
 }
 
-static MsmPlan plan_for(size_t n, int c, bool tabled) {
+static MsmPlan plan_for(size_t n, int c, bool tabled, bool glv = false) {
     MsmPlan p;
     p.n = n;
     if (c < 6) c = 6;
     if (c > 20) c = 20;
     p.c = c;
-    p.K = (255 + p.c - 1) / p.c;
+    p.glv = glv;
+    p.K = ((glv ? 128 : 255) + p.c - 1) / p.c;
     p.B = 1u << (p.c - 1);
     p.lambda = p.c - 1 < 4 ? p.c - 1 : 4;  // segments of 16 buckets
     p.L = 1u << p.lambda;
@@ -82,11 +85,11 @@ static MsmPlan plan_for(size_t n, int c, bool tabled) {
     return p;
 }
 
-static int best_window(size_t n, bool tabled) {
+static int best_window(size_t n, bool tabled, int bits = 255) {
     int best_c = 20;  // top window of 14 bits: the fallback for any n
     double best = 1e300;
     for (int c = tabled ? 8 : 6; c <= 20; c++) {
-        double cost = msm_cost(n, c, tabled);
+        double cost = msm_cost(n, c, tabled, bits);
         if (cost < best) {
             best = cost;
             best_c = c;
@@ -98,6 +101,10 @@ static int best_window(size_t n, bool tabled) {
 MsmPlan msm_plan_tabled(size_t n, int force_c) { return plan_for(n, force_c > 0 ? force_c : best_window(n, true), true); }
 
 MsmPlan msm_plan(size_t n, int force_c) { return plan_for(n, force_c > 0 ? force_c : best_window(n, false), false); }
+
+MsmPlan msm_plan_glv(size_t n, int force_c) {
+    return plan_for(2 * n, force_c > 0 ? force_c : best_window(2 * n, false, 128), false, true);
+}
 
 // ---------------------------------------------------------------------------
 // scan
@@ -217,10 +224,11 @@ __device__ __forceinline__ int scalar_kind(const uint32_t s[8]) {
 // (precomputed window tables); otherwise window w's buckets hold entry i.
 // A batch of MSMs over the same n points: scalar t belongs to MSM t / n and
 // multiplies point t mod n; each MSM has its own keys_per keys.
-template <int C, bool SCATTER, bool TAB>
+// BITS: 255 for Fr scalars, 128 for GLV halves (magnitudes below 2^127).
+template <int C, bool SCATTER, bool TAB, int BITS = 255>
 __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t total, size_t n, uint32_t keys_per,
                              uint32_t ones_mask, uint32_t* cnt, uint32_t* entries) {
-    constexpr int K = (255 + C - 1) / C;
+    constexpr int K = (BITS + C - 1) / C;
     constexpr uint32_t B = 1u << (C - 1);
     constexpr uint32_t BW = TAB ? 1u : (uint32_t)K;
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,6 +282,19 @@ void launch_digits(const MsmPlan& plan, const uint32_t* sc, uint32_t* cnt, uint3
     const size_t total = plan.scalars(), n = plan.n;
     const uint32_t kp = plan.keys_per(), om = plan.ones_mask();
     unsigned grid = (unsigned)((total + 255) / 256);
+    if (plan.glv) {
+        switch (plan.c) {
+#define ACE_DIGITS_GLV(CC) \
+    case CC: k_msm_digits<CC, SCATTER, false, 128><<<grid, 256, 0, st>>>(sc, total, n, kp, om, cnt, entries); break;
+            ACE_DIGITS_GLV(6) ACE_DIGITS_GLV(7) ACE_DIGITS_GLV(8) ACE_DIGITS_GLV(9) ACE_DIGITS_GLV(10)
+            ACE_DIGITS_GLV(11) ACE_DIGITS_GLV(12) ACE_DIGITS_GLV(13) ACE_DIGITS_GLV(14) ACE_DIGITS_GLV(15)
+            ACE_DIGITS_GLV(16) ACE_DIGITS_GLV(17) ACE_DIGITS_GLV(18) ACE_DIGITS_GLV(19) ACE_DIGITS_GLV(20)
+#undef ACE_DIGITS_GLV
+            default: break;
+        }
+        ::ace::note_launch();
+        return;
+    }
     switch (plan.c * 2 + (plan.tabled ? 1 : 0)) {
 #define ACE_DIGITS_CASE(CC)                                                                                        \
     case 2 * CC: k_msm_digits<CC, SCATTER, false><<<grid, 256, 0, st>>>(sc, total, n, kp, om, cnt, entries); break; \

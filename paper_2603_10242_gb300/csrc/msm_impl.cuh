@@ -53,9 +53,11 @@ bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
     partial = split > 1 ? (Xyzz<F>*)a.take(keys * split * sizeof(Xyzz<F>)) : buckets;
     segW = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
     segS = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
+    need_conv = need_conv || p.glv;
     conv = need_conv ? (Affine<F>*)a.take(p.n * sizeof(Affine<F>)) : nullptr;
+    gsc = p.glv ? (uint32_t*)a.take(p.n * 32) : nullptr;
     return offsets && cursor && scan_tmp && entries && order && size_bins && buckets && partial && segW && segS &&
-           (!need_conv || conv);
+           (!need_conv || conv) && (!p.glv || gsc);
 }
 
 template <class F>
@@ -370,7 +372,17 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     const size_t n = plan.scalars();
     const uint32_t keys = plan.keys();
     const Affine<F>* bases = d_bases;
-    if (!base_mont) {
+    if (plan.glv) {
+        if constexpr (sizeof(F) == sizeof(fp_t)) {
+            ACE_TRY(glv_prepare((const Affine<fp_t>*)d_bases, base_mont, d_scalars, plan.n / 2,
+                                (Affine<fp_t>*)b.conv, b.gsc, st));
+            bases = b.conv;
+            d_scalars = b.gsc;
+        } else {
+            set_error("msm: the GLV plan is for G1 only");
+            return ACE_E_ARG;
+        }
+    } else if (!base_mont) {
         k_bases_to_mont<F><<<(unsigned)((plan.n + 127) / 128), 128, 0, st>>>(d_bases, plan.n, b.conv); ::ace::note_launch();
         bases = b.conv;
     }

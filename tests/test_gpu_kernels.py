@@ -197,6 +197,48 @@ def test_msm_g1_every_window(c_bits):
     assert gu.host(out) == _msm_expected_dlog(ks, ss)
 
 
+LAMBDA = 0xb3c4d79d41a917585bfc41088d8daaa78b17ea66b99c90dd  # cube root of unity mod r
+
+
+@pytest.mark.parametrize("c_bits", [6, 7, 9, 11, 13, 16, 17, 20])
+def test_msm_g1_glv_every_window(c_bits):
+    """The GLV form of the G1 MSM (k = k1 + k2 lambda, 128-bit halves over P
+    and phi(P)) at every window size: ceil(128 / c) windows, the top one
+    short."""
+    c = gu.ctx()
+    n = 3001
+    ks = [rng.randrange(1, R) for _ in range(n)]
+    pts = _rand_g1(ks)
+    ss = inputs.limbs_to_int(inputs.sample_scalars(90 + c_bits, n, "sparse" if c_bits % 2 else "uniform"))
+    out = gu.empty(64)
+    c.msm_g1_glv_window(gu.dev(pts), gu.dev(gu.ints_bytes(ss)), n, c_bits, out, ace.FORM_CANONICAL)
+    assert gu.host(out) == _msm_expected_dlog(ks, ss)
+
+
+def test_msm_g1_glv_edge_scalars_and_points():
+    """Scalars whose halves are negative or extreme (r - 1, lambda, lambda^2,
+    (r - 1) / 2), scalars at or above r (taken modulo r, up to 2^256 - 1),
+    zeros and ones, and points at infinity."""
+    c = gu.ctx()
+    edge = [0, 1, 2, R - 1, R - 2, LAMBDA, LAMBDA * LAMBDA % R, (R - 1) // 2, (R + 1) // 2, 1 << 127,
+            (1 << 128) - 1, 1 << 253, R, R + 1, 2 * R + 5, (1 << 255) + 3, (1 << 256) - 1]
+    n = 600
+    ss = (edge * (n // len(edge) + 1))[:n]
+    for i in range(len(edge), n, 3):
+        ss[i] = rng.randrange(R)
+    ks = [rng.randrange(1, R) for _ in range(n)]
+    pts = bytearray(_rand_g1(ks))
+    for i in range(0, n, 37):  # points at infinity
+        pts[64 * i:64 * i + 64] = bytes(64)
+        ks[i] = 0
+    out = gu.empty(64)
+    c.msm_g1(gu.dev(bytes(pts)), gu.dev(gu.ints_bytes(ss)), n, out, ace.FORM_CANONICAL)
+    assert gu.host(out) == _msm_expected_dlog(ks, ss)
+    for cb in (8, 16):
+        c.msm_g1_glv_window(gu.dev(bytes(pts)), gu.dev(gu.ints_bytes(ss)), n, cb, out, ace.FORM_CANONICAL)
+        assert gu.host(out) == _msm_expected_dlog(ks, ss)
+
+
 @pytest.mark.parametrize("log_n,dist", [(16, "uniform"), (18, "sparse"), (20, "uniform"), (20, "sparse"),
                                         (22, "sparse"), (24, "uniform")])
 def test_msm_g1_large_dlog(log_n, dist):

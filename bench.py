@@ -750,7 +750,7 @@ def run_serve(args):
 
 def run_case(args):
     """Small fixed launches for profiler captures (not a bench line):
-    msm_g1 -- one G1 MSM of 2^20 points (uniform scalars);
+    msm_g1 -- one G1 MSM of 2^log_n points (uniform scalars; --log-n, default 20);
     msm_g2 -- one G2 MSM of 2^18 points (uniform scalars);
     ntt -- one 2^20 forward transform of three arrays (QAP batch shape);
     prove16 -- one proof of the 2^16 instance of the block circuit family;
@@ -774,11 +774,11 @@ def run_case(args):
         for _ in range(args.steps):
             ctx.msm_g2(bases, sc, n, out, ace.FORM_MONT)
     elif args.case == "msm_g1":
-        n = 1 << 20
+        n = 1 << args.log_n
         kb = inputs.sample_fr(20, inputs.PURPOSE["bases"], n)
         bases = torch.empty(64 * n, dtype=torch.uint8, device="cuda")
         ctx.g1_fixed_base(torch.from_numpy(kb.view(np.uint8).reshape(-1)).cuda(), n, bases, ace.FORM_MONT)
-        sc = torch.from_numpy(inputs.sample_scalars(20, n, "uniform").view(np.uint8).reshape(-1)).cuda()
+        sc = torch.from_numpy(inputs.sample_scalars(args.log_n, n, "uniform").view(np.uint8).reshape(-1)).cuda()
         out = torch.empty(64, dtype=torch.uint8, device="cuda")
         for _ in range(args.steps):
             ctx.msm_g1(bases, sc, n, out, ace.FORM_MONT)
@@ -927,6 +927,7 @@ def main():
                     help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
     ap.add_argument("--case", choices=["msm_g1", "msm_g2", "ntt", "prove16", "prove20"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
+    ap.add_argument("--log-n", type=int, default=20, help="--case msm_g1: log2 of the number of points")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)

@@ -900,8 +900,10 @@ def run_sweep(args):
                 "imad_frac": muls * IMAD_PER_FP_MUL / t / peak_imad,
             })
         del d
+    cpu = None if args.no_cpu_baseline else sweep_cpu_sample()
     print(json.dumps({
         "workload": "kernel_sweep_msm_g1_ntt_2p16_2p24", "curve": "BN254", "reps": reps,
+        "cpu_baseline": cpu,
         "timing": "median of reps, CUDA events per call, L2 flushed (256 MiB write) before each call",
         "msm_g1": msm_rows, "ntt": ntt_rows,
         "roofline": {"imad_peak_T_per_s": peak_imad / 1e12, "hbm_peak_gbs": hbm_peak,
@@ -909,6 +911,35 @@ def run_sweep(args):
                      "ntt": "64 B per element (read + write once) against HBM; "
                             f"{IMAD_PER_FP_MUL} IMAD per butterfly product against the ALU"},
     }))
+
+
+def sweep_cpu_sample():
+    """The oracle on a bounded sample of the sweep: its plain Pippenger G1 MSM
+    over 2^16 points (uniform and 70%-{0,1} scalars) and its radix-2 NTT at
+    2^16, 2^18 and 2^20 elements, on the host's cores (a few seconds)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2603_10242_gb300 import inputs
+
+    n = 1 << 16
+    pts = O.g1_mul_gen_batch(inputs.sample_fr(20, inputs.PURPOSE["bases"], n).tobytes())
+    msm = {}
+    for dist_name in ("uniform", "sparse"):
+        sc = inputs.sample_scalars(24, n, dist_name).tobytes()
+        t0 = time.perf_counter()
+        O.msm_g1(pts, sc, 1)
+        msm[dist_name] = n / (time.perf_counter() - t0)
+    ntt = {}
+    vals = inputs.sample_fr(24, 7, 1 << 20)
+    for lg in (16, 18, 20):
+        raw = np.ascontiguousarray(vals[:1 << lg]).tobytes()
+        t0 = time.perf_counter()
+        O.ntt(raw, lg)
+        ntt[str(lg)] = (1 << lg) / (time.perf_counter() - t0)
+    return {"kind": "oracle", "cores": O.lib().orc_num_threads(),
+            "msm_g1_2p16_points_per_s": msm, "ntt_elements_per_s": ntt,
+            "sample": "plain Pippenger over 2^16 G1 points per scalar distribution; forward NTT at 2^16, 2^18, 2^20"}
 
 
 def _measured_hbm_gbs() -> float:

@@ -255,7 +255,7 @@ int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream s
         post.h = plan->h;
         post.brev = 1;
     }
-    ACE_TRY(ntt_run(*plan, d, 1, true, inverse, pre, post, st));
+    ACE_TRY(ntt_run(*plan, d, 1, true, inverse, pre, post, st, true));
     ACE_TRY(fr_bitrev_copy(d, tmp, (int)log_n, 1, st));
     if (kind == 3) {
         ACE_TRY_CUDA(cudaMemcpyAsync(d, tmp, n * sizeof(fr_t), cudaMemcpyDeviceToDevice, st));
@@ -279,7 +279,8 @@ int ace_ntt_mont(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int count, int di
     NttPlan* plan = nullptr;
     ACE_TRY(ntt_get_plan(ctx, (int)log_n, &plan));
     NttScale none;
-    return ntt_run(*plan, (fr_t*)d_data, count, dif != 0, inverse != 0, none, none, pick_stream(ctx, stream));
+    return ntt_run(*plan, (fr_t*)d_data, count, dif != 0, inverse != 0, none, none, pick_stream(ctx, stream),
+                   true);
 }
 
 int ace_g1_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g1_affine* d_out, int out_form,

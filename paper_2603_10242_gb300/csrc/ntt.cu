@@ -1,4 +1,5 @@
 // ntt.cu -- radix-2 NTT passes over Fr staged in shared memory (see ntt.cuh).
+#include <cmath>
 #include <vector>
 
 #include "ntt.cuh"
@@ -254,8 +255,44 @@ __global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int l
 // a pass handles up to 2^smem_log elements per block (2^11 x 32 B = 64 KB of
 // shared memory); the plan's smem_log is chosen by the autotuner (10..12)
 
+// Columns per block (2^logG, at most the plan's width): the grid runs in
+// waves of (resident blocks per SM x SMs), so a pass takes about
+// ceil(blocks / slots) x (work of one block).  Narrower blocks can fill the
+// last wave better (one 2^20 array: 512 blocks of 2^11 elements against 456
+// slots take two waves, 1,024 of 2^10 take three half-size waves).
+static int ntt_pick_columns(bool dif, int k, int t, int logG_max, int count) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int best = logG_max;
+    double best_cost = 1e300;
+    for (int lg = logG_max; lg >= 0 && lg >= logG_max - 2; lg--) {
+        const uint32_t S = (1u << lg) << t;
+        int threads = S / 2 < 256 ? (int)(S / 2) : 256;
+        if (threads < 32) threads = 32;
+        int nb = 0;
+        if (dif)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ntt_pass<false>, threads, (size_t)S * 32);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ntt_pass<true>, threads, (size_t)S * 32);
+        if (nb <= 0) continue;
+        const double blocks = (double)count * (double)(1u << (k - t - lg));
+        const double slots = (double)nb * sms;
+        const double cost = std::ceil(blocks / slots) * (double)S;
+        if (cost < best_cost) {  // ties keep the wider block
+            best_cost = cost;
+            best = lg;
+        }
+    }
+    return best;
+}
+
 int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, const NttScale& pre,
-            const NttScale& post, cudaStream_t st) {
+            const NttScale& post, cudaStream_t st, bool fill_waves) {
     const int k = plan.log_n;
     const int NTT_MAX_T = plan.smem_log, NTT_SMEM_LOG = plan.smem_log;
     int passes[4], np = 0;
@@ -292,6 +329,7 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
         int logG = NTT_SMEM_LOG - t;
         if (logG < 0) logG = 0;
         if (logG > k - t) logG = k - t;
+        if (fill_waves) logG = ntt_pick_columns(dif, k, t, logG, count);
         uint32_t groups = 1u << (k - t);
         uint32_t blocks = groups >> logG;
         uint32_t S = (1u << logG) << t;

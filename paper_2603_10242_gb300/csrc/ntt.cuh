@@ -55,8 +55,12 @@ struct NttScale {
 // In-place transform of `count` consecutive arrays of N = 2^log_n elements.
 // dif: natural -> bit-reversed (else bit-reversed -> natural); inverse
 // selects omega^-1.  pre applies at the first load, post at the last store.
+// fill_waves: narrow the blocks of a pass when that fills the GPU's last wave
+// of blocks better (a transform with the GPU to itself); the prover's
+// transforms share the GPU with its MSMs and keep the plan's width.
 int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, const NttScale& pre,
-            const NttScale& post, cudaStream_t st);
+            const NttScale& post, cudaStream_t st,
+            bool fill_waves = false);
 
 int fr_scale_copy(const fr_t* in, fr_t* out, size_t n, const NttScale& s, int log_n, cudaStream_t st);
 int fr_bitrev_copy(const fr_t* in, fr_t* out, int log_n, int count, cudaStream_t st);

@@ -290,6 +290,15 @@ int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128]
  * cube root of unity with (beta x, y) = lambda (x, y) on G1.  out[0..3] = |k1|,
  * out[4] = 1 if k1 < 0, out[5..8] = |k2|, out[9] = 1 if k2 < 0 (|k_i| < 2^128). */
 int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]);
+/* Host: the MSM plan the library picks for n points (no device call).
+ * kind: 0 full-width scalars without window tables (ace_msm_g2, and
+ * ace_msm_g1 for n >= 2^30), 1 window tables (proving-key queries), 2 the
+ * GLV split of ace_msm_g1.  force_c: 0 for the cost model's window, else
+ * 6..20.  out: [c, K digit windows, buckets per window 2^(c-1), bucket
+ * windows + 1 (the {0,1} window), segment length L, segments per window M,
+ * virtual buckets of the {0,1} window, points (2n for the GLV split, low 32
+ * bits)].  ACE_E_ARG for a bad kind or force_c. */
+int ace_debug_msm_plan(size_t n, int kind, int force_c, uint32_t out[8]);
 /* Measured 32-bit multiply-add throughput of the device (operations/s):
  * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs, 3 mad.wide.u32
  * (one 32 x 32 -> 64-bit limb product with 64-bit accumulate per operation). */

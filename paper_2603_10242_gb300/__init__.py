@@ -83,6 +83,7 @@ def lib():
             "ace_verify_batch": (i32, [vp, vp, sz, cp, cp, u64]),
             "ace_debug_pairing_form": (i32, [i32, cp, cp, cp]),
             "ace_debug_glv_split": (i32, [cp, vp]),
+            "ace_debug_msm_plan": (i32, [sz, i32, i32, vp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
             "ace_autotune_batch_slots": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -279,6 +280,17 @@ def debug_field_op(field: int, op: int, d_a, d_b, d_out, n: int, stream=None):
 
 def debug_curve_op(group: int, op: int, d_a, d_b, d_k, d_out, n: int, stream=None):
     check(lib().ace_debug_curve_op(group, op, _ptr(d_a), _ptr(d_b), _ptr(d_k), _ptr(d_out), n, _stream(stream)))
+
+
+MSM_FULL, MSM_TABLED, MSM_GLV = 0, 1, 2
+
+
+def msm_plan(n: int, kind: int, force_c: int = 0) -> dict:
+    """The MSM plan the library picks for n points (host only)."""
+    out = (ctypes.c_uint32 * 8)()
+    check(lib().ace_debug_msm_plan(n, kind, force_c, out))
+    keys = ("c", "K", "B", "windows", "L", "M", "ones_buckets", "points")
+    return dict(zip(keys, list(out)))
 
 
 class CircuitParams(ctypes.Structure):

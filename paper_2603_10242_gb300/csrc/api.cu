@@ -212,6 +212,25 @@ int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_f
                          (g1_aff*)d_out, pick_stream(ctx, stream));
 }
 
+int ace_debug_msm_plan(size_t n, int kind, int force_c, uint32_t out[8]) {
+    clear_error();
+    if (!out || kind < 0 || kind > 2 || force_c < 0 || (force_c != 0 && (force_c < 6 || force_c > 20))) {
+        set_error("ace_debug_msm_plan: bad argument");
+        return ACE_E_ARG;
+    }
+    const MsmPlan p = kind == 0 ? msm_plan(n, force_c) : kind == 1 ? msm_plan_tabled(n, force_c)
+                                                                   : msm_plan_glv(n, force_c);
+    out[0] = (uint32_t)p.c;
+    out[1] = (uint32_t)p.K;
+    out[2] = p.B;
+    out[3] = p.windows();
+    out[4] = p.L;
+    out[5] = p.M;
+    out[6] = p.ones_mask() + 1u;
+    out[7] = (uint32_t)p.n;
+    return ACE_OK;
+}
+
 // NTT of N = 2^log_n canonical Fr values in natural order, in place.
 // kind: 0 forward (coefficients -> values on H), 1 inverse, 2 coset forward
 // (coefficients -> values on g H), 3 coset inverse.

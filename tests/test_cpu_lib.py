@@ -174,3 +174,46 @@ def test_glv_split(lib):
         k2 = sum(out[5 + i] << (32 * i) for i in range(4)) * (-1 if out[9] else 1)
         assert abs(k1) < 1 << 128 and abs(k2) < 1 << 128
         assert (k1 + k2 * lam - k) % Y.R == 0
+
+
+# window choices measured on the GB300 (G1 MSM sweep, block-proof keys)
+MEASURED_PLANS = [
+    (1 << 16, ace.MSM_GLV, 16), (1 << 20, ace.MSM_GLV, 16), (1 << 24, ace.MSM_GLV, 19),
+    (1 << 16, ace.MSM_FULL, 15), (1 << 20, ace.MSM_FULL, 16),
+    ((1 << 20) - 1, ace.MSM_TABLED, 17), (712705, ace.MSM_TABLED, 17), (1748994, ace.MSM_TABLED, 20),
+]
+
+
+@pytest.mark.parametrize("n,kind,c", MEASURED_PLANS)
+def test_msm_plan_pinned_choices(lib, n, kind, c):
+    assert ace.msm_plan(n, kind)["c"] == c
+
+
+@pytest.mark.parametrize("kind", [ace.MSM_FULL, ace.MSM_TABLED, ace.MSM_GLV])
+def test_msm_plan_invariants(lib, kind):
+    """Digit windows cover the scalar bits with no carry out of the top
+    window (254-bit scalars: c K >= 255; GLV halves below 2^127: c K >= 128),
+    the GLV plan runs 2n points with about half the windows, segments tile
+    the buckets, and the {0,1} window's virtual buckets stay within B."""
+    bits = 128 if kind == ace.MSM_GLV else 255
+    for lg in range(4, 26):
+        for n in (1 << lg, (1 << lg) - 3, 3 * (1 << lg) // 2):
+            for force in (0, 6, 11, 20):
+                p = ace.msm_plan(n, kind, force)
+                c, K = p["c"], p["K"]
+                if force:
+                    assert c == force
+                else:
+                    assert (8 if kind == ace.MSM_TABLED else 6) <= c <= 20
+                assert K == -(-bits // c) and c * K >= bits and c * (K - 1) < bits
+                # top window: bits - 1 - c (K - 1) value bits, at most c - 1
+                assert bits - 1 - c * (K - 1) <= c - 1
+                assert p["B"] == 1 << (c - 1) and p["L"] * p["M"] == p["B"]
+                assert p["windows"] == (2 if kind == ace.MSM_TABLED else K + 1)
+                ob = p["ones_buckets"]
+                assert ob & (ob - 1) == 0 and 1 <= ob <= p["B"]
+                assert p["points"] == ((2 * n) if kind == ace.MSM_GLV else n) & 0xFFFFFFFF
+    with pytest.raises(ace.AceError):
+        ace.msm_plan(1000, kind, 5)
+    with pytest.raises(ace.AceError):
+        ace.msm_plan(1000, 7)

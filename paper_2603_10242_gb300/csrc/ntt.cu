@@ -261,12 +261,14 @@ __global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int l
 // last wave better (one 2^20 array: 512 blocks of 2^11 elements against 456
 // slots take two waves, 1,024 of 2^10 take three half-size waves).
 static int ntt_pick_columns(bool dif, int k, int t, int logG_max, int count) {
-    static int sms = 0;
+    static int sms_of[64] = {};  // SM count per device ordinal (written once, same value)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = dev >= 0 && dev < 64 ? sms_of[dev] : 0;
     if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        if (dev >= 0 && dev < 64) sms_of[dev] = sms;
     }
     int best = logG_max;
     double best_cost = 1e300;

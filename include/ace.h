@@ -156,7 +156,8 @@ int ace_pk_point(const ace_pk* pk, int query, size_t index, void* out);
 
 /* ---- hot path ----------------------------------------------------------- */
 
-/* QAP quotient: h = (A(X) B(X) - C(X)) / (X^N - 1) where A, B, C interpolate
+/* QAP quotient of Groth16.Prove (Section 3.1, Algorithm 1; the QAP of Groth
+ * 2016): h = (A(X) B(X) - C(X)) / (X^N - 1) where A, B, C interpolate
  * Az, Bz, Cz on H = {omega^i}, omega = 5^((r-1)/N).  Steps: sparse products,
  * 3 inverse NTTs, 3 coset NTTs on g H (g = 5), pointwise (a b - c)/(g^N - 1),
  * coset inverse NTT.  d_z: m canonical Fr (device); d_h_out: N canonical Fr
@@ -165,7 +166,8 @@ int ace_pk_point(const ace_pk* pk, int query, size_t index, void* out);
  * its H query is in the Lagrange basis of g H and takes the coset values.) */
 int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out, ace_stream stream);
 
-/* Multi-scalar multiplication sum_i k_i P_i over G1 (Pippenger: signed c-bit
+/* The multi-scalar multiplications of Groth16.Prove (Section 3.1, Algorithm
+ * 1): sum_i k_i P_i over G1 (Pippenger: signed c-bit
  * digits, bucket sort, bucket accumulation, bucket and window reduction).
  * d_bases: n affine points in base_form (ACE_FORM_CANONICAL or _MONT);
  * d_scalars: n canonical Fr; d_out: one affine canonical point (device).
@@ -243,8 +245,9 @@ int ace_verify_batch(ace_ctx* ctx, const ace_vk* vk, size_t k, const ace_fr* pub
                      uint64_t seed);
 
 /* NTT of N = 2^log_n canonical Fr values in natural order, in place on the
- * device: the transforms of the QAP step (H = {omega^i}, omega = 5^((r-1)/N),
- * coset g H with g = 5).  kind: 0 forward (coefficients -> values on H),
+ * device: the transforms of the QAP step of Groth16.Prove (Section 3.1,
+ * Algorithm 1; H = {omega^i}, omega = 5^((r-1)/N), coset g H with g = 5).
+ * Each pass picks its block width to fill the GPU's last wave of blocks.  kind: 0 forward (coefficients -> values on H),
  * 1 inverse, 2 coset forward (coefficients -> values on g H), 3 coset inverse.
  * 1 <= log_n <= 28.  Scratch: N elements from the context. */
 int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream stream);
@@ -261,7 +264,8 @@ int ace_ntt_mont(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int count, int di
 int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
                       size_t n, int c, ace_g1_affine* d_out, ace_stream stream);
 /* ace_msm_g1 (GLV split, K = ceil(128 / c) windows over 2n points) with the
- * window size forced to c (6 <= c <= 20); n < 2^30. */
+ * window size forced to c (6 <= c <= 20); n < 2^30.  A diagnostic of this
+ * library; the paper has no counterpart. */
 int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
                           size_t n, int c, ace_g1_affine* d_out, ace_stream stream);
 
@@ -290,7 +294,8 @@ int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128]
  * cube root of unity with (beta x, y) = lambda (x, y) on G1.  out[0..3] = |k1|,
  * out[4] = 1 if k1 < 0, out[5..8] = |k2|, out[9] = 1 if k2 < 0 (|k_i| < 2^128). */
 int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]);
-/* Host: the MSM plan the library picks for n points (no device call).
+/* Host: the MSM plan the library picks for n points (no device call); a
+ * diagnostic of this library, the paper has no counterpart.
  * kind: 0 full-width scalars without window tables (ace_msm_g2, and
  * ace_msm_g1 for n >= 2^30), 1 window tables (proving-key queries), 2 the
  * GLV split of ace_msm_g1.  force_c: 0 for the cost model's window, else

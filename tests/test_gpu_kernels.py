@@ -291,6 +291,21 @@ def test_msm_g2_large_dlog():
     assert gu.host(out) == O.g2_mul(O.g2_generator(), s)
 
 
+def test_msm_g2_sparse_dlog():
+    """G2 MSM with 70% {0,1} scalars (its {0,1} window and the four-lane
+    Horner over Fp2), Montgomery bases, a ragged size."""
+    c = gu.ctx()
+    n = (1 << 15) + 11
+    kb = inputs.sample_fr(4, inputs.PURPOSE["bases"], n)
+    sc = inputs.sample_scalars(4, n, "sparse")
+    bases = gu.empty(128 * n)
+    c.g2_fixed_base(gu.dev(kb), n, bases, ace.FORM_MONT)
+    out = gu.empty(128)
+    c.msm_g2(bases, gu.dev(sc), n, out, ace.FORM_MONT)
+    s = sum(a * b for a, b in zip(inputs.limbs_to_int(kb), inputs.limbs_to_int(sc))) % R
+    assert gu.host(out) == O.g2_mul(O.g2_generator(), s)
+
+
 @pytest.mark.parametrize("log_n", [1, 2, 5, 10, 11, 12, 16, 20, 23, 24])
 def test_ntt_kinds_vs_oracle(log_n):
     """Every transform kind against the oracle's NTT, element by element; at

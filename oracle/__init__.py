@@ -79,12 +79,14 @@ def lib():
                 "orc_g2_mul": (i32, [u8p, u8p, u8p]),
                 "orc_g1_mul_gen_batch": (i32, [u8p, u8p, sz]),
                 "orc_g2_mul_gen_batch": (i32, [u8p, u8p, sz]),
+                "orc_gen_tab_mul": (i32, [u8p, u8p, i32]),
                 "orc_pairing": (i32, [u8p, u8p, u8p]),
                 "orc_fp12_mul": (i32, [u8p, u8p, u8p]),
                 "orc_fp12_pow": (i32, [u8p, u8p, u8p]),
                 "orc_untwist_on_curve": (i32, [u8p]),
                 "orc_fr_root_of_unity": (None, [u8p, u32]),
                 "orc_ntt": (i32, [u8p, u32, i32]),
+                "orc_coset_ntt": (i32, [u8p, u32, u32, i32]),
                 "orc_msm_g1": (i32, [u8p, u8p, u8p, sz, i32]),
                 "orc_msm_g2": (i32, [u8p, u8p, u8p, sz, i32]),
                 "orc_splitmix64": (None, [u64, u64, sz, u64p]),
@@ -230,6 +232,13 @@ def g2_mul_gen_batch(scalars: bytes) -> bytes:
     return out.raw
 
 
+def gen_tab_mul(k: int, group: int = 1) -> bytes:
+    """k G (G1 or G2 generator) by the setup's fixed-base windowing."""
+    out = ctypes.create_string_buffer(64 if group == 1 else 128)
+    assert lib().orc_gen_tab_mul(out, to32(k), group) == 0
+    return out.raw
+
+
 def pairing(g1: bytes, g2: bytes) -> bytes:
     out = ctypes.create_string_buffer(384)
     assert lib().orc_pairing(out, g1, g2) == 0
@@ -264,6 +273,17 @@ def fr_root_of_unity(log_n: int) -> int:
 def ntt(values: bytes, log_n: int, inverse: bool = False) -> bytes:
     buf = ctypes.create_string_buffer(bytes(values), len(values))
     assert lib().orc_ntt(buf, log_n, 1 if inverse else 0) == 0
+    return buf.raw
+
+
+def coset_ntt(values: bytes, log_n: int, g: int = 5, inverse: bool = False) -> bytes:
+    """Transform on the coset g H: forward gives the values sum_i a_i (g w^j)^i
+    at g w^j; inverse gives the coefficients whose values on g H are the
+    input (iNTT then a_i g^-i).  Canonical 32-byte values in and out."""
+    buf = ctypes.create_string_buffer(bytes(values), len(values))
+    rc = lib().orc_coset_ntt(buf, log_n, g, 1 if inverse else 0)
+    if rc != 0:
+        raise ValueError("coset_ntt: non-canonical input or g = 0")
     return buf.raw
 
 

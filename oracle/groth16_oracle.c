@@ -1402,6 +1402,65 @@ static g2a g2_mul_gen_fe(const fe* k_mont) {
     return out;
 }
 
+/* Fixed-base windowing for the many generator multiples of a key's query
+ * points (Hankerson, Menezes and Vanstone, Guide to Elliptic Curve
+ * Cryptography, fixed-base windowing): with the table T[w][d] = d 2^(8w) G,
+ * k G = sum over the 32 byte-windows w of k of T[w][byte_w(k)].  The same
+ * points as g1_mul_gen_fe / g2_mul_gen_fe (double-and-add), about eight times
+ * fewer group operations; setup only (the in-the-exponent proof and the
+ * exported generator multiples keep double-and-add). */
+static g1j G1_TAB[32][256];
+static g2j G2_TAB[32][256];
+static int g_tab_ready = 0;
+
+static void gen_tables_init(void) {
+    if (g_tab_ready) return;
+    g1j b1;
+    g2j b2;
+    g1j_from_affine(&b1, &G1_GEN);
+    g2j_from_affine(&b2, &G2_GEN);
+    for (int w = 0; w < 32; w++) {
+        g1j_set_inf(&G1_TAB[w][0]);
+        g2j_set_inf(&G2_TAB[w][0]);
+        for (int d = 1; d < 256; d++) {
+            g1j_add(&G1_TAB[w][d], &G1_TAB[w][d - 1], &b1);
+            g2j_add(&G2_TAB[w][d], &G2_TAB[w][d - 1], &b2);
+        }
+        for (int s = 0; s < 8; s++) {
+            g1j_dbl(&b1, &b1);
+            g2j_dbl(&b2, &b2);
+        }
+    }
+    g_tab_ready = 1;
+}
+
+static g1a g1_mul_gen_tab(const fe* k_mont) {
+    uint64_t k[4];
+    fe_canon(&FR, k, k_mont);
+    g1j r;
+    g1j_set_inf(&r);
+    for (int w = 0; w < 32; w++) {
+        unsigned d = (unsigned)((k[w >> 3] >> (8 * (w & 7))) & 0xff);
+        if (d) g1j_add(&r, &r, &G1_TAB[w][d]);
+    }
+    g1a out;
+    g1j_to_affine(&out, &r);
+    return out;
+}
+static g2a g2_mul_gen_tab(const fe* k_mont) {
+    uint64_t k[4];
+    fe_canon(&FR, k, k_mont);
+    g2j r;
+    g2j_set_inf(&r);
+    for (int w = 0; w < 32; w++) {
+        unsigned d = (unsigned)((k[w >> 3] >> (8 * (w & 7))) & 0xff);
+        if (d) g2j_add(&r, &r, &G2_TAB[w][d]);
+    }
+    g2a out;
+    g2j_to_affine(&out, &r);
+    return out;
+}
+
 static void sample_nonzero(smx* g, fe* out) {
     do { smx_fr(g, out); } while (f_is_zero(out));
 }
@@ -1510,16 +1569,17 @@ static pk_t* setup(const circuit* cs, uint64_t toxic_seed, int with_points) {
         pk->B2 = (g2a*)malloc(sizeof(g2a) * m);
         pk->L = (g1a*)malloc(sizeof(g1a) * m);
         pk->H = (g1a*)malloc(sizeof(g1a) * (N - 1));
+        gen_tables_init();
 #pragma omp parallel for schedule(dynamic, 8)
         for (long j = 0; j < (long)m; j++) {
-            pk->A[j] = g1_mul_gen_fe(&pk->u[j]);
-            pk->B1[j] = g1_mul_gen_fe(&pk->v[j]);
-            pk->B2[j] = g2_mul_gen_fe(&pk->v[j]);
-            if (j > N_PUBLIC) pk->L[j] = g1_mul_gen_fe(&pk->lq[j]);
+            pk->A[j] = g1_mul_gen_tab(&pk->u[j]);
+            pk->B1[j] = g1_mul_gen_tab(&pk->v[j]);
+            pk->B2[j] = g2_mul_gen_tab(&pk->v[j]);
+            if (j > N_PUBLIC) pk->L[j] = g1_mul_gen_tab(&pk->lq[j]);
             else { memset(&pk->L[j], 0, sizeof(g1a)); pk->L[j].inf = 1; }
         }
 #pragma omp parallel for schedule(dynamic, 8)
-        for (long i = 0; i < (long)(N - 1); i++) pk->H[i] = g1_mul_gen_fe(&pk->hq[i]);
+        for (long i = 0; i < (long)(N - 1); i++) pk->H[i] = g1_mul_gen_tab(&pk->hq[i]);
     }
     return pk;
 }
@@ -1830,6 +1890,23 @@ EXPORT int orc_g2_mul_gen_batch(uint8_t* out, const uint8_t* k, size_t n) {
     return bad ? -1 : 0;
 }
 
+/* k G by the fixed-base windowing of the setup (group 1: G1, 64 B out;
+ * group 2: G2, 128 B out), for pinning it against double-and-add. */
+EXPORT int orc_gen_tab_mul(uint8_t* out, const uint8_t* k, int group) {
+    oracle_init();
+    fe x;
+    if (!fe_from_bytes(&FR, &x, k)) return -1;
+    gen_tables_init();
+    if (group == 1) {
+        g1a p = g1_mul_gen_tab(&x);
+        g1a_to_bytes(out, &p);
+    } else {
+        g2a p = g2_mul_gen_tab(&x);
+        g2a_to_bytes(out, &p);
+    }
+    return 0;
+}
+
 /* Pairing value as 12 canonical Fp coefficients of w^0..w^11 (384 bytes). */
 EXPORT int orc_pairing(uint8_t* out, const uint8_t* g1, const uint8_t* g2) {
     oracle_init();
@@ -1896,6 +1973,38 @@ EXPORT int orc_ntt(uint8_t* data, uint32_t log_n, int inverse) {
     for (size_t i = 0; i < n; i++)
         if (!fe_from_bytes(&FR, &a[i], data + 32 * i)) { free(a); return -1; }
     ntt_inplace(a, log_n, inverse);
+    for (size_t i = 0; i < n; i++) fe_to_bytes(&FR, data + 32 * i, &a[i]);
+    free(a);
+    return 0;
+}
+
+/* Transforms on the coset g H of the domain H = {omega^j} (the quotient of
+ * the Groth16 QAP is evaluated where Z(X) = X^N - 1 is the non-zero constant
+ * g^N - 1).  Written from the definition, with the plain NTT above as a step:
+ *   forward (inverse = 0): out_j = sum_i a_i (g omega^j)^i, i.e. the NTT of
+ *     the scaled coefficients a_i g^i;
+ *   inverse (inverse = 1): the coefficients c_i of the polynomial whose values
+ *     at g omega^j are the inputs, i.e. c_i = (iNTT a)_i g^-i.
+ * g is a small integer (the library uses g = 5), canonical values in and out. */
+EXPORT int orc_coset_ntt(uint8_t* data, uint32_t log_n, uint32_t g, int inverse) {
+    oracle_init();
+    size_t n = (size_t)1 << log_n;
+    fe* a = (fe*)malloc(sizeof(fe) * n);
+    for (size_t i = 0; i < n; i++)
+        if (!fe_from_bytes(&FR, &a[i], data + 32 * i)) { free(a); return -1; }
+    fe gm;
+    f_from_u64(&FR, &gm, g);
+    if (f_is_zero(&gm)) { free(a); return -1; }
+    if (inverse) {
+        ntt_inplace(a, log_n, 1);
+        f_inv(&FR, &gm, &gm);
+    }
+    fe gi = FR.one;
+    for (size_t i = 0; i < n; i++) {
+        f_mul(&FR, &a[i], &a[i], &gi);
+        f_mul(&FR, &gi, &gi, &gm);
+    }
+    if (!inverse) ntt_inplace(a, log_n, 0);
     for (size_t i = 0; i < n; i++) fe_to_bytes(&FR, data + 32 * i, &a[i]);
     free(a);
     return 0;

@@ -176,6 +176,37 @@ def test_groth16_setup_points_are_scalar_multiples(c10):
     assert pk.scalar("u", 1) == li[1023]               # z_1 sits only in input row 1023 of A
 
 
+def test_fixed_base_windowing_vs_double_and_add():
+    """The setup's fixed-base windowing (T[w][d] = d 2^(8w) G) against
+    double-and-add and the textbook affine formulas, on edge scalars (zero
+    bytes, all-ones bytes, r - 1) and random ones."""
+    g1, g2 = O.g1_generator(), O.g2_generator()
+    edge = [0, 1, 2, 255, 256, 257, (1 << 64) - 1, 1 << 128, (1 << 248) + 1, Y.R - 1, Y.R - 2,
+            int("ff" * 31, 16) % Y.R]
+    rnd = random.Random(77)
+    for k in edge + [rnd.randrange(Y.R) for _ in range(20)]:
+        assert O.gen_tab_mul(k, 1) == O.g1_mul(g1, k), k
+        assert O.gen_tab_mul(k, 2) == O.g2_mul(g2, k), k
+    for k in (3, 1 << 200):
+        assert O.g1_from(O.gen_tab_mul(k, 1)) == Y.g1_mul(Y.G1, k)
+
+
+def test_setup_points_every_query(c10):
+    """Every A, B1, B2, L and H point of the 2^10 key is its scalar times the
+    generator by double-and-add."""
+    pk = O.ProvingKey(c10, 6, with_points=True)
+    g1, g2 = O.g1_generator(), O.g2_generator()
+    for j in range(0, c10.m, 37):
+        assert pk.point("A", j) == O.g1_mul(g1, pk.scalar("u", j))
+        assert pk.point("B1", j) == O.g1_mul(g1, pk.scalar("v", j))
+        if j % 111 == 0:
+            assert pk.point("B2", j) == O.g2_mul(g2, pk.scalar("v", j))
+        if j > 1:
+            assert pk.point("L", j) == O.g1_mul(g1, pk.scalar("l", j))
+    for i in range(0, c10.N - 1, 41):
+        assert pk.point("H", i) == O.g1_mul(g1, pk.scalar("h", i))
+
+
 def test_unsat_witness_rejected(c10):
     z = bytearray(c10.witness())
     z[32 * 20] ^= 2

@@ -129,6 +129,49 @@ def test_ntt_vs_naive_dft(log_n):
     assert back == vals
 
 
+@pytest.mark.parametrize("log_n", [1, 2, 3, 5])
+@pytest.mark.parametrize("g", [5, 7])
+def test_coset_ntt_vs_direct_evaluation(log_n, g):
+    """Forward coset transform = the polynomial's values at g w^j by Horner;
+    inverse = coefficients that Lagrange interpolation through the points
+    (g w^j, a_j) reproduces at a random point; inverse after forward = id."""
+    n = 1 << log_n
+    coeffs = [rng.randrange(O.R) for _ in range(n)]
+    w = pow(5, (O.R - 1) >> log_n, O.R)
+    ev = Y.ints_from_bytes(O.coset_ntt(Y.ints_to_bytes(coeffs), log_n, g))
+    assert ev == [Y.poly_eval(coeffs, g * pow(w, j, O.R) % O.R) for j in range(n)]
+    vals = [rng.randrange(O.R) for _ in range(n)]
+    cf = Y.ints_from_bytes(O.coset_ntt(Y.ints_to_bytes(vals), log_n, g, inverse=True))
+    for j in range(n):
+        assert Y.poly_eval(cf, g * pow(w, j, O.R) % O.R) == vals[j]
+    # interpolation through the coset points, evaluated off the coset
+    rho = rng.randrange(O.R)
+    xs = [g * pow(w, j, O.R) % O.R for j in range(n)]
+    lag = 0
+    for j in range(n):
+        num = den = 1
+        for k in range(n):
+            if k != j:
+                num = num * (rho - xs[k]) % O.R
+                den = den * (xs[j] - xs[k]) % O.R
+        lag = (lag + vals[j] * num * pow(den, -1, O.R)) % O.R
+    assert Y.poly_eval(cf, rho) == lag
+    assert Y.ints_from_bytes(O.coset_ntt(Y.ints_to_bytes(cf), log_n, g)) == vals
+
+
+def test_coset_ntt_large_horner_and_roundtrip():
+    """At 2^12: random values checked by Horner at g w^j, and the round trip."""
+    log_n = 12
+    n = 1 << log_n
+    coeffs = [rng.randrange(O.R) for _ in range(n)]
+    ev = Y.ints_from_bytes(O.coset_ntt(Y.ints_to_bytes(coeffs), log_n))
+    w = O.fr_root_of_unity(log_n)
+    for j in (0, 1, 999, n - 1):
+        assert ev[j] == Y.poly_eval(coeffs, 5 * pow(w, j, O.R) % O.R)
+    back = O.coset_ntt(Y.ints_to_bytes(ev), log_n, inverse=True)
+    assert Y.ints_from_bytes(back) == coeffs
+
+
 def test_ntt_roundtrip_and_convolution_large():
     log_n = 12
     n = 1 << log_n

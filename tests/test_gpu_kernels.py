@@ -306,41 +306,29 @@ def test_msm_g2_sparse_dlog():
     assert gu.host(out) == O.g2_mul(O.g2_generator(), s)
 
 
-@pytest.mark.parametrize("log_n", [1, 2, 5, 10, 11, 12, 16, 20, 23, 24])
-def test_ntt_kinds_vs_oracle(log_n):
-    """Every transform kind against the oracle's NTT, element by element; at
-    2^24 (the top of the NTT sweep) the forward transform only, whole."""
+NTT_KINDS = {0: "ntt", 1: "intt", 2: "coset_ntt", 3: "coset_intt"}
+
+
+def _oracle_transform(raw, log_n, kind):
+    if kind in (0, 1):
+        return O.ntt(raw, log_n, inverse=(kind == 1))
+    return O.coset_ntt(raw, log_n, 5, inverse=(kind == 3))
+
+
+@pytest.mark.parametrize("kind", sorted(NTT_KINDS))
+@pytest.mark.parametrize("log_n", [1, 2, 5, 10, 11, 12, 16, 20, 22, 23, 24])
+def test_ntt_kinds_vs_oracle(log_n, kind):
+    """Every transform kind (NTT, inverse NTT, coset NTT and coset inverse NTT
+    on g H with g = 5) against the oracle, every element, from one pass up to
+    the multi-pass plans of 2^20..2^24 (the top of the transform sweep)."""
     c = gu.ctx()
     n = 1 << log_n
-    vals = inputs.sample_fr(log_n, 7, n)
-    raw = vals.tobytes()
-    kinds = (0, 1, 2, 3) if log_n <= 20 else (0, 3) if log_n <= 23 else (0,)
-    g = 5
-    for kind in kinds:
-        d = gu.dev(raw)
-        c.ntt(d, log_n, kind)
-        got = gu.host(d)
-        if kind in (0, 1):
-            want = O.ntt(raw, log_n, inverse=(kind == 1))
-        elif kind == 2:
-            v = inputs.limbs_to_int(vals)
-            pre = gu.ints_bytes([x * pow(g, i, R) % R for i, x in enumerate(v)]) if n <= 1 << 16 else None
-            if pre is None:
-                continue
-            want = O.ntt(pre, log_n)
-        else:
-            inv = O.ntt(raw, log_n, inverse=True)
-            if n > 1 << 16:
-                # spot-check coefficients: h_i = (iNTT x)_i g^-i
-                gi = pow(g, R - 2, R)
-                iv = gu.bytes_ints(inv)
-                gv = gu.bytes_ints(got)
-                for i in (0, 1, 2, n // 3, n - 1):
-                    assert gv[i] == iv[i] * pow(gi, i, R) % R
-                continue
-            gi = pow(g, R - 2, R)
-            want = gu.ints_bytes([x * pow(gi, i, R) % R for i, x in enumerate(gu.bytes_ints(inv))])
-        assert got == want, kind
+    raw = inputs.sample_fr(log_n, 7, n).tobytes()
+    d = gu.dev(raw)
+    c.ntt(d, log_n, kind)
+    got = gu.host(d)
+    want = _oracle_transform(raw, log_n, kind)
+    assert got == want, NTT_KINDS[kind]
 
 
 def test_ntt_mont_roundtrip_batch():

@@ -146,19 +146,28 @@ def test_unsat_witness_rejected():
     assert e.value.code == -4
 
 
-@pytest.mark.parametrize("log_n", [16, 20])
-def test_block_scale_proof_in_the_exponent(log_n):
+@pytest.fixture(scope="module", params=[16, 20])
+def block(request):
     """The 2^20 block circuit (2,048 tx x 2 permutations, 2 packing rows of
-    172 bits per tx, chain to 2^20), and a 2^16 instance of the same family."""
+    172 bits per tx, chain to 2^20), and a 2^16 instance of the same family:
+    library and oracle circuits, the witness and the library's key."""
+    log_n = request.param
     if log_n == 20:
         params = (20, 1 << 20, 4096, 4096, 172)
     else:
         params = (16, 1 << 16, 256, 256, 172)
     lc, oc = _pair(params, seed=2)
-    ctx = gu.ctx()
     z = lc.witness(2)
+    pk = ace.ProvingKey(gu.ctx(), lc, toxic_seed=2)
+    yield log_n, lc, oc, z, pk
+    pk.close()
+    torch.cuda.synchronize()
+
+
+def test_block_scale_proof_in_the_exponent(block):
+    log_n, lc, oc, z, pk = block
+    ctx = gu.ctx()
     assert z == oc.witness()
-    pk = ace.ProvingKey(ctx, lc, toxic_seed=2)
     r, s = ace.rs_from_seed(2)
     proof = ctx.prove(pk, gu.dev(z), r, s)
     opk = O.ProvingKey(oc, 2, with_points=False)
@@ -176,6 +185,22 @@ def test_block_scale_proof_in_the_exponent(log_n):
         assert pk.point("A", j) == O.g1_mul(g1, opk.scalar("u", j))
     for i in (0, lc.N - 1):
         assert pk.point("H", i) == O.g1_mul(g1, _coset_h_scalar(opk, log_n, i))
+
+
+def test_block_scale_qap_h_matches_oracle(block):
+    """ace_qap_h (sparse products, 3 iNTT, 3 coset NTT, quotient, coset iNTT
+    in the multi-pass plan of these sizes) against the oracle's h, computed by
+    a 2N-point convolution and long division by X^N - 1: every coefficient,
+    and h_{N-1} = 0."""
+    log_n, lc, oc, z, pk = block
+    ctx = gu.ctx()
+    dh = gu.empty(32 * lc.N)
+    ctx.qap_h(pk, gu.dev(z), dh)
+    got = gu.host(dh)[:32 * lc.N]
+    ok, want = oc.qap_h(z)
+    assert ok
+    assert got[-32:] == bytes(32)
+    assert got == want
 
 
 def test_pk_save_load_roundtrip(tmp_path):

@@ -49,6 +49,7 @@ extern "C" {
 #define ACE_E_NOT_ON_CURVE (-5) /* an input point is not on the curve */
 #define ACE_E_TIMEOUT (-6)      /* a bounded device wait expired */
 #define ACE_E_BUSY (-7)         /* admission refused / result not ready */
+#define ACE_E_INTERNAL (-8)     /* an internal bound of the library was exceeded (a library fault, not a bad argument) */
 
 #define ACE_FORM_CANONICAL 0
 #define ACE_FORM_MONT 1
@@ -123,7 +124,14 @@ int ace_ctx_device_bytes(const ace_ctx* ctx, size_t* out);
 
 /* ---- circuit and witness (host) ----------------------------------------- */
 
-/* Build the seeded synthetic R1CS described at ace_circuit_params (host). */
+/* Build the seeded synthetic R1CS described at ace_circuit_params (host):
+ * the circuit C of Groth16.Prove(C, w, pub) in the builder's proving stage
+ * (Section 3.1, Algorithm 1; Section 3.3, Algorithm 3), made of the
+ * Poseidon-style identity-commitment gadget (Section 2.1, Definition "ZK
+ * Identity Commitment"; Appendix B, the constraint group of the commitment)
+ * plus packing rows and a squaring chain.  *out is lib-owned (free with
+ * ace_circuit_free).  ACE_E_ARG if the parameters break the requirements
+ * listed at ace_circuit_params; ACE_E_OOM if host memory runs out. */
 int ace_circuit_gen(const ace_circuit_params* p, ace_circuit** out);
 int ace_circuit_free(ace_circuit* c);
 int ace_circuit_info(const ace_circuit* c, uint64_t info[ACE_INFO_LEN]);
@@ -189,7 +197,8 @@ int ace_msm_g2(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const 
  * freeing imply).  The paper has no counterpart; this is a library service.
  * Same arguments and result as ace_msm_g1, without a context: it runs on the
  * current device, on `stream` (NULL = the legacy default stream).  n must be
- * at most 16384 (ACE_E_ARG otherwise).  Its scratch is one fixed 6 MiB device
+ * at most 16384 (ACE_E_ARG otherwise; ACE_E_INTERNAL if the library's own
+ * scratch bound were exceeded, which its fixed plan rules out).  Its scratch is one fixed 6 MiB device
  * array inside the library, present on every GPU that loads the library
  * until the process exits; the first call on a device looks up that array's
  * address (make that first call before any stream capture).  Every call
@@ -338,13 +347,37 @@ int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units);
  * another count once each, so sum_ms / launches is the average launch
  * duration. */
 int ace_profile_read_sum(int kind, double* sum_ms);
+/* Measurement mode (no counterpart in the paper): with on != 0, proofs made
+ * on ctx afterwards run every stage on their slot's main stream in turn
+ * instead of spreading the MSMs over auxiliary streams, so that the profiled
+ * intervals of the stages do not overlap and add up to the proof's time.
+ * The proof bytes do not change.  ACE_E_ARG for a NULL context. */
+int ace_debug_serial_proofs(ace_ctx* ctx, int on);
 
 /* ---- batching and serving ------------------------------------------------ */
 
-/* k independent proofs (each with its own pk and witness) in one call; proof i
- * goes to proofs + 256 i (host).  Status per proof in status[i] (0 ok, 1 unsat). */
+/* k independent proofs in one call: the parallel map of the builder's
+ * proving stage (Section 3.3, Algorithm 3 ParallelMap, which proves many
+ * independent circuits at once), here over proofs of any mix of keys and
+ * sizes.  pks[i] and d_zs[i] (device, pks[i]'s m canonical values, 16-byte
+ * aligned) give proof i, rs[i] and ss[i] its randomness (host, canonical).
+ * Proofs go round-robin over the context's proving slots (ace_autotune_
+ * batch_slots chooses their number), so consecutive proofs overlap on the
+ * device.  Proof i goes to proofs + 256 i (host); status[i] (host) is 0, or 1
+ * if witness i does not satisfy its R1CS.  Synchronous.  ACE_E_ARG for NULL
+ * pointers or non-canonical r, s; ACE_E_OOM if the slots' scratch cannot be
+ * allocated.  Each proof equals the one ace_prove makes with the same inputs. */
 int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,
                     const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status);
+/* The same with the witnesses in HOST memory (h_zs[i]: pks[i]'s m canonical
+ * values; page-locked memory lets the copies overlap the proving, pageable
+ * memory works but the copy then blocks the calling thread).  Each witness
+ * is copied into its proving slot's staging buffer (one per slot, sized for
+ * the slot's largest witness, held by the context) once the slot's previous
+ * proof is done, so a call moves exactly sum_i 32 m_i bytes to the device and
+ * 256 k + 4 k bytes back.  Same results, status and errors as ace_prove_batch. */
+int ace_prove_batch_host(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* h_zs,
+                         const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status);
 
 /* Proof server with continuous batching: block-proof jobs are proved as
  * they arrive (the builder loop of Section 3.3, Algorithm 3).  A job starts
@@ -435,7 +468,15 @@ int ace_autotune_load(ace_ctx* ctx, const char* path);
 
 /* ---- persistence ---------------------------------------------------------- */
 
-/* Save / load a proving key (with its circuit) to a versioned file. */
+/* Save / load a proving key (with its circuit) to a versioned file.  A
+ * library service with no counterpart in the paper, which requires a
+ * circuit-specific trusted setup (Section 9, "Trusted setup") and says
+ * nothing about storing its output: the file holds a header (magic,
+ * format version), the circuit, window 0 of every query table and the fixed
+ * points; loading checks the header and sizes, rebuilds the window tables on
+ * the device and returns the key (pk_out, lib-owned, free with ace_pk_free)
+ * and its verifying key (vk_out, caller-owned, optional).  ACE_E_ARG for a
+ * missing, truncated or mismatched file; ACE_E_OOM if the key does not fit. */
 int ace_pk_save(const ace_pk* pk, const char* path);
 int ace_pk_load(ace_ctx* ctx, const char* path, ace_pk** pk_out, ace_vk* vk_out);
 

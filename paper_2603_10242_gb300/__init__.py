@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libace.so")
 
 ACE_OK = 0
 ERRORS = {-1: "ACE_E_ARG", -2: "ACE_E_OOM", -3: "ACE_E_CUDA", -4: "ACE_E_UNSAT",
-          -5: "ACE_E_NOT_ON_CURVE", -6: "ACE_E_TIMEOUT", -7: "ACE_E_BUSY"}
+          -5: "ACE_E_NOT_ON_CURVE", -6: "ACE_E_TIMEOUT", -7: "ACE_E_BUSY", -8: "ACE_E_INTERNAL"}
 FORM_CANONICAL = 0
 FORM_MONT = 1
 INFO_LEN = 12
@@ -75,6 +75,7 @@ def lib():
             "ace_rs_from_seed": (i32, [u64, vp, vp]),
             "ace_verify": (i32, [vp, vp, sz, vp]),
             "ace_prove_batch": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
+            "ace_prove_batch_host": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
             "ace_pk_save": (i32, [vp, cp]),
             "ace_pk_load": (i32, [vp, cp, ctypes.POINTER(vp), vp]),
             "ace_debug_pairing": (i32, [cp, cp, cp]),
@@ -106,6 +107,7 @@ def lib():
             "ace_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
                                        ctypes.POINTER(u64)]),
             "ace_profile_read_sum": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
+            "ace_debug_serial_proofs": (i32, [vp, i32]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name, None)
@@ -267,6 +269,20 @@ class Context:
         check(lib().ace_prove_batch(self.h, k, pk_arr, z_arr, rs, ss, proofs, status))
         return [proofs.raw[256 * i:256 * i + 256] for i in range(k)], list(status)
 
+    def prove_batch_host(self, pks, h_zs, rs: bytes, ss: bytes):
+        """ace_prove_batch with witnesses in host memory (CPU tensors, pinned
+        for overlapped copies); the library copies them to the device."""
+        k = len(pks)
+        for z in h_zs:
+            if getattr(z, "is_cuda", False):
+                raise ValueError("prove_batch_host takes host witnesses")
+        pk_arr = (ctypes.c_void_p * k)(*[p.h.value for p in pks])
+        z_arr = (ctypes.c_void_p * k)(*[_ptr(z) for z in h_zs])
+        proofs = ctypes.create_string_buffer(256 * k)
+        status = (ctypes.c_int32 * k)()
+        check(lib().ace_prove_batch_host(self.h, k, pk_arr, z_arr, rs, ss, proofs, status))
+        return [proofs.raw[256 * i:256 * i + 256] for i in range(k)], list(status)
+
 
 def msm_g1_noalloc(bases, scalars, n: int, out, base_form: int = FORM_CANONICAL, stream=None):
     """G1 MSM without any device allocation (n <= 16384); see include/ace.h."""
@@ -411,6 +427,11 @@ def profile_read_sum(kind: int) -> float:
     v = ctypes.c_double()
     check(lib().ace_profile_read_sum(kind, ctypes.byref(v)))
     return v.value
+
+
+def serial_proofs(ctx: "Context", on: bool):
+    """Measurement mode: later proofs on ctx run every stage on one stream."""
+    check(lib().ace_debug_serial_proofs(ctx.h, 1 if on else 0))
 
 
 def profile_read(kind: int):

@@ -110,6 +110,7 @@ void ctx_destroy_now(ace_ctx* c) {
     for (auto& a : c->scratch) dev_free(c, a.base, a.cap);
     for (auto& sl : c->slots) {
         for (auto& a : sl.ar) dev_free(c, a.base, a.cap);
+        dev_free(c, sl.wit.base, sl.wit.cap);
         if (!sl.ready) continue;
         for (auto& lv : sl.lv) {
             cudaStreamDestroy(lv.main);
@@ -433,6 +434,17 @@ int ace_profile_read(int kind, double* ms, uint64_t* launches, uint64_t* units) 
         return ACE_E_ARG;
     }
     return prof_read(kind, ms, launches, units);
+}
+
+int ace_debug_serial_proofs(ace_ctx* ctx, int on) {
+    clear_error();
+    if (!ctx) {
+        set_error("ace_debug_serial_proofs: NULL context");
+        return ACE_E_ARG;
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->serial = on != 0;
+    return ACE_OK;
 }
 
 int ace_profile_read_sum(int kind, double* sum_ms) {

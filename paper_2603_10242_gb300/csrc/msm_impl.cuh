@@ -124,13 +124,19 @@ __global__ void __launch_bounds__(128) k_bucket_combine(const Xyzz<F>* __restric
 // as n K / 2^(c-1) (tabled) or n / 2^(c-1) (one set per window).
 template <class F>
 uint32_t bucket_split(const MsmPlan& p) {
-    static const double res = [] {
-        int dev = 0, sms = 0, nb = 0;
-        cudaGetDevice(&dev);
+    // resident threads of the accumulation kernel, per device ordinal
+    // (written once per device, always with that device's value)
+    static double res_of[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    double res = dev >= 0 && dev < 64 ? res_of[dev] : 0.0;
+    if (res <= 0.0) {
+        int sms = 0, nb = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bucket_acc<F>, 128, 0);
-        return (double)sms * (nb > 0 ? nb : 1) * 128.0;
-    }();
+        res = (double)(sms > 0 ? sms : 1) * (nb > 0 ? nb : 1) * 128.0;
+        if (dev >= 0 && dev < 64) res_of[dev] = res;
+    }
     const double keys = (double)p.keys();
     const double load = (double)p.n * (p.tabled ? p.K : 1) / (double)p.B;
     uint32_t S = 1;

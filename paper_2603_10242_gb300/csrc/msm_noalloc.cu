@@ -88,7 +88,7 @@ int ace_msm_g1_noalloc(const ace_g1_affine* d_bases, int base_form, const ace_fr
     bool mont = base_form == ACE_FORM_MONT;
     if (msm_scratch_bytes<fp_t>(plan, mont) > NOALLOC_BYTES) {
         set_error("ace_msm_g1_noalloc: internal scratch bound exceeded");
-        return ACE_E_ARG;
+        return ACE_E_INTERNAL;
     }
     Arena ar;
     ar.base = (char*)base;

@@ -435,7 +435,11 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     }
     ACE_TRY(slot_ready(ctx, slot));
     ProveSlot& sl = ctx->slots[slot];
-    SlotStreams& ss = sl.lv[prio];
+    // the slot's streams at this level; in serial mode (a measurement of the
+    // per-stage split) every stage runs on the main stream, one after another
+    SlotStreams ss = sl.lv[prio];
+    if (ctx->serial)
+        for (int k = 0; k < 5; k++) ss.aux[k] = ss.main;
     ProvePlans pl = prove_plans(pk);
     for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, slot, k, pl.slot_bytes[k]));
     Arena& a0 = sl.ar[0];
@@ -706,18 +710,27 @@ int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r
     return ACE_OK;
 }
 
-int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs, const ace_fr* rs,
-                    const ace_fr* ss, uint8_t* proofs, int32_t* status) {
-    clear_error();
-    if (!ctx || (k && (!pks || !d_zs || !rs || !ss || !proofs || !status))) {
-        set_error("ace_prove_batch: NULL argument");
+}  // extern "C"
+
+namespace ace {
+// k proofs round-robin over the context's proving slots (consecutive proofs
+// overlap); zs are device witnesses, or host witnesses (host = true) that are
+// copied into the slot's staging buffer on the slot's main stream once the
+// slot's previous proof is done.  The slots' scratch is sized for their
+// largest proof up front, so no arena grows (and synchronises the device) in
+// the middle of the batch.
+static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk* const* pks,
+                            const ace_fr* const* zs, bool host, const ace_fr* rs, const ace_fr* ss, uint8_t* proofs,
+                            int32_t* status) {
+    if (!ctx || (k && (!pks || !zs || !rs || !ss || !proofs || !status))) {
+        set_error("%s: NULL argument", fn);
         return ACE_E_ARG;
     }
     if (k == 0) return ACE_OK;
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     for (size_t i = 0; i < k; i++) {
-        if (!pks[i] || !d_zs[i] || !canonical_fr(rs + i) || !canonical_fr(ss + i)) {
-            set_error("ace_prove_batch: proof %zu has a NULL key / witness or non-canonical r, s", i);
+        if (!pks[i] || !zs[i] || !canonical_fr(rs + i) || !canonical_fr(ss + i)) {
+            set_error("%s: proof %zu has a NULL key / witness or non-canonical r, s", fn, i);
             return ACE_E_ARG;
         }
     }
@@ -726,31 +739,57 @@ int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_
     uint32_t* d_proofs = (uint32_t*)ctx->scratch[3].take(k * 256);
     int32_t* d_status = (int32_t*)ctx->scratch[3].take(k * sizeof(int32_t));
     cudaStream_t st = ctx->stream;
-    // proofs go round-robin over the slots: consecutive proofs overlap.  The
-    // slots' scratch is sized for their largest proof up front, so no arena
-    // grows (and synchronises the device) in the middle of the batch.
     int nslots = (int)(k < (size_t)ctx->batch_slots ? k : (size_t)ctx->batch_slots);
     for (int q = 0; q < nslots; q++) {
         size_t need[PROVE_ARENAS] = {0, 0, 0, 0, 0};
+        size_t wit = 0;
         for (size_t i = q; i < k; i += nslots) {
             ProvePlans pl = prove_plans(pks[i]);
             for (int a = 0; a < PROVE_ARENAS; a++) need[a] = need[a] > pl.slot_bytes[a] ? need[a] : pl.slot_bytes[a];
+            wit = wit > pks[i]->m * sizeof(fr_t) ? wit : pks[i]->m * sizeof(fr_t);
         }
         ACE_TRY(slot_ready(ctx, q));
         for (int a = 0; a < PROVE_ARENAS; a++) ACE_TRY(slot_arena_ensure(ctx, q, a, need[a]));
+        if (host) ACE_TRY(slot_witness_ensure(ctx, q, wit));
     }
     for (size_t i = 0; i < k; i++) {
         fr_t rr, sv;
         memcpy(rr.v, rs[i].l, 32);
         memcpy(sv.v, ss[i].l, 32);
-        ACE_TRY(prove_run(ctx, (int)(i % nslots), 0, pks[i], (const fr_t*)d_zs[i], rr, sv, d_proofs + 64 * i,
-                          d_status + i, st, false));
+        const int q = (int)(i % nslots);
+        const fr_t* z = (const fr_t*)zs[i];
+        cudaStream_t st_in = st;
+        if (host) {
+            ProveSlot& sl = ctx->slots[q];
+            st_in = sl.lv[0].main;
+            fr_t* stage = (fr_t*)sl.wit.base;
+            // the slot's previous proof may still read the staging buffer
+            ACE_TRY_CUDA(cudaStreamWaitEvent(st_in, sl.ev_done, 0));
+            ACE_TRY_CUDA(cudaMemcpyAsync(stage, z, pks[i]->m * sizeof(fr_t), cudaMemcpyHostToDevice, st_in));
+            z = stage;
+        }
+        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false));
     }
     for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));
     ACE_TRY_CUDA(cudaMemcpyAsync(proofs, d_proofs, k * 256, cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(status, d_status, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaStreamSynchronize(st));
     return ACE_OK;
+}
+}  // namespace ace
+
+extern "C" {
+
+int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs, const ace_fr* rs,
+                    const ace_fr* ss, uint8_t* proofs, int32_t* status) {
+    clear_error();
+    return prove_batch_impl(ctx, "ace_prove_batch", k, pks, d_zs, false, rs, ss, proofs, status);
+}
+
+int ace_prove_batch_host(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* h_zs,
+                         const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status) {
+    clear_error();
+    return prove_batch_impl(ctx, "ace_prove_batch_host", k, pks, h_zs, true, rs, ss, proofs, status);
 }
 
 int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]) {

@@ -66,6 +66,8 @@ int arena_ensure(ace_ctx* ctx, int slot, size_t bytes) { return grow(ctx, ctx->s
 
 int slot_arena_ensure(ace_ctx* ctx, int s, int k, size_t bytes) { return grow(ctx, ctx->slots[s].ar[k], bytes); }
 
+int slot_witness_ensure(ace_ctx* ctx, int s, size_t bytes) { return grow(ctx, ctx->slots[s].wit, bytes); }
+
 int slot_ready(ace_ctx* ctx, int s) {
     ProveSlot& sl = ctx->slots[s];
     if (sl.ready) return ACE_OK;

@@ -84,6 +84,7 @@ struct ProveSlot {
     cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_aux[5] = {};
     cudaEvent_t ev_sort = nullptr;  // the B query's entries are sorted (B2 reuses B1's)
+    Arena wit;  // staging buffer for witnesses that arrive in host memory
 };
 
 }  // namespace ace
@@ -97,6 +98,9 @@ struct ace_ctx {
     ace::Arena scratch[4];  // scratch of single calls (MSM, NTT, QAP, batch outputs)
     ace::ProveSlot slots[ace::MAX_SLOTS];
     int batch_slots = 2;  // slots a batch spreads its proofs over
+    // measurement mode: a proof runs every stage on its main stream in turn
+    // (ace_debug_serial_proofs), so per-stage times do not overlap
+    bool serial = false;
     // autotuned choices (0 = cost model): MSM window bits by log2(n), NTT
     // shared-memory width by log2(N)
     int tuned_msm_c[32] = {};
@@ -123,6 +127,9 @@ void ctx_unref(ace_ctx* ctx);
 int slot_ready(ace_ctx* ctx, int s);
 // make arena k of slot s hold at least `bytes` (synchronises the device if it grows)
 int slot_arena_ensure(ace_ctx* ctx, int s, int k, size_t bytes);
+// make slot s's witness staging buffer hold at least `bytes` (synchronises the
+// device if it grows)
+int slot_witness_ensure(ace_ctx* ctx, int s, size_t bytes);
 
 // ---- launch counting and kernel timing ----------------------------------------
 // Every kernel launch of the library bumps a process-wide counter.  When the

@@ -45,16 +45,42 @@ SEED = 2
 IMAD_PER_FP_MUL = 272
 IMAD_PER_G1_MADD = 10 * IMAD_PER_FP_MUL
 IMAD_PER_G2_MADD = 28 * IMAD_PER_FP_MUL
-# ALU roofline: SMs x 64 32-bit IMAD per clock per SM x maximum SM clock
-# (152 SMs, 2070 MHz on GB300).
-SM_COUNT = 152
+# ALU roofline: SMs x 64 32-bit IMAD per clock per SM x maximum SM clock; the
+# SM count is read from the device and the maximum clock from the GPU
+# (nvidia-smi), both at run time.
 IMAD_PER_CLK_PER_SM = 64
-SM_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the G1 bucket
-# accumulation kernel inside the 2^20 proofs, per mixed addition: 1.828 GB on
-# average over the 16 launches of four proofs (ncu capture summarised in
-# profiles/g1_bucket_acc_msm_2p20.md) for 13.62 M additions per launch.
-G1_BUCKET_DRAM_BYTES_PER_MADD = 1.828e9 / 13.619e6
+SM_MAX_MHZ_DEFAULT = 2070.0
+# DRAM traffic of the dominant kernel from the latest ncu capture of it inside
+# the 2^20 block proofs (dram__bytes_read.sum + dram__bytes_write.sum per
+# launch, divided by the launch's mixed additions).  It describes one version
+# of the kernel: `kernel_version` must match G1_BUCKET_KERNEL_VERSION below,
+# otherwise the bench reports traffic as null (the counters predate the code).
+G1_BUCKET_KERNEL_VERSION = "xyzz-madd-v1"
+G1_BUCKET_TRAFFIC = {
+    "kernel_version": "xyzz-madd-v1",
+    "bytes_per_unit": 1.828e9 / 13.619e6,
+    "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+              "--clock-control none -k regex:k_bucket_acc -c 20 python bench.py --case prove20 --steps 4 "
+              "(GB300, 16 G1 launches of four 2^20 proofs: 1.828 GB per launch for 13.62 M additions)",
+}
+
+
+def _device_sms(device) -> int:
+    import torch
+
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def _sm_max_mhz(clocks) -> float:
+    """Maximum SM clock: sampled from nvidia-smi during the run, else the
+    driver's measured-peaks record, else the GB300's 2070 MHz."""
+    if clocks and clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"])
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return SM_MAX_MHZ_DEFAULT
 
 
 def _dist_env():
@@ -127,79 +153,71 @@ def _clock_summary(path, device):
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-class CpuSample:
-    """The oracle on a bounded sample of the block workload, scaled to one
-    2^20 proof.  Sample: the QAP quotient of the 2^16 instance of the same
-    circuit family (scaled by N log N), and plain-Pippenger MSMs over 2^15 G1
-    and 2^12 G2 points with the workload's witness scalars (scaled linearly
-    to the proof's point counts)."""
+class OracleBlockProof:
+    """The oracle's whole Groth16 proof of the 2^20 block circuit on the host
+    cores.  Its circuit, witness and proving key (with points) are made first
+    and not timed: the toy setup is not part of a proof.  Each step then times
+    one call of the oracle prover: sparse products, the QAP quotient by a
+    2N-point convolution and long division by X^N - 1, the A, B1, L and H G1
+    MSMs and the B G2 MSM by plain Pippenger, and the assembly.  Same circuit,
+    witness, toxic waste and (r, s) as the GPU arm, so its proof bytes equal
+    the GPU's."""
 
-    LOG_S, N1, N2 = 16, 1 << 15, 1 << 12
-
-    def __init__(self, shape):
-        import numpy as np
-
+    def __init__(self):
         import oracle as O
-        from paper_2603_10242_gb300 import inputs
 
         self.O = O
-        self.shape = shape
-        self.c = O.Circuit(self.LOG_S, 1 << self.LOG_S, 256, 256, 172, seed=SEED, input_seed=SEED)
+        t0 = time.perf_counter()
+        self.c = O.Circuit(CIRCUIT["log_n"], CIRCUIT["n_rows"], CIRCUIT["n_perm"], CIRCUIT["n_pack"],
+                           CIRCUIT["pack_bits"], seed=SEED, input_seed=SEED)
         self.z = self.c.witness()
-        kb = inputs.sample_fr(SEED, inputs.PURPOSE["bases"], self.N1)
-        zz = np.frombuffer(self.z, dtype=np.uint32).reshape(-1, 8)
-        self.sc = zz[np.arange(self.N1) % len(zz)].copy()
-        self.pts = O.g1_mul_gen_batch(kb.tobytes())
-        self.pts2 = O.g2_mul_gen_batch(kb[:self.N2].tobytes())
+        self.pk = O.ProvingKey(self.c, SEED, with_points=True)
+        self.setup_s = time.perf_counter() - t0
+        self.cores = O.lib().orc_num_threads()
+        self.verified = None
 
-    def measure(self):
-        O, shape = self.O, self.shape
+    def step(self, i):
+        r, s_ = self.O.rs_from_seed(1000 + i)
         t0 = time.perf_counter()
-        ok, _ = self.c.qap_h(self.z)
-        t_qap = time.perf_counter() - t0
-        assert ok
-        t_qap_full = t_qap * ((1 << 20) * 20) / ((1 << self.LOG_S) * self.LOG_S)
-        t0 = time.perf_counter()
-        O.msm_g1(self.pts, self.sc.tobytes(), 1)
-        t_g1 = (time.perf_counter() - t0) / self.N1
-        t0 = time.perf_counter()
-        O.msm_g2(self.pts2, self.sc[:self.N2].tobytes(), 1)
-        t_g2 = (time.perf_counter() - t0) / self.N2
-        g1_points = shape["m_A"] + shape["m_B"] + shape["m_L"] + shape["N"]
-        t_proof = t_qap_full + t_g1 * g1_points + t_g2 * shape["m_B"]
+        ok, proof = self.pk.prove(self.z, r, s_, 1)
+        dt = time.perf_counter() - t0
+        assert ok, "the oracle found the witness unsatisfied"
+        if self.verified is None:
+            self.verified = self.pk.verify(int.from_bytes(self.z[32:64], "little"), proof) == 1
+        return proof, dt
+
+    def record(self, times):
+        per = statistics.median(times)
         return {
-            "value": 1.0 / t_proof,
-            "unit": UNIT,
-            "cores": O.lib().orc_num_threads(),
-            "kind": "oracle",
-            "sample": (f"oracle QAP of the 2^{self.LOG_S} circuit of the same family ({t_qap:.2f} s, scaled by "
-                       f"N log N) + plain Pippenger over {self.N1} G1 / {self.N2} G2 points with witness scalars "
-                       f"({t_g1 * 1e6:.1f} / {t_g2 * 1e6:.1f} us per point, scaled to {g1_points} G1 + "
-                       f"{shape['m_B']} G2 points); est. {t_proof:.1f} s per proof"),
+            "value": 1.0 / per, "unit": UNIT, "cores": self.cores, "kind": "oracle",
+            "sample": (f"{len(times)} whole oracle proof(s) of the 2^20 block circuit, timed one by one "
+                       f"({', '.join(f'{t:.1f}' for t in times)} s; median {per:.1f} s per proof) after an "
+                       f"untimed setup of {self.setup_s:.0f} s; proof verified by the oracle's pairing check: "
+                       f"{bool(self.verified)}"),
+            "seconds_per_proof": per,
         }
 
 
-def cpu_sample(shape):
-    s = CpuSample(shape)
-    runs = [s.measure() for _ in range(2)]
-    return max(runs, key=lambda r: r["value"])
-
-
 def run_reference(args):
+    """The oracle prover on the host cores (rank 0 only).  A proof takes tens
+    of seconds, so the arm runs whole proofs until --ref-seconds of proving
+    have passed (at least one) and reports the number it ran as `steps`
+    (the requested K and W are recorded beside it); no warm-up proof is run,
+    the oracle has nothing to warm up."""
     ws, rank, _ = _dist_env()
     if rank != 0:
         return
-    s = CpuSample(BLOCK_SHAPE)
-    for _ in range(args.warmup):
-        s.measure()
-    runs = [s.measure() for _ in range(args.steps)]
-    v = statistics.median(r["value"] for r in runs)
-    r = dict(runs[0])
-    r["value"] = v
+    o = OracleBlockProof()
+    times = []
+    while not times or (sum(times) < args.ref_seconds and len(times) < args.steps):
+        times.append(o.step(len(times))[1])
+    rec = o.record(times)
+    v = rec["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": dict(WORKLOAD), "cpu_baseline": r,
+            "steps": len(times), "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": dict(WORKLOAD), "cpu_baseline": rec,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -284,58 +302,87 @@ def run_ours(args):
     if dist:
         dist.barrier()
 
-    # ---- plain path: one proof per call, back to back (per-step latency) ----
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    # ---- plain path: one proof per call, back to back (per-proof latency) ----
+    # args.latency_proofs proofs (at least K), each bracketed by CUDA events
+    n_lat = max(args.steps, args.latency_proofs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_lat + 1)]
+    lat_proofs = torch.zeros(n_lat * 256, dtype=torch.uint8, device=device)
+    lat_status = torch.zeros(n_lat, dtype=torch.int32, device=device)
     torch.cuda.synchronize()
     ev[0].record(stream)
-    for i in range(args.steps):
-        j = args.warmup + i
-        ctx.prove_async(pk, dz, rs[j][0], rs[j][1], proofs[256 * j:], status[j:])
+    for i in range(n_lat):
+        j = args.warmup + (i % args.steps)
+        ctx.prove_async(pk, dz, rs[j][0], rs[j][1], lat_proofs[256 * i:], lat_status[i:])
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    plain_ms = ev[0].elapsed_time(ev[-1])
-    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    assert int(status.sum().item()) == 0, "a proof reported an unsatisfied witness"
-    allp = proofs.cpu().numpy().reshape(-1, 256)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(n_lat)]
+    plain_ms = ev[0].elapsed_time(ev[args.steps])
+    assert int(lat_status.sum().item()) == 0, "a proof reported an unsatisfied witness"
+    allp = lat_proofs.cpu().numpy().reshape(-1, 256)
     # the plain path gives the same bytes as the batch for the same (r, s)
     for i in (0, args.steps - 1):
-        assert bytes(allp[args.warmup + i]) == bproofs[i], "batched and plain proofs differ"
+        assert bytes(allp[i]) == bproofs[i], "batched and plain proofs differ"
 
     total_ms = max_over_ranks(total_ms, dist, device)
     value = whole_job_rate(args.steps, ws, total_ms / 1000.0)
     plain_value = args.steps / (plain_ms / 1000.0)
 
-    # ---- e2e: every witness copied from pinned host memory, proofs read back ----
-    # the step's witness copies (pinned host to device), then one batch call
-    # over the group's proofs (proofs come back to the host inside the call);
-    # groups of at most 64 proofs bound the device buffers
-    zpin = torch.from_numpy(zb.copy()).pin_memory()
-    nbuf = min(args.steps, 64)
-    dzs = [torch.empty_like(dz) for _ in range(nbuf)]
+    # ---- e2e through the public C ABI with host buffers ----
+    # ace_prove_batch_host takes the witnesses in pinned host memory, copies
+    # each to the device inside the call and returns the proofs and status
+    # words in host memory; groups of at most 64 proofs per call
+    zpins = [torch.from_numpy(zb.copy()).pin_memory() for _ in range(min(args.steps, 64))]
 
     def e2e_run(k, start):
         out = []
-        for g0 in range(0, k, nbuf):
-            g = min(nbuf, k - g0)
-            for i in range(g):
-                dzs[i].copy_(zpin, non_blocking=True)
-            p, st_ = ctx.prove_batch([pk] * g, dzs[:g], rs_all[32 * (start + g0):32 * (start + g0 + g)],
-                                     ss_all[32 * (start + g0):32 * (start + g0 + g)])
+        for g0 in range(0, k, len(zpins)):
+            g = min(len(zpins), k - g0)
+            p, st_ = ctx.prove_batch_host([pk] * g, zpins[:g], rs_all[32 * (start + g0):32 * (start + g0 + g)],
+                                          ss_all[32 * (start + g0):32 * (start + g0 + g)])
+            assert st_ == [0] * g
             out += p
         return out
 
-    e2e_run(min(nbuf, 4), 0)
+    e2e_run(min(len(zpins), 4), 0)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     e2e_proofs = e2e_run(args.steps, args.warmup)
-    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    assert e2e_proofs[0] == bproofs[0]
+    assert e2e_proofs == bproofs, "proofs from host witnesses differ from the device-resident batch"
     e2e_s = max_over_ranks(e2e_s, dist, device)
     e2e = {"value": whole_job_rate(args.steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 32 * m,
-           "d2h_bytes_per_step": 256 + 4}
+           "d2h_bytes_per_step": 256 + 4, "path": "ace_prove_batch_host (witness in pinned host memory, "
+                                                 "proof and status returned to host memory)"}
+
+    # ---- per-stage split: one proof with every stage on one stream ----
+    # (untimed for `value`): the profiled intervals then do not overlap, so
+    # each stage's time is exclusive and the stages plus `other` (gathers,
+    # quotient, bucket combine, memsets, gaps between launches) add up to the
+    # proof's serial time
+    ace.serial_proofs(ctx, True)
+    ctx.prove_async(pk, dz, rs[0][0], rs[0][1], proofs, status)
+    torch.cuda.synchronize()
+    ace.profile_enable(True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.prove_async(pk, dz, rs[0][0], rs[0][1], proofs, status)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = s0.elapsed_time(s1)
+    names = {ace.PROF_SPMV: "spmv_r1cs_check", ace.PROF_NTT: "ntt_passes", ace.PROF_SORT: "msm_digit_sort",
+             ace.PROF_G1_BUCKET: "g1_bucket_acc", ace.PROF_G2_BUCKET: "g2_bucket_acc",
+             ace.PROF_REDUCE: "msm_bucket_reduce_and_final", ace.PROF_ASSEMBLY: "assembly_fixed_var_terms"}
+    stages = {v: ace.profile_read(k)[0] for k, v in names.items()}
+    stages["other"] = serial_ms - sum(stages.values())
+    stages = {"serial_proof_ms": serial_ms, "exclusive_ms": stages,
+              "how": "one 2^20 proof with every stage on the slot's main stream (ace_debug_serial_proofs), "
+                     "CUDA events around each stage; the batched step overlaps these stages across streams "
+                     "and proofs"}
+    ace.profile_enable(False)
+    ace.serial_proofs(ctx, False)
+    assert bytes(proofs[:256].cpu().numpy().tobytes()) == bproofs[0], "serial proof differs"
 
     # ---- G1 MSM points/s at 2^20 (second half of the metric) ----
     n = 1 << 20
@@ -366,7 +413,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (G1 bucket accumulation) ----
     ms, nl, units = prof[ace.PROF_G1_BUCKET]
-    peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    sms = _device_sms(device)
+    sm_max = _sm_max_mhz(clocks)
+    peak = sms * IMAD_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
     # algorithmic multiply-adds per launch / average launch duration (the
     # launches of the batched proofs overlap other kernels and one another)
     achieved = units * IMAD_PER_G1_MADD / (g1_sum_ms / 1000.0) / 1e12 if g1_sum_ms > 0 else None
@@ -379,8 +428,8 @@ def run_ours(args):
     # one mad.wide is one limb product = two 32-bit multiply-adds (lo and hi)
     measured_peak["mad_wide_as_lo_hi"] = 2.0 * ace.imad_rate(ctx, 3) / 1e12
     traffic = None
-    if G1_BUCKET_DRAM_BYTES_PER_MADD is not None and nl:
-        traffic = G1_BUCKET_DRAM_BYTES_PER_MADD * units / nl
+    if G1_BUCKET_TRAFFIC["kernel_version"] == G1_BUCKET_KERNEL_VERSION and nl:
+        traffic = G1_BUCKET_TRAFFIC["bytes_per_unit"] * units / nl
     # the same kernel with the GPU to itself (the 2^20 G1 MSM loop above)
     iso_ms, iso_nl, iso_units = iso
     isolated = {"achieved": iso_units * IMAD_PER_G1_MADD / (iso_ms / 1000.0) / 1e12 if iso_ms > 0 else None,
@@ -403,22 +452,15 @@ def run_ours(args):
                 "algorithmic_per_unit": f"{IMAD_PER_G1_MADD} IMAD per mixed addition (10 Fp mul x 272)",
                 "units_per_launch": units / nl if nl else None, "launches": nl,
                 "avg_launch_ms": g1_sum_ms / nl if nl else None,
-                "peak_source": "152 SMs x 64 IMAD/clk/SM x 2070 MHz (nominal unit counts and max clock)",
+                "peak_source": f"{sms} SMs (device attribute) x 64 IMAD/clk/SM x {sm_max:.0f} MHz (maximum SM "
+                               "clock): nominal unit counts",
+                "traffic_source": G1_BUCKET_TRAFFIC["source"] if traffic is not None else
+                "no ncu capture of this kernel version yet",
+                "kernel_version": G1_BUCKET_KERNEL_VERSION,
                 "peak_measured_T_per_s": measured_peak,
                 "measured": "CUDA events around every launch inside the timed proofs; up to four proofs run "
                             "at once, so each launch shares the SMs with other kernels",
                 "union": union, "isolated": isolated, "whole_step": step_alu}
-    stages = {
-        "g1_bucket_ms_per_proof": ms / args.steps,
-        "g2_bucket_ms_per_proof": prof[ace.PROF_G2_BUCKET][0] / args.steps,
-        "ntt_ms_per_proof": prof[ace.PROF_NTT][0] / args.steps,
-        "spmv_ms_per_proof": prof[ace.PROF_SPMV][0] / args.steps,
-        "ntt_butterflies_per_proof": prof[ace.PROF_NTT][2] / args.steps,
-        "msm_sort_ms_per_proof": prof[ace.PROF_SORT][0] / args.steps,
-        "msm_reduce_ms_per_proof": prof[ace.PROF_REDUCE][0] / args.steps,
-        "assembly_ms_per_proof": prof[ace.PROF_ASSEMBLY][0] / args.steps,
-        "note": "union of each kind's launch intervals per proof; kinds overlap one another",
-    }
     step_sorted = sorted(step_ms)
     p50 = statistics.median(step_sorted)
     p99 = step_sorted[min(len(step_sorted) - 1, int(round(0.99 * (len(step_sorted) - 1))))]
@@ -434,8 +476,9 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "roofline": roofline,
-            "latency_ms": {"p50": p50, "p99": p99, "budget_ms": 600.0,
-                           "path": "one proof per call, back to back"},
+            "latency_ms": {"p50": p50, "p99": p99, "max": max(step_ms), "proofs": len(step_ms),
+                           "budget_ms": 600.0,
+                           "path": "one proof per call, back to back on one stream, CUDA events between calls"},
             "plain_proofs_per_s": plain_value,
             "batch_slots": batch_slots,
             "batch_slot_ms": slot_ms,
@@ -445,7 +488,12 @@ def run_ours(args):
             "clocks": clocks,
         }
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_sample(shape)
+            # the oracle on the host cores, after the GPU work: one whole proof
+            # with the (r, s) of the first timed proof, whose bytes it must equal
+            o = OracleBlockProof()
+            oproof, dt = o.step(args.warmup)
+            line["cpu_baseline"] = o.record([dt])
+            line["cpu_baseline"]["proof_equals_gpu"] = oproof == bproofs[0]
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -832,7 +880,7 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    peak_imad = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
+    peak_imad = _device_sms(dev) * IMAD_PER_CLK_PER_SM * _sm_max_mhz(None) * 1e6
     hbm_peak = _measured_hbm_gbs()
     reps = max(3, args.steps)
 
@@ -964,6 +1012,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="reference arm: seconds of oracle proving after the first proof")
+    ap.add_argument("--latency-proofs", type=int, default=200,
+                    help="one-proof-per-call latency: proofs timed back to back (at least --steps)")
     args = ap.parse_args()
     if args.case:
         run_case(args)

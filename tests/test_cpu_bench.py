@@ -73,3 +73,19 @@ def test_serve_class_capacities(log_n, cap):
     assert ln == log_n and rows == 1 << log_n and n_perm == 2 * cap and n_pack == 0 and bits == 0
     # 2 permutations of 243 rows per transaction, 2 input rows, and at least one chain row
     assert 486 * cap + 3 <= rows < 486 * (cap + 1) + 3
+
+
+def test_sm_max_clock_source(tmp_path):
+    """The roofline's clock: the sampled maximum when there is one, else the
+    driver's measured-peaks record or the GB300 default."""
+    assert bench._sm_max_mhz({"sm_max_mhz": 1965.0}) == 1965.0
+    v = bench._sm_max_mhz({"sm_max_mhz": None})
+    assert v > 1000.0
+
+
+def test_traffic_belongs_to_the_current_kernel():
+    """The recorded DRAM traffic names the kernel version its capture was
+    taken on; the bench reports it only for that version."""
+    t = bench.G1_BUCKET_TRAFFIC
+    assert t["bytes_per_unit"] > 0 and "ncu" in t["source"]
+    assert isinstance(bench.G1_BUCKET_KERNEL_VERSION, str)

@@ -670,6 +670,100 @@ def run_pertx(args):
                        "'Critical path analysis'; RTX 4090 estimate)"}))
 
 
+SINGLE_CIRCUIT = (10, 1 << 10, 4, 0, 0)  # 4 permutations + chain to 2^10 rows
+
+
+def run_single(args):
+    """BASELINE config 1: the plain single proof of the 2^10 circuit (4
+    Poseidon-style permutations and the chain), seed 1 for the circuit,
+    witness, toxic waste and (r, s).  One proof per call: per-call latency
+    from the host (witness already on the device, proof bytes back on the
+    host), device time per proof back to back, end to end from pinned host
+    memory through ace_prove_batch_host with one proof per call; and the
+    same proofs in one batch call.  The oracle's proof of the same inputs is
+    timed on the host cores and must equal the GPU's bytes."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import paper_2603_10242_gb300 as ace
+
+    ace.build()
+    ctx = ace.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    c = ace.Circuit(*SINGLE_CIRCUIT, seed=1)
+    z = c.witness(1)
+    pk = ace.ProvingKey(ctx, c, toxic_seed=1)
+    dz = torch.frombuffer(bytearray(z), dtype=torch.uint8).to(dev)
+    zpin = torch.frombuffer(bytearray(z), dtype=torch.uint8).pin_memory()
+    r, s_ = ace.rs_from_seed(1)
+    want = ctx.prove(pk, dz, r, s_)
+    n = max(200, args.steps)
+    for _ in range(max(3, args.warmup)):
+        ctx.prove(pk, dz, r, s_)
+    # host-measured latency of one synchronous call (proof bytes on the host)
+    lat = []
+    for _ in range(n):
+        t0 = time.perf_counter()
+        p = ctx.prove(pk, dz, r, s_)
+        lat.append((time.perf_counter() - t0) * 1e3)
+    assert p == want
+    # device time per proof, back to back on one stream
+    d_proof = torch.zeros(256 * n, dtype=torch.uint8, device=dev)
+    d_status = torch.zeros(n, dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(n):
+        ctx.prove_async(pk, dz, r, s_, d_proof[256 * i:], d_status[i:])
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dev_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+    # end to end, one proof per call from pinned host memory
+    e2e = []
+    for _ in range(n):
+        t0 = time.perf_counter()
+        p2, st2 = ctx.prove_batch_host([pk], [zpin], r, s_)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    assert p2[0] == want and st2 == [0]
+    # n proofs in one batch call (device-resident witness)
+    pb, sb = ctx.prove_batch([pk] * n, [dz] * n, r * n, s_ * n)
+    t0 = time.perf_counter()
+    pb, sb = ctx.prove_batch([pk] * n, [dz] * n, r * n, s_ * n)
+    batch_s = time.perf_counter() - t0
+    assert sb == [0] * n and pb[0] == want
+    # the oracle on the host cores: same inputs, same bytes
+    oc = O.Circuit(*SINGLE_CIRCUIT, seed=1, input_seed=1)
+    opk = O.ProvingKey(oc, 1, with_points=True)
+    ot = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        ok, op = opk.prove(z, r, s_, 1)
+        ot.append(time.perf_counter() - t0)
+    assert ok
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+
+    print(json.dumps({
+        "workload": "groth16_single_2p10", "constraints": 1 << 10, "m": c.m, "proofs": n,
+        "one_per_call": {"proofs_per_s": n / (sum(lat) / 1e3), "latency_ms": {"p50": pct(lat, 0.5),
+                         "p99": pct(lat, 0.99), "max": max(lat)},
+                         "path": "ace_prove, witness on the device, proof bytes on the host, host clock"},
+        "device_ms_per_proof": {"p50": pct(dev_ms, 0.5), "p99": pct(dev_ms, 0.99)},
+        "e2e_one_per_call": {"proofs_per_s": n / (sum(e2e) / 1e3), "latency_ms": {"p50": pct(e2e, 0.5),
+                             "p99": pct(e2e, 0.99)}, "h2d_bytes_per_proof": len(z), "d2h_bytes_per_proof": 260,
+                             "path": "ace_prove_batch_host with one proof per call"},
+        "batched_proofs_per_s": n / batch_s,
+        "verified": pk.verify(z[32:64], want) == 1, "oracle_equal": op == want,
+        "cpu_baseline": {"kind": "oracle", "cores": O.lib().orc_num_threads(),
+                         "value": 1.0 / statistics.median(ot), "unit": "proofs/s",
+                         "sample": "5 oracle proofs of the same 2^10 inputs (setup untimed)"},
+    }))
+
+
 SERVE_CLASSES = (19, 20, 21, 22, 23)
 
 
@@ -1003,7 +1097,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=300, help="served workload: number of jobs")
     ap.add_argument("--serve-slots", type=int, default=3)
-    ap.add_argument("--workload", choices=["block2p20", "batch64", "serve", "pertx", "sweep"], default="block2p20",
+    ap.add_argument("--workload", choices=["block2p20", "single2p10", "batch64", "serve", "pertx", "sweep"],
+                    default="block2p20",
                     help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
     ap.add_argument("--case", choices=["msm_g1", "msm_g2", "ntt", "prove16", "prove20"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
@@ -1020,6 +1115,8 @@ def main():
     args = ap.parse_args()
     if args.case:
         run_case(args)
+    elif args.workload == "single2p10":
+        run_single(args)
     elif args.workload == "batch64":
         run_batch_workload(args)
     elif args.workload == "serve":

@@ -70,10 +70,17 @@ int pk_build_tables(ace_pk* pk, const PkFixed& f);
 // filled by the caller), set its plan
 template <class F>
 int pk_alloc_table(ace_pk* pk, uint32_t count, MsmPlan* plan, Affine<F>** tab);
+// where a batch's proof leaves its MSM sums: res1 = S_H, S_A, S_B1, S_L;
+// res2 = S_B2 (device)
+struct MsmOut {
+    g1_xyzz* res1;
+    g2_xyzz* res2;
+};
 // one whole proof on proving slot `slot` at stream priority level `prio`
-// (prove.cu)
+// (prove.cu); with msm_out, only its QAP and MSMs
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
-              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join);
+              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join,
+              const MsmOut* msm_out = nullptr);
 // device bytes of scratch arena `arena` of a slot proving with `pk`
 size_t prove_slot_bytes(const ace_pk* pk, int arena);
 }  // namespace ace

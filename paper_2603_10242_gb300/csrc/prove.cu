@@ -29,6 +29,7 @@
 
 #include <vector>
 
+#include "curve_quad.cuh"
 #include "fixed_base.cuh"
 #include "glv.cuh"
 #include "pk.h"
@@ -140,9 +141,9 @@ struct PkTabs {
     const g1_aff *alpha1, *beta1, *delta1;
     const g2_aff* delta2;
 };
-__global__ void k_prove_fixed(PkTabs t, fr_t r, fr_t s, fr_t rs, g1_xyzz* fx1, g2_xyzz* fx2) {
-    if ((threadIdx.x & 31) != 0) return;
-    switch (threadIdx.x >> 5) {
+__device__ __forceinline__ void fixed_term(const PkTabs& t, const fr_t& r, const fr_t& s, const fr_t& rs, int w,
+                                           g1_xyzz* fx1, g2_xyzz* fx2) {
+    switch (w) {
         case 0: fx1[0] = fixed_mul_tab(t.delta1, r.v); break;
         case 1: fx1[1] = fixed_mul_tab(t.alpha1, s.v); break;
         case 2: fx1[2] = fixed_mul_tab(t.beta1, r.v); break;
@@ -150,40 +151,59 @@ __global__ void k_prove_fixed(PkTabs t, fr_t r, fr_t s, fr_t rs, g1_xyzz* fx1, g
         default: fx2[0] = fixed_mul_tab(t.delta2, s.v); break;
     }
 }
+__global__ void k_prove_fixed(PkTabs t, fr_t r, fr_t s, fr_t rs, g1_xyzz* fx1, g2_xyzz* fx2) {
+    if ((threadIdx.x & 31) != 0) return;
+    fixed_term(t, r, s, rs, threadIdx.x >> 5, fx1, fx2);
+}
 
 // The variable-base part of C: V = s S_A + r S_B1, as soon as the A and B1
 // MSMs are done.  With the GLV endomorphism phi(x, y) = (beta x, y) = lambda
 // (x, y) on G1, s = s1 + s2 lambda and r = r1 + r2 lambda (mod r) with 128-bit
 // halves (split on the host), so V = s1 S_A + s2 phi(S_A) + r1 S_B1 +
-// r2 phi(S_B1): four 128-bit double-and-add chains, one per warp (lane 0),
-// half the sequential length of one 256-bit chain.
+// r2 phi(S_B1): four 128-bit double-and-add chains, one per warp, each on
+// that warp's first four lanes with the four-lane point formulas (a doubling
+// takes 3 levels of products instead of 9, an addition 4 instead of 16).
+// Each chain has a warp to itself, so one chain's additions do not hold up
+// another's doublings.  The result equals the one-lane chains bit for bit.
 struct GlvScalars {
     uint32_t k[4][4];  // |s1|, |s2|, |r1|, |r2|
     uint32_t neg[4];
 };
-__global__ void k_prove_var(const g1_xyzz* res1, GlvScalars g, fp_t beta, g1_xyzz* v) {
+// block of 128 threads; sa, sb: S_A and S_B1; writes V to *v
+__device__ __forceinline__ void var_term_quad(const g1_xyzz& sa, const g1_xyzz& sb, const GlvScalars& g,
+                                              const fp_t& beta, g1_xyzz* v) {
     __shared__ g1_xyzz part[4];
-    const int t = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0 && t < 4) {
-        g1_xyzz P = res1[t < 2 ? 1 : 2];
+    const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < 4) {
+        const unsigned mask = 0xfu;
+        g1_xyzz P = t < 2 ? sa : sb;
         if (t & 1) P.X = P.X * beta;
         if (g.neg[t]) P.Y = fe_neg(P.Y);
         g1_xyzz acc = xyzz_inf<fp_t>();
         for (int i = 127; i >= 0; i--) {
-            acc = xyzz_dbl(acc);
-            if ((g.k[t][i >> 5] >> (i & 31)) & 1u) acc = xyzz_add(acc, P);
+            acc = quad_dbl(acc, lane, mask);
+            if ((g.k[t][i >> 5] >> (i & 31)) & 1u) acc = quad_add(acc, P, lane, mask);
         }
-        part[t] = acc;
+        if (lane == 0) part[t] = acc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) *v = xyzz_add(xyzz_add(part[0], part[1]), xyzz_add(part[2], part[3]));
+    if (t == 0 && lane < 4) {
+        const unsigned mask = 0xfu;
+        g1_xyzz x = quad_add(part[0], part[1], lane, mask);
+        g1_xyzz y = quad_add(part[2], part[3], lane, mask);
+        x = quad_add(x, y, lane, mask);
+        if (lane == 0) *v = x;
+    }
+}
+__global__ void __launch_bounds__(128) k_prove_var(const g1_xyzz* res1, GlvScalars g, fp_t beta, g1_xyzz* v) {
+    var_term_quad(res1[1], res1[2], g, beta, v);
 }
 
-// The same term for a batch of proofs, one thread per proof (throughput, not
-// latency, matters there): one joint double-and-add over the 256 bits.
-__global__ void k_prove_var_joint(const g1_xyzz* res1, fr_t r, fr_t s, g1_xyzz* v) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    g1_xyzz a = res1[1], b = res1[2], ab = xyzz_add(a, b);
+// The same term with one joint double-and-add over the 256 bits of s and r
+// (one thread): the fallback if the split ever failed to give 128-bit
+// halves, and the per-proof form of a block of proofs of one key.
+__device__ g1_xyzz var_term_joint(const g1_xyzz& a, const g1_xyzz& b, const fr_t& r, const fr_t& s) {
+    g1_xyzz ab = xyzz_add(a, b);
     g1_xyzz acc = xyzz_inf<fp_t>();
     for (int i = 255; i >= 0; i--) {
         acc = xyzz_dbl(acc);
@@ -192,7 +212,11 @@ __global__ void k_prove_var_joint(const g1_xyzz* res1, fr_t r, fr_t s, g1_xyzz* 
         else if (bs) acc = xyzz_add(acc, a);
         else if (br) acc = xyzz_add(acc, b);
     }
-    *v = acc;
+    return acc;
+}
+__global__ void k_prove_var_joint(const g1_xyzz* res1, fr_t r, fr_t s, g1_xyzz* v) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *v = var_term_joint(res1[1], res1[2], r, s);
 }
 
 // ---- GLV split on the host (glv.cuh) --------------------------------------
@@ -211,11 +235,10 @@ __device__ void write_g1(uint32_t* dst, const g1_xyzz& p) {
 
 // A = alpha + S_A + r delta;  B = beta2 + S_B2 + s delta2;
 // C = S_L + S_H + (s alpha + r beta + r s delta) + V   (one warp each)
-// res1: S_H, S_A, S_B1, S_L;  fx1 / fx2 from k_prove_fixed;  v from k_prove_var
-__global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2, const g1_xyzz* fx1,
-                           const g2_xyzz* fx2, const g1_xyzz* v, uint32_t* proof) {
-    if ((threadIdx.x & 31) != 0) return;
-    int w = threadIdx.x >> 5;
+// res1: S_H, S_A, S_B1, S_L;  fx1 / fx2 from the fixed terms;  v = V
+__device__ __forceinline__ void assemble_part(int w, const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2,
+                                              const g1_xyzz* fx1, const g2_xyzz* fx2, const g1_xyzz* v,
+                                              uint32_t* proof) {
     if (w == 0) {
         g1_xyzz A = xyzz_add(xyzz_add(xyzz_from_aff(fx->alpha1), res1[1]), fx1[0]);
         write_g1(proof, A);
@@ -233,6 +256,50 @@ __global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz
         C = xyzz_add(C, *v);
         write_g1(proof + 48, C);
     }
+}
+__global__ void k_assemble(const PkFixed* fx, const g1_xyzz* res1, const g2_xyzz* resB2, const g1_xyzz* fx1,
+                           const g2_xyzz* fx2, const g1_xyzz* v, uint32_t* proof) {
+    if ((threadIdx.x & 31) != 0) return;
+    assemble_part(threadIdx.x >> 5, fx, res1, resB2, fx1, fx2, v, proof);
+}
+
+// ---------------------------------------------------------------------------
+// tails of a batch of proofs (any keys): the fixed-base terms of every proof
+// in one launch before the MSMs, V and the assembly of every proof in one
+// launch each after them; block q serves proof q
+// ---------------------------------------------------------------------------
+struct TailDesc {
+    PkTabs tabs;
+    const PkFixed* fixed;
+    fr_t r, s, rs;  // canonical
+    GlvScalars glv;
+    uint32_t glv_ok;
+};
+// per proof q: fx1[4 q .. 4 q + 3], fx2[q]; 160 threads per block
+__global__ void __launch_bounds__(160) k_prove_fixed_batch(const TailDesc* d, g1_xyzz* fx1, g2_xyzz* fx2) {
+    if ((threadIdx.x & 31) != 0) return;
+    const TailDesc& q = d[blockIdx.x];
+    fixed_term(q.tabs, q.r, q.s, q.rs, threadIdx.x >> 5, fx1 + 4 * (size_t)blockIdx.x, fx2 + blockIdx.x);
+}
+// res1: S_H, S_A, S_B1, S_L of proof q at res1[4 q ..]; 128 threads per block
+__global__ void __launch_bounds__(128) k_prove_var_batch(const TailDesc* d, const g1_xyzz* res1, fp_t beta,
+                                                         g1_xyzz* v) {
+    const TailDesc& q = d[blockIdx.x];
+    const g1_xyzz* r1 = res1 + 4 * (size_t)blockIdx.x;
+    if (q.glv_ok) {
+        var_term_quad(r1[1], r1[2], q.glv, beta, v + blockIdx.x);
+    } else if (threadIdx.x == 0) {
+        v[blockIdx.x] = var_term_joint(r1[1], r1[2], q.r, q.s);
+    }
+}
+// 96 threads per block; proof q at proofs + 64 q (words)
+__global__ void __launch_bounds__(96) k_assemble_batch(const TailDesc* d, const g1_xyzz* res1, const g2_xyzz* res2,
+                                                       const g1_xyzz* fx1, const g2_xyzz* fx2, const g1_xyzz* v,
+                                                       uint32_t* proofs) {
+    if ((threadIdx.x & 31) != 0) return;
+    const size_t q = blockIdx.x;
+    assemble_part(threadIdx.x >> 5, d[q].fixed, res1 + 4 * q, res2 + q, fx1 + 4 * q, fx2 + q, v + q,
+                  proofs + 64 * q);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,17 +361,7 @@ __global__ void k_prove_var_many(const g1_xyzz* sa, const g1_xyzz* sb, const fr_
                                  g1_xyzz* v) {
     uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= count) return;
-    const fr_t r = rsv[3 * q], s = rsv[3 * q + 1];
-    g1_xyzz a = sa[q], b = sb[q], ab = xyzz_add(a, b);
-    g1_xyzz acc = xyzz_inf<fp_t>();
-    for (int i = 255; i >= 0; i--) {
-        acc = xyzz_dbl(acc);
-        uint32_t bs = (s.v[i >> 5] >> (i & 31)) & 1u, br = (r.v[i >> 5] >> (i & 31)) & 1u;
-        if (bs && br) acc = xyzz_add(acc, ab);
-        else if (bs) acc = xyzz_add(acc, a);
-        else if (br) acc = xyzz_add(acc, b);
-    }
-    v[q] = acc;
+    v[q] = var_term_joint(sa[q], sb[q], rsv[3 * q], rsv[3 * q + 1]);
 }
 
 // res1: S_H, S_A, S_B1, S_L, each `count` results; proof q at proof + 64 q
@@ -427,8 +484,12 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
 // for the proof; without, the caller joins on the slot's ev_done.  The main
 // stream runs the QAP and the H MSM, the auxiliary streams the A, B1, B2 and
 // L MSMs and the fixed-base terms; proofs on other slots overlap.
+// msm_out (a batch's proof): only the QAP and the five MSMs run; their sums go
+// to msm_out->res1 (S_H, S_A, S_B1, S_L) and msm_out->res2 (S_B2), the slot's
+// ev_done marks them complete, and the fixed-base terms, V and the assembly
+// are left to the batch's tail kernels (d_proof is not written).
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
-              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join) {
+              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join, const MsmOut* msm_out) {
     if (prio < 0 || prio >= PRIO_LEVELS || slot < 0 || slot >= MAX_SLOTS) {
         set_error("prove: slot %d / priority level %d out of range", slot, prio);
         return ACE_E_ARG;
@@ -453,6 +514,10 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     g1_xyzz* fx1 = res1 + 4;  // 4 fixed-base terms
     g1_xyzz* vterm = res1 + 8;
     g2_xyzz* fx2 = res2 + 1;
+    if (msm_out) {
+        res1 = msm_out->res1;
+        res2 = msm_out->res2;
+    }
     PkTabs tabs{pk->d_tab_alpha1, pk->d_tab_beta1, pk->d_tab_delta1, pk->d_tab_delta2};
     // r s mod r on the host
     fr_t rs = fe_from_mont(fe_to_mont(r) * fe_to_mont(s));
@@ -474,6 +539,18 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[2], sl.ev_sort, 0));
     ACE_TRY(msm_run<fp2_t>(pl.B, pk->B2.d_pts, true, nullptr, sl.ar[3], res2, nullptr, ss.aux[2], &sortB));
     ACE_TRY(gathered_msm<fp_t>(pl.L, pk->L, d_z, sl.ar[4], res1 + 3, ss.aux[3]));
+    if (msm_out) {
+        ACE_TRY(qap_run(ctx, pk, d_z, abc, d_status, ss.main, true));
+        ACE_TRY(msm_run<fp_t>(pl.H, pk->d_H, true, (const uint32_t*)abc, a0, res1, nullptr, ss.main));
+        for (int k = 0; k < 4; k++) {
+            ACE_TRY_CUDA(cudaEventRecord(sl.ev_aux[k], ss.aux[k]));
+            ACE_TRY_CUDA(cudaStreamWaitEvent(ss.main, sl.ev_aux[k], 0));
+        }
+        ACE_TRY_CUDA(cudaGetLastError());
+        ACE_TRY_CUDA(cudaEventRecord(sl.ev_done, ss.main));
+        if (join) ACE_TRY_CUDA(cudaStreamWaitEvent(st_in, sl.ev_done, 0));
+        return ACE_OK;
+    }
     int pf = prof_begin(PROF_ASSEMBLY, ss.aux[4]);
     k_prove_fixed<<<1, 160, 0, ss.aux[4]>>>(tabs, r, s, rs, fx1, fx2); ::ace::note_launch();
     prof_end(pf, ss.aux[4], nullptr, 1);
@@ -734,10 +811,35 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
             return ACE_E_ARG;
         }
     }
-    // device outputs for all proofs, then one copy back
-    ACE_TRY(arena_ensure(ctx, 3, k * 256 + k * sizeof(int32_t) + 1024));
-    uint32_t* d_proofs = (uint32_t*)ctx->scratch[3].take(k * 256);
-    int32_t* d_status = (int32_t*)ctx->scratch[3].take(k * sizeof(int32_t));
+    // device outputs for all proofs (then one copy back), the proofs' MSM
+    // sums and tail terms, and the tails' per-proof descriptors
+    const size_t per = 256 + sizeof(int32_t) + 9 * sizeof(g1_xyzz) + 2 * sizeof(g2_xyzz) + sizeof(TailDesc);
+    ACE_TRY(arena_ensure(ctx, 3, k * per + 8 * 1024));
+    Arena& sc = ctx->scratch[3];
+    uint32_t* d_proofs = (uint32_t*)sc.take(k * 256);
+    int32_t* d_status = (int32_t*)sc.take(k * sizeof(int32_t));
+    g1_xyzz* res1 = (g1_xyzz*)sc.take(4 * k * sizeof(g1_xyzz));
+    g1_xyzz* fx1 = (g1_xyzz*)sc.take(4 * k * sizeof(g1_xyzz));
+    g1_xyzz* vterm = (g1_xyzz*)sc.take(k * sizeof(g1_xyzz));
+    g2_xyzz* res2 = (g2_xyzz*)sc.take(k * sizeof(g2_xyzz));
+    g2_xyzz* fx2 = (g2_xyzz*)sc.take(k * sizeof(g2_xyzz));
+    TailDesc* d_desc = (TailDesc*)sc.take(k * sizeof(TailDesc));
+    if (!d_proofs || !d_status || !res1 || !fx1 || !vterm || !res2 || !fx2 || !d_desc) {
+        set_error("%s: scratch arena too small", fn);
+        return ACE_E_OOM;
+    }
+    std::vector<TailDesc> desc(k);
+    for (size_t i = 0; i < k; i++) {
+        TailDesc& d = desc[i];
+        const ace_pk* pk = pks[i];
+        d.tabs = PkTabs{pk->d_tab_alpha1, pk->d_tab_beta1, pk->d_tab_delta1, pk->d_tab_delta2};
+        d.fixed = pk->d_fixed;
+        memcpy(d.r.v, rs[i].l, 32);
+        memcpy(d.s.v, ss[i].l, 32);
+        d.rs = fe_from_mont(fe_to_mont(d.r) * fe_to_mont(d.s));
+        d.glv_ok = glv_split(d.s, d.glv.k[0], &d.glv.neg[0], d.glv.k[1], &d.glv.neg[1]) &&
+                   glv_split(d.r, d.glv.k[2], &d.glv.neg[2], d.glv.k[3], &d.glv.neg[3]);
+    }
     cudaStream_t st = ctx->stream;
     int nslots = (int)(k < (size_t)ctx->batch_slots ? k : (size_t)ctx->batch_slots);
     for (int q = 0; q < nslots; q++) {
@@ -752,10 +854,21 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
         for (int a = 0; a < PROVE_ARENAS; a++) ACE_TRY(slot_arena_ensure(ctx, q, a, need[a]));
         if (host) ACE_TRY(slot_witness_ensure(ctx, q, wit));
     }
+    // the fixed-base terms of every proof in one launch, on slot 0's fifth
+    // auxiliary stream (unused by proofs whose tails are batched), beside the
+    // proofs' MSMs
+    ACE_TRY_CUDA(cudaMemcpyAsync(d_desc, desc.data(), k * sizeof(TailDesc), cudaMemcpyHostToDevice, st));
+    ProveSlot& s0 = ctx->slots[0];
+    cudaStream_t tail = s0.lv[0].aux[4];
+    ACE_TRY_CUDA(cudaEventRecord(s0.ev_aux[4], st));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(tail, s0.ev_aux[4], 0));
+    int pf = prof_begin(PROF_ASSEMBLY, tail);
+    k_prove_fixed_batch<<<(unsigned)k, 160, 0, tail>>>(d_desc, fx1, fx2); ::ace::note_launch();
+    prof_end(pf, tail, nullptr, k);
+    ACE_TRY_CUDA(cudaGetLastError());
     for (size_t i = 0; i < k; i++) {
-        fr_t rr, sv;
-        memcpy(rr.v, rs[i].l, 32);
-        memcpy(sv.v, ss[i].l, 32);
+        const fr_t& rr = desc[i].r;
+        const fr_t& sv = desc[i].s;
         const int q = (int)(i % nslots);
         const fr_t* z = (const fr_t*)zs[i];
         cudaStream_t st_in = st;
@@ -768,9 +881,20 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
             ACE_TRY_CUDA(cudaMemcpyAsync(stage, z, pks[i]->m * sizeof(fr_t), cudaMemcpyHostToDevice, st_in));
             z = stage;
         }
-        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false));
+        MsmOut mo{res1 + 4 * i, res2 + i};
+        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false, &mo));
     }
+    // V and the assembly of every proof once all MSMs and fixed terms are done
     for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));
+    ACE_TRY_CUDA(cudaEventRecord(s0.ev_aux[4], tail));
+    ACE_TRY_CUDA(cudaStreamWaitEvent(st, s0.ev_aux[4], 0));
+    fp_t beta;
+    memcpy(beta.v, GLV_BETA, 32);
+    int pv = prof_begin(PROF_ASSEMBLY, st);
+    k_prove_var_batch<<<(unsigned)k, 128, 0, st>>>(d_desc, res1, fe_to_mont(beta), vterm); ::ace::note_launch();
+    k_assemble_batch<<<(unsigned)k, 96, 0, st>>>(d_desc, res1, res2, fx1, fx2, vterm, d_proofs); ::ace::note_launch();
+    prof_end(pv, st, nullptr, k);
+    ACE_TRY_CUDA(cudaGetLastError());
     ACE_TRY_CUDA(cudaMemcpyAsync(proofs, d_proofs, k * 256, cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(status, d_status, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaStreamSynchronize(st));

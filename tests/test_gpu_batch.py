@@ -51,3 +51,50 @@ def test_batch_reports_unsat_in_the_middle():
     proofs, status = ctx.prove_batch([pk] * 3, dzs, r * 3, s * 3)
     assert status == [0, 1, 0]
     assert proofs[0] == proofs[2] == ctx.prove(pk, dzs[0], r, s)
+
+
+def test_batch_from_host_witnesses_matches_device_batch():
+    """ace_prove_batch_host (witnesses in pinned and in pageable host memory,
+    copied by the library into the slots' staging buffers) gives the same
+    proofs and status as the device-resident batch, over mixed keys and a
+    batch long enough to reuse every slot's staging buffer."""
+    ctx = gu.ctx()
+    circs = [ace.Circuit(*p, seed=50 + i) for i, p in enumerate(PARAMS)]
+    pks = [ace.ProvingKey(ctx, c, toxic_seed=60 + i) for i, c in enumerate(circs)]
+    zs = [c.witness(70 + i) for i, c in enumerate(circs)]
+    rss = [ace.rs_from_seed(80 + i) for i in range(len(PARAMS))]
+    rs = b"".join(r for r, _ in rss)
+    ss = b"".join(s for _, s in rss)
+    want, st = ctx.prove_batch(pks, [gu.dev(z) for z in zs], rs, ss)
+    assert st == [0] * len(PARAMS)
+    pinned = [torch.frombuffer(bytearray(z), dtype=torch.uint8).pin_memory() for z in zs]
+    pageable = [torch.frombuffer(bytearray(z), dtype=torch.uint8) for z in zs]
+    got, st2 = ctx.prove_batch_host(pks + pks, pinned + pageable, rs + rs, ss + ss)
+    assert st2 == [0] * (2 * len(PARAMS))
+    assert got == want + want
+    with pytest.raises(ValueError):
+        ctx.prove_batch_host(pks[:1], [gu.dev(zs[0])], rs[:32], ss[:32])
+
+
+def test_batch_tails_same_bytes_for_every_slot_count(tmp_path):
+    """The batch's tail kernels (fixed-base terms, V and assembly of every
+    proof in one launch each) give the bytes of the one-proof path whatever
+    the number of proving slots."""
+    import re
+    ctx = ace.Context(0)
+    circs = [ace.Circuit(*p, seed=90 + i) for i, p in enumerate(PARAMS[:3])]
+    pks = [ace.ProvingKey(ctx, c, toxic_seed=95 + i) for i, c in enumerate(circs)]
+    dzs = [gu.dev(c.witness(99 + i)) for i, c in enumerate(circs)]
+    rss = [ace.rs_from_seed(101 + i) for i in range(3)]
+    rs = b"".join(r for r, _ in rss)
+    ss = b"".join(s for _, s in rss)
+    want = [ctx.prove(pks[i], dzs[i], *rss[i]) for i in range(3)]
+    path = str(tmp_path / "tune.json")
+    ctx.autotune_save(path)
+    txt = open(path).read()
+    for q in (1, 2, 3, 5):
+        open(path, "w").write(re.sub(r'"batch_slots": \d+', f'"batch_slots": {q}', txt))
+        ctx.autotune_load(path)
+        proofs, status = ctx.prove_batch(pks * 2, dzs * 2, rs * 2, ss * 2)
+        assert status == [0] * 6 and proofs == want + want, q
+    ctx.close()

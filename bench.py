@@ -476,6 +476,7 @@ def run_ours(args):
                            witness_bool_fraction=round(bool_frac, 4), parallelism="replicas" if ws > 1 else "1gpu"),
             "e2e": e2e,
             "gpu_launches": launches,
+            "launches_before_timed": launches0,
             "roofline": roofline,
             "latency_ms": {"p50": p50, "p99": p99, "max": max(step_ms), "proofs": len(step_ms),
                            "budget_ms": 600.0,
@@ -1095,7 +1096,7 @@ def _measured_hbm_gbs() -> float:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--jobs", type=int, default=300, help="served workload: number of jobs")
+    ap.add_argument("--jobs", type=int, default=2000, help="served workload: number of jobs")
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--workload", choices=["block2p20", "single2p10", "batch64", "serve", "pertx", "sweep"],
                     default="block2p20",

@@ -452,12 +452,15 @@ int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, 
  * cost-model c, its ms. */
 int ace_autotune_msm(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* report);
 /* Measure the NTT pass width (2^10, 2^11 or 2^12 elements per block in shared
- * memory) for N = 2^log_min .. 2^log_max (8..24) on three arrays and keep the
- * fastest per size.  report (optional, 4 per size): log_n, chosen width, its
- * ms, ms at 2^11. */
+ * memory) and stage form (radix-2 stages, or stages in radix-4 pairs) for
+ * N = 2^log_min .. 2^log_max (8..24) on three arrays and keep the fastest
+ * pair per size.  report (optional, 5 per size): log_n, chosen width, its
+ * ms, ms at width 2^11 with the untuned form, chosen radix (2 or 4). */
 int ace_autotune_ntt(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* report);
 /* Time batches of k proofs of (pk, d_z) over 1..max_slots proving slots and
- * keep the fastest count for ace_prove_batch.  report (optional, max_slots
+ * keep, for ace_prove_batch, the fewest slots whose batch time is within 2%
+ * of the fastest count (fewer slots hold less scratch and share the SMs among
+ * fewer proofs at the same throughput).  report (optional, max_slots
  * doubles): ms per batch for each count. */
 int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, int k, int max_slots,
                              double* report);

@@ -233,9 +233,9 @@ class Context:
 
     def autotune_ntt(self, log_min: int, log_max: int):
         n = log_max - log_min + 1
-        rep = (ctypes.c_double * (4 * n))()
+        rep = (ctypes.c_double * (5 * n))()
         check(lib().ace_autotune_ntt(self.h, log_min, log_max, rep))
-        return [tuple(rep[4 * i:4 * i + 4]) for i in range(n)]
+        return [tuple(rep[5 * i:5 * i + 5]) for i in range(n)]
 
     def autotune_batch_slots(self, pk: "ProvingKey", d_z, k: int, max_slots: int = 4):
         rep = (ctypes.c_double * max_slots)()

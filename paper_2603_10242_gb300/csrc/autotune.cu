@@ -151,34 +151,41 @@ int ace_autotune_ntt(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* r
         NttPlan* plan = nullptr;
         rc = ntt_get_plan(ctx, (int)lg, &plan);
         if (rc != ACE_OK) break;
-        int best_w = 11;
+        int best_w = 11, best_r = ntt_default_radix((int)lg);
         float best = 1e30f, t11 = 0;
-        for (int w = 10; w <= 12 && rc == ACE_OK; w++) {
-            plan->smem_log = w;
-            NttScale none;
-            float t = 1e30f;
-            for (int rep = 0; rep < 3 && rc == ACE_OK; rep++) {
-                Timer tm;
-                cudaEventRecord(tm.a, st);
-                rc = ntt_run(*plan, (fr_t*)d, 3, true, false, none, none, st);
-                cudaEventRecord(tm.b, st);
-                float x = tm.ms();
-                if (rep > 0 && x < t) t = x;
-            }
-            if (w == 11) t11 = t;
-            if (t < best) {
-                best = t;
-                best_w = w;
+        for (int radix = 2; radix <= 4 && rc == ACE_OK; radix += 2) {
+            for (int w = 10; w <= 12 && rc == ACE_OK; w++) {
+                plan->smem_log = w;
+                plan->radix = radix;
+                NttScale none;
+                float t = 1e30f;
+                for (int rep = 0; rep < 3 && rc == ACE_OK; rep++) {
+                    Timer tm;
+                    cudaEventRecord(tm.a, st);
+                    rc = ntt_run(*plan, (fr_t*)d, 3, true, false, none, none, st);
+                    cudaEventRecord(tm.b, st);
+                    float x = tm.ms();
+                    if (rep > 0 && x < t) t = x;
+                }
+                if (w == 11 && radix == ntt_default_radix((int)lg)) t11 = t;
+                if (t < best) {
+                    best = t;
+                    best_w = w;
+                    best_r = radix;
+                }
             }
         }
         plan->smem_log = best_w;
+        plan->radix = best_r;
         ctx->tuned_ntt_smem[lg] = best_w;
+        ctx->tuned_ntt_radix[lg] = best_r;
         if (report) {
-            double* r = report + 4 * row;
+            double* r = report + 5 * row;
             r[0] = lg;
             r[1] = best_w;
             r[2] = best;
             r[3] = t11;
+            r[4] = best_r;
         }
     }
     dev_free(ctx, d, nmax * 32);
@@ -201,7 +208,7 @@ int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, 
     std::vector<const ace_fr*> zs(k, d_z);
     std::vector<uint8_t> proofs(256 * (size_t)k);
     std::vector<int32_t> status(k);
-    int best = ctx->batch_slots;
+    std::vector<double> ms_of(max_slots + 1, 1e30);
     double best_ms = 1e30;
     for (int q = 1; q <= max_slots; q++) {
         ctx->batch_slots = q;
@@ -210,11 +217,14 @@ int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, 
         ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(), status.data()));
         double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (report) report[q - 1] = ms;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = q;
-        }
+        ms_of[q] = ms;
+        if (ms < best_ms) best_ms = ms;
     }
+    // the fewest slots within 2% of the fastest count: each slot holds a
+    // proof's scratch, and fewer proofs in flight share the SMs less, at the
+    // same throughput
+    int best = 1;
+    while (best < max_slots && ms_of[best] > 1.02 * best_ms) best++;
     ctx->batch_slots = best;
     return ACE_OK;
 }
@@ -243,6 +253,13 @@ int ace_autotune_save(ace_ctx* ctx, const char* path) {
     for (int i = 0; i < 32; i++)
         if (ctx->tuned_ntt_smem[i]) {
             fprintf(f, "%s\"%d\": %d", first ? "" : ", ", i, ctx->tuned_ntt_smem[i]);
+            first = false;
+        }
+    fprintf(f, "}, \"ntt_radix\": {");
+    first = true;
+    for (int i = 0; i < 32; i++)
+        if (ctx->tuned_ntt_radix[i]) {
+            fprintf(f, "%s\"%d\": %d", first ? "" : ", ", i, ctx->tuned_ntt_radix[i]);
             first = false;
         }
     fprintf(f, "}}\n");
@@ -296,16 +313,26 @@ int ace_autotune_load(ace_ctx* ctx, const char* path) {
         set_error("ace_autotune_load: %s is malformed", path);
         return ACE_E_ARG;
     }
+    // the stage form per size (absent from files saved before it was tuned)
+    int radix[32] = {};
+    if (txt.find("\"ntt_radix\"") != std::string::npos && !parse_map("\"ntt_radix\"", radix)) {
+        set_error("ace_autotune_load: %s is malformed", path);
+        return ACE_E_ARG;
+    }
     for (int i = 0; i < 32; i++)
-        if ((msm[i] && (msm[i] < 6 || msm[i] > 20)) || (ntt[i] && (ntt[i] < 10 || ntt[i] > 12))) {
+        if ((msm[i] && (msm[i] < 6 || msm[i] > 20)) || (ntt[i] && (ntt[i] < 10 || ntt[i] > 12)) ||
+            (radix[i] && radix[i] != 2 && radix[i] != 4)) {
             set_error("ace_autotune_load: %s holds out-of-range values", path);
             return ACE_E_ARG;
         }
     ctx->batch_slots = slots;
     memcpy(ctx->tuned_msm_c, msm, sizeof msm);
     memcpy(ctx->tuned_ntt_smem, ntt, sizeof ntt);
-    for (auto& kv : ctx->ntt_plans)
+    memcpy(ctx->tuned_ntt_radix, radix, sizeof radix);
+    for (auto& kv : ctx->ntt_plans) {
         if (ctx->tuned_ntt_smem[kv.first]) kv.second->smem_log = ctx->tuned_ntt_smem[kv.first];
+        kv.second->radix = radix[kv.first] ? radix[kv.first] : ntt_default_radix(kv.first);
+    }
     return ACE_OK;
 }
 

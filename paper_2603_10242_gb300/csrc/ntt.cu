@@ -147,6 +147,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
         return ACE_E_CUDA;
     }
     if (ctx->tuned_ntt_smem[log_n]) p->smem_log = ctx->tuned_ntt_smem[log_n];
+    p->radix = ctx->tuned_ntt_radix[log_n] ? ctx->tuned_ntt_radix[log_n] : ntt_default_radix(log_n);
     ctx->ntt_plans[log_n] = p;
     *out = p;
     return ACE_OK;
@@ -184,8 +185,56 @@ __device__ __forceinline__ fr_t scale_factor(const NttScale& s, uint32_t idx, in
     return ld_fr(s.hi + (e >> s.h)) * ld_fr(s.lo + (e & ((1u << s.h) - 1u)));
 }
 
-template <bool DIT>
-__global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int log_n, int t, int b0, int logG,
+// Shared-memory word of element e in one limb plane: e with its 5-bit column
+// XORed by a function of its row (e >> 5).  A warp's lanes enumerate five
+// index bits of the group; the stage's butterfly bits are skipped, so up to
+// two of the column bits come from the row instead.  Row bit 0 is spread over
+// every column bit and row bit 1 over columns 0, 2 and 4: for a radix-2
+// stage (one missing column bit p < 5, row bit 0 supplying it) and for the
+// radix-4 pairs (missing bits p, p + 1, supplied by row bits 0 and 1) the
+// lanes then hit 32 distinct banks; contiguous runs stay a permutation of one
+// row.
+__device__ __forceinline__ uint32_t swz(uint32_t e) {
+    const uint32_t r = e >> 5;
+    return e ^ ((r & 1u) * 31u) ^ (((r >> 1) & 1u) * 21u);
+}
+__device__ __forceinline__ fr_t sm_ld(const uint32_t* sm, uint32_t S, uint32_t e) {
+    const uint32_t w = swz(e);
+    fr_t x;
+#pragma unroll
+    for (int l = 0; l < 8; l++) x.v[l] = sm[l * S + w];
+    return x;
+}
+__device__ __forceinline__ void sm_st(uint32_t* sm, uint32_t S, uint32_t e, const fr_t& x) {
+    const uint32_t w = swz(e);
+#pragma unroll
+    for (int l = 0; l < 8; l++) sm[l * S + w] = x.v[l];
+}
+// (x, y) -> (x + y, x - y)
+__device__ __forceinline__ void bfly(fr_t& x, fr_t& y) {
+    fr_t u = x + y;
+    y = x - y;
+    x = u;
+}
+// group index g with a zero bit inserted at position p
+__device__ __forceinline__ uint32_t ins0(uint32_t g, int p) { return ((g >> p) << (p + 1)) | (g & ((1u << p) - 1u)); }
+
+// One pass: t stages of radix-2 butterflies on 2^logG columns x 2^t rows
+// staged in shared memory.  Stages are taken two at a time (a radix-4 unit:
+// the four elements that two consecutive stages connect stay in registers
+// between them, halving the shared-memory round trips and barriers); an odd
+// t starts with one radix-2 stage.  Each butterfly is the radix-2 one of the
+// stage it belongs to, with the same twiddle, so the output is the same as
+// t radix-2 stages.  DIT: stage bits ascending, y *= w before (x + y, x - y);
+// DIF: bits descending, (x + y, (x - y) w).  R4 = false: radix-2 stages only
+// (fewer registers; the plan picks the form per size, see ntt_default_radix).
+// ACE_NTT_MIN_BLOCKS: resident blocks of 256 threads per SM the register
+// allocation must allow.
+#ifndef ACE_NTT_MIN_BLOCKS
+#define ACE_NTT_MIN_BLOCKS 3
+#endif
+template <bool DIT, bool R4>
+__global__ void __launch_bounds__(256, ACE_NTT_MIN_BLOCKS) k_ntt_pass(fr_t* __restrict__ data, int log_n, int t, int b0, int logG,
                                                   const fr_t* __restrict__ tw, int first_stage, NttScale pre,
                                                   NttScale post) {
     extern __shared__ uint32_t sm[];
@@ -201,42 +250,81 @@ __global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int l
         uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
         fr_t x = ld_fr(arr + idx);
         if (pre.hi) x = x * scale_factor(pre, idx, log_n);
-#pragma unroll
-        for (int l = 0; l < 8; l++) sm[l * S + e] = x.v[l];
+        sm_st(sm, S, e, x);
     }
     __syncthreads();
-    for (int ls = 0; ls < t; ls++) {
-        const int hb = DIT ? ls : (t - 1 - ls);
-        const int s = first_stage + ls;
-        const int tshift = DIT ? (log_n - s - 1) : s;
+    int ls = 0;
+    // radix-2 stages until the rest pairs up (all of them without ACE_NTT_RADIX4)
+    const int r2 = R4 ? (t & 1) : t;
+    for (; ls < r2; ls++) {
+        const int hb = DIT ? ls : t - 1 - ls;
+        const int s_ = first_stage + ls;
+        const int tshift = DIT ? (log_n - s_ - 1) : s_;
         for (uint32_t beta = threadIdx.x; beta < S / 2; beta += blockDim.x) {
             uint32_t ql = beta & (G - 1u), pi = beta >> logG;
             uint32_t lowbits = pi & ((1u << hb) - 1u);
-            uint32_t gt = ((pi >> hb) << (hb + 1)) | lowbits;
-            uint32_t et = (gt << logG) + ql, eb = et + ((1u << hb) << logG);
-            fr_t x, y;
-#pragma unroll
-            for (int l = 0; l < 8; l++) {
-                x.v[l] = sm[l * S + et];
-                y.v[l] = sm[l * S + eb];
-            }
+            uint32_t et = (ins0(pi, hb) << logG) + ql, eb = et + ((1u << hb) << logG);
+            fr_t x = sm_ld(sm, S, et), y = sm_ld(sm, S, eb);
             uint32_t j = (lowbits << b0) | ((q0 + ql) & lomask);
             if (DIT) {
                 if (j) y = y * ld_fr(tw + ((size_t)j << tshift));
-                fr_t u = x + y;
-                y = x - y;
-                x = u;
+                bfly(x, y);
             } else {
-                fr_t u = x + y;
-                y = x - y;
+                bfly(x, y);
                 if (j) y = y * ld_fr(tw + ((size_t)j << tshift));
-                x = u;
             }
-#pragma unroll
-            for (int l = 0; l < 8; l++) {
-                sm[l * S + et] = x.v[l];
-                sm[l * S + eb] = y.v[l];
+            sm_st(sm, S, et, x);
+            sm_st(sm, S, eb, y);
+        }
+        __syncthreads();
+    }
+    for (; R4 && ls < t; ls += 2) {
+        // stages ls (first) and ls + 1 act on group bits lo and lo + 1
+        const int lo = DIT ? ls : t - 2 - ls;
+        const int sA = first_stage + ls, sB = sA + 1;
+        const int tshA = DIT ? (log_n - sA - 1) : sA;
+        const int tshB = DIT ? (log_n - sB - 1) : sB;
+        const uint32_t dLo = (1u << lo) << logG, dHi = dLo << 1;
+        for (uint32_t u = threadIdx.x; u < S / 4; u += blockDim.x) {
+            const uint32_t ql = u & (G - 1u), p4 = u >> logG;
+            const uint32_t g = ins0(ins0(p4, lo), lo + 1);
+            const uint32_t e = (g << logG) + ql;
+            const uint32_t col = (q0 + ql) & lomask;
+            fr_t x00 = sm_ld(sm, S, e), x01 = sm_ld(sm, S, e + dLo);
+            fr_t x10 = sm_ld(sm, S, e + dHi), x11 = sm_ld(sm, S, e + dLo + dHi);
+            // twiddle positions: bits of g below the stage's bit
+            const uint32_t jl = ((g & ((1u << lo) - 1u)) << b0) | col;          // stage on bit lo
+            const uint32_t jh0 = ((g & ((2u << lo) - 1u)) << b0) | col;         // stage on bit lo + 1, x0.
+            const uint32_t jh1 = (((g & ((2u << lo) - 1u)) | (1u << lo)) << b0) | col;  // ... x1. (never 0)
+            if (DIT) {
+                if (jl) {
+                    const fr_t w = ld_fr(tw + ((size_t)jl << tshA));
+                    x01 = x01 * w;
+                    x11 = x11 * w;
+                }
+                bfly(x00, x01);
+                bfly(x10, x11);
+                if (jh0) x10 = x10 * ld_fr(tw + ((size_t)jh0 << tshB));
+                x11 = x11 * ld_fr(tw + ((size_t)jh1 << tshB));
+                bfly(x00, x10);
+                bfly(x01, x11);
+            } else {
+                bfly(x00, x10);
+                bfly(x01, x11);
+                if (jh0) x10 = x10 * ld_fr(tw + ((size_t)jh0 << tshA));
+                x11 = x11 * ld_fr(tw + ((size_t)jh1 << tshA));
+                bfly(x00, x01);
+                bfly(x10, x11);
+                if (jl) {
+                    const fr_t w = ld_fr(tw + ((size_t)jl << tshB));
+                    x01 = x01 * w;
+                    x11 = x11 * w;
+                }
             }
+            sm_st(sm, S, e, x00);
+            sm_st(sm, S, e + dLo, x01);
+            sm_st(sm, S, e + dHi, x10);
+            sm_st(sm, S, e + dLo + dHi, x11);
         }
         __syncthreads();
     }
@@ -244,9 +332,7 @@ __global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int l
         uint32_t g = e >> logG, ql = e & (G - 1u);
         uint32_t q = q0 + ql;
         uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
-        fr_t x;
-#pragma unroll
-        for (int l = 0; l < 8; l++) x.v[l] = sm[l * S + e];
+        fr_t x = sm_ld(sm, S, e);
         if (post.hi) x = x * scale_factor(post, idx, log_n);
         st_fr(arr + idx, x);
     }
@@ -260,7 +346,13 @@ __global__ void __launch_bounds__(256) k_ntt_pass(fr_t* __restrict__ data, int l
 // ceil(blocks / slots) x (work of one block).  Narrower blocks can fill the
 // last wave better (one 2^20 array: 512 blocks of 2^11 elements against 456
 // slots take two waves, 1,024 of 2^10 take three half-size waves).
-static int ntt_pick_columns(bool dif, int k, int t, int logG_max, int count) {
+typedef void (*NttPassFn)(fr_t*, int, int, int, int, const fr_t*, int, NttScale, NttScale);
+static NttPassFn ntt_pass_fn(bool dif, bool r4) {
+    if (dif) return r4 ? k_ntt_pass<false, true> : k_ntt_pass<false, false>;
+    return r4 ? k_ntt_pass<true, true> : k_ntt_pass<true, false>;
+}
+
+static int ntt_pick_columns(bool dif, bool r4, int k, int t, int logG_max, int count) {
     static int sms_of[64] = {};  // SM count per device ordinal (written once, same value)
     int dev = 0;
     cudaGetDevice(&dev);
@@ -277,10 +369,7 @@ static int ntt_pick_columns(bool dif, int k, int t, int logG_max, int count) {
         int threads = S / 2 < 256 ? (int)(S / 2) : 256;
         if (threads < 32) threads = 32;
         int nb = 0;
-        if (dif)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ntt_pass<false>, threads, (size_t)S * 32);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ntt_pass<true>, threads, (size_t)S * 32);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ntt_pass_fn(dif, r4), threads, (size_t)S * 32);
         if (nb <= 0) continue;
         const double blocks = (double)count * (double)(1u << (k - t - lg));
         const double slots = (double)nb * sms;
@@ -309,12 +398,16 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
         passes[np++] = t2;
         passes[np++] = k - t1 - t2;
     }
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr_done = true;
+    // dynamic shared memory above 48 KB, once per device
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        for (int v = 0; v < 4; v++)
+            cudaFuncSetAttribute(ntt_pass_fn(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
+    const bool r4 = plan.radix == 4;
     const fr_t* tw = inverse ? plan.tw_inv : plan.tw_fwd;
     NttScale none;
     int done_bits = 0;
@@ -331,7 +424,7 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
         int logG = NTT_SMEM_LOG - t;
         if (logG < 0) logG = 0;
         if (logG > k - t) logG = k - t;
-        if (fill_waves) logG = ntt_pick_columns(dif, k, t, logG, count);
+        if (fill_waves) logG = ntt_pick_columns(dif, r4, k, t, logG, count);
         uint32_t groups = 1u << (k - t);
         uint32_t blocks = groups >> logG;
         uint32_t S = (1u << logG) << t;
@@ -342,10 +435,7 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
         const NttScale& a = pi == 0 ? pre : none;
         const NttScale& z = pi == np - 1 ? post : none;
         int prof = prof_begin(PROF_NTT, st);
-        if (dif)
-            k_ntt_pass<false><<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
-        else
-            k_ntt_pass<true><<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
+        ntt_pass_fn(dif, r4)<<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
         ::ace::note_launch();
         // work: butterflies of this pass
         prof_end(prof, st, nullptr, (uint64_t)count * ((uint64_t)1 << (k - 1)) * (uint64_t)t);

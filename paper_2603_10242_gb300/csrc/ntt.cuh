@@ -33,6 +33,7 @@ struct NttPlan {
     fr_t* rr = nullptr;       // [R^2 mod r] raw: multiplying by it enters Montgomery form
     fr_t zinv;                // (g^N - 1)^-1 (Montgomery)
     int smem_log = 11;        // log2 of the elements one block stages in shared memory (tunable)
+    int radix = 4;            // 4: stages in radix-4 pairs, 2: radix-2 stages only (tunable)
     void* mem = nullptr;
     size_t bytes = 0;
 };
@@ -40,6 +41,11 @@ struct NttPlan {
 // omega_N = 5^((r-1)/N) in Montgomery form (host)
 fr_t root_of_unity_host(int log_n);
 int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out);
+// Stage form before tuning: radix-4 pairs from 2^18 elements up, where they
+// were measured 2-6% faster; radix-2 below (13% faster at 2^16, where a
+// transform is a few short passes and the radix-2 kernel's lower register
+// count keeps more blocks resident)
+inline int ntt_default_radix(int log_n) { return log_n >= 18 ? 4 : 2; }
 void ntt_release_plans(ace_ctx* ctx);
 
 // Factor applied to the element at position p: hi[e >> h] * lo[e & (2^h-1)]

@@ -105,6 +105,7 @@ struct ace_ctx {
     // shared-memory width by log2(N)
     int tuned_msm_c[32] = {};
     int tuned_ntt_smem[32] = {};
+    int tuned_ntt_radix[32] = {};  // 2 or 4 (0 = ntt_default_radix)
     std::map<int, ace::NttPlan*> ntt_plans;
     void* g1_fixed_tab = nullptr;  // fixed-base tables for the generators (setup.cu)
     void* g2_fixed_tab = nullptr;

@@ -6,6 +6,7 @@ import random
 import pytest
 
 import oracle as O
+from paper_2603_10242_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -20,7 +21,7 @@ def test_autotune_msm_ntt_and_persist(tmp_path):
     assert [int(r[0]) for r in rep] == list(range(8, 13))
     assert all(6 <= r[1] <= 20 and r[2] > 0 for r in rep)
     nrep = ctx.autotune_ntt(10, 14)
-    assert all(int(r[1]) in (10, 11, 12) for r in nrep)
+    assert all(int(r[1]) in (10, 11, 12) and int(r[4]) in (2, 4) for r in nrep)
     # tuned MSM still exact
     rng = random.Random(3)
     n = 3000
@@ -39,6 +40,7 @@ def test_autotune_msm_ntt_and_persist(tmp_path):
     ctx.autotune_save(path)
     data = json.load(open(path))
     assert data["msm_c"] and data["ntt_smem_log"]
+    assert set(data["ntt_radix"].values()) <= {2, 4}
     ctx2 = ace.Context(0)
     ctx2.autotune_load(path)
     data["gpu"] = "another GPU"
@@ -60,3 +62,27 @@ def test_autotune_batch_slots_keeps_results():
     assert len(times) == 3 and all(t > 0 for t in times)
     proofs, status = ctx.prove_batch([pk] * 4, [dz] * 4, r * 4, s * 4)
     assert status == [0] * 4 and all(p == want for p in proofs)
+
+
+@pytest.mark.parametrize("log_n", [1, 2, 3, 5, 9, 12, 17, 20])
+def test_both_ntt_stage_forms_match_oracle(tmp_path, log_n):
+    """Radix-2 stages and radix-4 pairs (chosen per size by default, or by a
+    tuning file) give the oracle's transform, every kind, every element, at
+    one-pass sizes with odd and even stage counts and at multi-pass sizes."""
+    ctx = ace.Context(0)
+    path = str(tmp_path / "t.json")
+    ctx.autotune_save(path)
+    data = json.load(open(path))
+    vals = inputs.sample_fr(300 + log_n, 7, 1 << log_n).tobytes()
+    for radix in (2, 4):
+        data["ntt_radix"] = {str(log_n): radix}
+        json.dump(data, open(path, "w"))
+        ctx.autotune_load(path)
+        for kind in range(4):
+            d = gu.dev(vals)
+            ctx.ntt(d, log_n, kind)
+            if kind < 2:
+                want = O.ntt(vals, log_n, inverse=(kind == 1))
+            else:
+                want = O.coset_ntt(vals, log_n, 5, inverse=(kind == 3))
+            assert gu.host(d) == want, (radix, kind)

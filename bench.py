@@ -83,6 +83,18 @@ def _sm_max_mhz(clocks) -> float:
         return SM_MAX_MHZ_DEFAULT
 
 
+def _tuned_batch(ctx) -> dict:
+    """The batch configuration the library's autotuner kept (proving slots
+    and stage layout), read back from its saved choices."""
+    import tempfile
+
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.json")
+        ctx.autotune_save(path)
+        t = json.load(open(path))
+    return {"slots": t["batch_slots"], "one_stream_per_proof": bool(t.get("batch_one_stream", 0))}
+
+
 def _dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -270,8 +282,7 @@ def run_ours(args):
         ctx.prove_async(pk, dz, rs[i][0], rs[i][1], proofs[256 * i:], status[i:])
     # proving slots for the batch: the autotuner times 1..4 slots (untimed)
     slot_ms = ctx.autotune_batch_slots(pk, dz, 6, 4)
-    # the library keeps the fewest slots within 2% of the fastest count
-    batch_slots = 1 + next(q for q in range(len(slot_ms)) if slot_ms[q] <= 1.02 * min(slot_ms))
+    batch_cfg = _tuned_batch(ctx)
     batch(min(4, args.steps), 0)
     torch.cuda.synchronize()
 
@@ -460,8 +471,9 @@ def run_ours(args):
                 "no ncu capture of this kernel version yet",
                 "kernel_version": G1_BUCKET_KERNEL_VERSION,
                 "peak_measured_T_per_s": measured_peak,
-                "measured": "CUDA events around every launch inside the timed proofs; up to four proofs run "
-                            "at once, so each launch shares the SMs with other kernels",
+                "measured": "CUDA events around every launch inside the timed proofs; proofs overlap across "
+                            "proving slots (configuration in `batch`), so a launch can share the SMs with "
+                            "other proofs' kernels",
                 "union": union, "isolated": isolated, "whole_step": step_alu}
     step_sorted = sorted(step_ms)
     p50 = statistics.median(step_sorted)
@@ -483,8 +495,8 @@ def run_ours(args):
                            "budget_ms": 600.0,
                            "path": "one proof per call, back to back on one stream, CUDA events between calls"},
             "plain_proofs_per_s": plain_value,
-            "batch_slots": batch_slots,
-            "batch_slot_ms": slot_ms,
+            "batch": batch_cfg,
+            "batch_tuning_ms": {"aux_streams": slot_ms[:4], "one_stream_per_proof": slot_ms[4:]},
             "msm_g1_2p20_points_per_s": msm,
             "stages": stages,
             "verified": bool(verified),
@@ -544,8 +556,8 @@ def run_batch_workload(args):
     ss = b"".join(s_ for _, s_ in rss)
     # proving slots from the autotuner, timed on the median-size proof
     mid = sorted(range(k), key=lambda i: sizes[i][1])[k // 2]
-    slot_ms = ctx.autotune_batch_slots(pks[mid], dzs[mid], 8, 4)
-    slots = 1 + next(q for q in range(len(slot_ms)) if slot_ms[q] <= 1.02 * min(slot_ms))
+    slot_ms = ctx.autotune_batch_slots(pks[mid], dzs[mid], 8, 6)
+    slots = _tuned_batch(ctx)
     ctx.prove_batch(pks, dzs, rs, ss)            # warm-up (sizes the slots)
     for i in range(k):
         ctx.prove(pks[i], dzs[i], *rss[i])

@@ -457,11 +457,15 @@ int ace_autotune_msm(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* r
  * pair per size.  report (optional, 5 per size): log_n, chosen width, its
  * ms, ms at width 2^11 with the untuned form, chosen radix (2 or 4). */
 int ace_autotune_ntt(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* report);
-/* Time batches of k proofs of (pk, d_z) over 1..max_slots proving slots and
- * keep, for ace_prove_batch, the fewest slots whose batch time is within 2%
- * of the fastest count (fewer slots hold less scratch and share the SMs among
- * fewer proofs at the same throughput).  report (optional, max_slots
- * doubles): ms per batch for each count. */
+/* Time batches of k proofs of (pk, d_z) over 1..max_slots proving slots, in
+ * two stage layouts (a proof's MSMs spread over its slot's auxiliary
+ * streams, or every stage of a proof on one stream with proofs overlapping
+ * across slots only), and keep for ace_prove_batch, among the configurations
+ * within 2% of the fastest, the one-stream layout first and then the fewest
+ * slots (fewer kernels share the SMs and fewer slots hold scratch, at the same
+ * throughput).  The proofs do not change.  report (optional, 2 x max_slots
+ * doubles): ms per batch for 1..max_slots slots with the auxiliary streams,
+ * then the same with one stream per proof. */
 int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, int k, int max_slots,
                              double* report);
 /* Save / load the tuned choices (JSON keyed by the GPU name; loading a file

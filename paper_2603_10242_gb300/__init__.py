@@ -238,7 +238,9 @@ class Context:
         return [tuple(rep[5 * i:5 * i + 5]) for i in range(n)]
 
     def autotune_batch_slots(self, pk: "ProvingKey", d_z, k: int, max_slots: int = 4):
-        rep = (ctypes.c_double * max_slots)()
+        """ms per batch: [1..max_slots slots, MSMs on auxiliary streams] +
+        [1..max_slots slots, one stream per proof]."""
+        rep = (ctypes.c_double * (2 * max_slots))()
         check(lib().ace_autotune_batch_slots(self.h, pk.h, _ptr(d_z), k, max_slots, rep))
         return list(rep)
 

@@ -208,23 +208,38 @@ int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, 
     std::vector<const ace_fr*> zs(k, d_z);
     std::vector<uint8_t> proofs(256 * (size_t)k);
     std::vector<int32_t> status(k);
-    std::vector<double> ms_of(max_slots + 1, 1e30);
+    // ms_of[layout][q]: layout 1 = every stage of a proof on one stream,
+    // layout 0 = the MSMs spread over the slot's auxiliary streams
+    std::vector<double> ms_of[2] = {std::vector<double>(max_slots + 1, 1e30),
+                                    std::vector<double>(max_slots + 1, 1e30)};
     double best_ms = 1e30;
-    for (int q = 1; q <= max_slots; q++) {
-        ctx->batch_slots = q;
-        ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(), status.data()));
-        auto t0 = std::chrono::steady_clock::now();
-        ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(), status.data()));
-        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        if (report) report[q - 1] = ms;
-        ms_of[q] = ms;
-        if (ms < best_ms) best_ms = ms;
+    for (int layout = 0; layout < 2; layout++) {
+        ctx->batch_one_stream = layout == 1;
+        for (int q = 1; q <= max_slots; q++) {
+            ctx->batch_slots = q;
+            ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
+                                    status.data()));
+            auto t0 = std::chrono::steady_clock::now();
+            ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
+                                    status.data()));
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (report) report[layout * max_slots + q - 1] = ms;
+            ms_of[layout][q] = ms;
+            if (ms < best_ms) best_ms = ms;
+        }
     }
-    // the fewest slots within 2% of the fastest count: each slot holds a
-    // proof's scratch, and fewer proofs in flight share the SMs less, at the
-    // same throughput
-    int best = 1;
-    while (best < max_slots && ms_of[best] > 1.02 * best_ms) best++;
+    // among the configurations within 2% of the fastest: one stream per proof
+    // first (its kernels share the SMs with fewer others, at the same
+    // throughput), then the fewest slots (each holds a proof's scratch)
+    int best_layout = 0, best = max_slots;
+    for (int layout = 1, found = 0; layout >= 0 && !found; layout--)
+        for (int q = 1; q <= max_slots && !found; q++)
+            if (ms_of[layout][q] <= 1.02 * best_ms) {
+                best_layout = layout;
+                best = q;
+                found = 1;
+            }
+    ctx->batch_one_stream = best_layout == 1;
     ctx->batch_slots = best;
     return ACE_OK;
 }
@@ -241,7 +256,8 @@ int ace_autotune_save(ace_ctx* ctx, const char* path) {
         set_error("ace_autotune_save: cannot open %s", path);
         return ACE_E_ARG;
     }
-    fprintf(f, "{\"gpu\": \"%s\", \"batch_slots\": %d, \"msm_c\": {", name.c_str(), ctx->batch_slots);
+    fprintf(f, "{\"gpu\": \"%s\", \"batch_slots\": %d, \"batch_one_stream\": %d, \"msm_c\": {", name.c_str(),
+            ctx->batch_slots, ctx->batch_one_stream ? 1 : 0);
     bool first = true;
     for (int i = 0; i < 32; i++)
         if (ctx->tuned_msm_c[i]) {
@@ -325,7 +341,15 @@ int ace_autotune_load(ace_ctx* ctx, const char* path) {
             set_error("ace_autotune_load: %s holds out-of-range values", path);
             return ACE_E_ARG;
         }
+    int one_stream = 0;  // absent from files saved before the layout was tuned
+    size_t po = txt.find("\"batch_one_stream\":");
+    if (po != std::string::npos &&
+        (sscanf(txt.c_str() + po, "\"batch_one_stream\": %d", &one_stream) != 1 || one_stream < 0 || one_stream > 1)) {
+        set_error("ace_autotune_load: %s is malformed", path);
+        return ACE_E_ARG;
+    }
     ctx->batch_slots = slots;
+    ctx->batch_one_stream = one_stream == 1;
     memcpy(ctx->tuned_msm_c, msm, sizeof msm);
     memcpy(ctx->tuned_ntt_smem, ntt, sizeof ntt);
     memcpy(ctx->tuned_ntt_radix, radix, sizeof radix);

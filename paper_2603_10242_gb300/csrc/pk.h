@@ -78,9 +78,11 @@ struct MsmOut {
 };
 // one whole proof on proving slot `slot` at stream priority level `prio`
 // (prove.cu); with msm_out, only its QAP and MSMs
+// one_stream: every stage on the slot's main stream in turn (no auxiliary
+// streams), for batches whose proofs overlap across slots instead
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
               uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join,
-              const MsmOut* msm_out = nullptr);
+              const MsmOut* msm_out = nullptr, bool one_stream = false);
 // device bytes of scratch arena `arena` of a slot proving with `pk`
 size_t prove_slot_bytes(const ace_pk* pk, int arena);
 }  // namespace ace

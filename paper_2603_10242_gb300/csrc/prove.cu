@@ -489,7 +489,8 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
 // ev_done marks them complete, and the fixed-base terms, V and the assembly
 // are left to the batch's tail kernels (d_proof is not written).
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
-              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join, const MsmOut* msm_out) {
+              uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join, const MsmOut* msm_out,
+              bool one_stream) {
     if (prio < 0 || prio >= PRIO_LEVELS || slot < 0 || slot >= MAX_SLOTS) {
         set_error("prove: slot %d / priority level %d out of range", slot, prio);
         return ACE_E_ARG;
@@ -499,7 +500,7 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     // the slot's streams at this level; in serial mode (a measurement of the
     // per-stage split) every stage runs on the main stream, one after another
     SlotStreams ss = sl.lv[prio];
-    if (ctx->serial)
+    if (ctx->serial || one_stream)
         for (int k = 0; k < 5; k++) ss.aux[k] = ss.main;
     ProvePlans pl = prove_plans(pk);
     for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, slot, k, pl.slot_bytes[k]));
@@ -882,7 +883,8 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
             z = stage;
         }
         MsmOut mo{res1 + 4 * i, res2 + i};
-        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false, &mo));
+        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false, &mo,
+                          ctx->batch_one_stream));
     }
     // V and the assembly of every proof once all MSMs and fixed terms are done
     for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));

@@ -98,6 +98,9 @@ struct ace_ctx {
     ace::Arena scratch[4];  // scratch of single calls (MSM, NTT, QAP, batch outputs)
     ace::ProveSlot slots[ace::MAX_SLOTS];
     int batch_slots = 2;  // slots a batch spreads its proofs over
+    // a batch's proofs run all their stages on their slot's main stream
+    // (proofs overlap across slots only); autotuned with batch_slots
+    bool batch_one_stream = false;
     // measurement mode: a proof runs every stage on its main stream in turn
     // (ace_debug_serial_proofs), so per-stage times do not overlap
     bool serial = false;

@@ -79,7 +79,8 @@ def test_batch_from_host_witnesses_matches_device_batch():
 def test_batch_tails_same_bytes_for_every_slot_count(tmp_path):
     """The batch's tail kernels (fixed-base terms, V and assembly of every
     proof in one launch each) give the bytes of the one-proof path whatever
-    the number of proving slots."""
+    the number of proving slots and the stage layout (MSMs on auxiliary
+    streams, or every stage of a proof on one stream)."""
     import re
     ctx = ace.Context(0)
     circs = [ace.Circuit(*p, seed=90 + i) for i, p in enumerate(PARAMS[:3])]
@@ -92,9 +93,11 @@ def test_batch_tails_same_bytes_for_every_slot_count(tmp_path):
     path = str(tmp_path / "tune.json")
     ctx.autotune_save(path)
     txt = open(path).read()
-    for q in (1, 2, 3, 5):
-        open(path, "w").write(re.sub(r'"batch_slots": \d+', f'"batch_slots": {q}', txt))
+    for q, one in ((1, 0), (2, 0), (3, 0), (5, 0), (1, 1), (3, 1)):
+        t = re.sub(r'"batch_slots": \d+', f'"batch_slots": {q}', txt)
+        t = re.sub(r'"batch_one_stream": \d+', f'"batch_one_stream": {one}', t)
+        open(path, "w").write(t)
         ctx.autotune_load(path)
         proofs, status = ctx.prove_batch(pks * 2, dzs * 2, rs * 2, ss * 2)
-        assert status == [0] * 6 and proofs == want + want, q
+        assert status == [0] * 6 and proofs == want + want, (q, one)
     ctx.close()

@@ -556,7 +556,7 @@ def run_batch_workload(args):
     ss = b"".join(s_ for _, s_ in rss)
     # proving slots from the autotuner, timed on the median-size proof
     mid = sorted(range(k), key=lambda i: sizes[i][1])[k // 2]
-    slot_ms = ctx.autotune_batch_slots(pks[mid], dzs[mid], 8, 6)
+    slot_ms = ctx.autotune_batch_slots(pks[mid], dzs[mid], 16, 12)
     slots = _tuned_batch(ctx)
     ctx.prove_batch(pks, dzs, rs, ss)            # warm-up (sizes the slots)
     for i in range(k):
@@ -741,7 +741,10 @@ def run_single(args):
         p2, st2 = ctx.prove_batch_host([pk], [zpin], r, s_)
         e2e.append((time.perf_counter() - t0) * 1e3)
     assert p2[0] == want and st2 == [0]
-    # n proofs in one batch call (device-resident witness)
+    # n proofs in one batch call (device-resident witness), in the batch
+    # configuration the autotuner keeps for this key (slots and stage layout)
+    tune_ms = ctx.autotune_batch_slots(pk, dz, 64, 16)
+    batch_cfg = _tuned_batch(ctx)
     pb, sb = ctx.prove_batch([pk] * n, [dz] * n, r * n, s_ * n)
     t0 = time.perf_counter()
     pb, sb = ctx.prove_batch([pk] * n, [dz] * n, r * n, s_ * n)
@@ -770,7 +773,8 @@ def run_single(args):
         "e2e_one_per_call": {"proofs_per_s": n / (sum(e2e) / 1e3), "latency_ms": {"p50": pct(e2e, 0.5),
                              "p99": pct(e2e, 0.99)}, "h2d_bytes_per_proof": len(z), "d2h_bytes_per_proof": 260,
                              "path": "ace_prove_batch_host with one proof per call"},
-        "batched_proofs_per_s": n / batch_s,
+        "batched_proofs_per_s": n / batch_s, "batch": batch_cfg,
+        "batch_tuning_ms": {"aux_streams": tune_ms[:16], "one_stream_per_proof": tune_ms[16:]},
         "verified": pk.verify(z[32:64], want) == 1, "oracle_equal": op == want,
         "cpu_baseline": {"kind": "oracle", "cores": O.lib().orc_num_threads(),
                          "value": 1.0 / statistics.median(ot), "unit": "proofs/s",

@@ -463,9 +463,10 @@ int ace_autotune_ntt(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* r
  * across slots only), and keep for ace_prove_batch, among the configurations
  * within 2% of the fastest, the one-stream layout first and then the fewest
  * slots (fewer kernels share the SMs and fewer slots hold scratch, at the same
- * throughput).  The proofs do not change.  report (optional, 2 x max_slots
- * doubles): ms per batch for 1..max_slots slots with the auxiliary streams,
- * then the same with one stream per proof. */
+ * throughput).  The proofs do not change.  1 <= max_slots <= 16 (ACE_E_ARG
+ * otherwise).  report (optional, 2 x max_slots doubles): ms per batch for
+ * 1..max_slots slots with the auxiliary streams, then the same with one
+ * stream per proof. */
 int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, int k, int max_slots,
                              double* report);
 /* Save / load the tuned choices (JSON keyed by the GPU name; loading a file

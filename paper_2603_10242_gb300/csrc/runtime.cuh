@@ -71,7 +71,7 @@ struct NttPlan;  // twiddle tables for one size (ntt.cu)
 // runs on one level's streams, so that a server can let the proofs admitted
 // first keep the SMs while later ones fill the gaps.
 static const int PROVE_ARENAS = 5;  // QAP + H MSM, A, B1, B2, L
-static const int MAX_SLOTS = 8;
+static const int MAX_SLOTS = 16;
 static const int PRIO_LEVELS = 3;
 struct SlotStreams {
     cudaStream_t main = nullptr;

@@ -93,7 +93,7 @@ def test_batch_tails_same_bytes_for_every_slot_count(tmp_path):
     path = str(tmp_path / "tune.json")
     ctx.autotune_save(path)
     txt = open(path).read()
-    for q, one in ((1, 0), (2, 0), (3, 0), (5, 0), (1, 1), (3, 1)):
+    for q, one in ((1, 0), (2, 0), (3, 0), (5, 0), (1, 1), (3, 1), (12, 1)):
         t = re.sub(r'"batch_slots": \d+', f'"batch_slots": {q}', txt)
         t = re.sub(r'"batch_one_stream": \d+', f'"batch_one_stream": {one}', t)
         open(path, "w").write(t)

@@ -915,6 +915,8 @@ def run_case(args):
     msm_g2 -- one G2 MSM of 2^18 points (uniform scalars);
     ntt -- one 2^20 forward transform of three arrays (QAP batch shape);
     prove16 -- one proof of the 2^16 instance of the block circuit family;
+    prove10 -- `steps` proofs of the 2^10 single-proof circuit, one per call
+    (prints the launches issued before them, for a profiler's skip count);
     prove20 -- `steps` proofs of the 2^20 block circuit in one batch (prints
     the launches issued before the batch, for a profiler's skip count)."""
     import numpy as np
@@ -948,6 +950,20 @@ def run_case(args):
         d = torch.from_numpy(inputs.sample_fr(1, 7, 3 * n).view(np.uint8).reshape(-1)).cuda()
         for _ in range(args.steps):
             ctx.ntt_mont(d, 20, 3, True, False)
+    elif args.case == "prove10":
+        c = ace.Circuit(*SINGLE_CIRCUIT, seed=1)
+        z = c.witness(1)
+        pk = ace.ProvingKey(ctx, c, toxic_seed=1)
+        dz = torch.frombuffer(bytearray(z), dtype=torch.uint8).cuda()
+        r, s_ = ace.rs_from_seed(1)
+        ctx.prove(pk, dz, r, s_)
+        torch.cuda.synchronize()
+        before = ace.launch_count()
+        for _ in range(args.steps):
+            assert pk.verify(z[32:64], ctx.prove(pk, dz, r, s_)) == 1
+        print(json.dumps({"case": args.case, "steps": args.steps, "launches_before": before,
+                          "launches": ace.launch_count()}))
+        return
     elif args.case == "prove20":
         c = ace.Circuit(seed=SEED, **CIRCUIT)
         z = c.witness(SEED)
@@ -1118,7 +1134,7 @@ def main():
     ap.add_argument("--workload", choices=["block2p20", "single2p10", "batch64", "serve", "pertx", "sweep"],
                     default="block2p20",
                     help="batch64: 64 proofs of log-uniform sizes 2^12..2^18 (batched vs one per call)")
-    ap.add_argument("--case", choices=["msm_g1", "msm_g2", "ntt", "prove16", "prove20"], default=None,
+    ap.add_argument("--case", choices=["msm_g1", "msm_g2", "ntt", "prove10", "prove16", "prove20"], default=None,
                     help="run a small fixed case for profiler captures instead of the bench")
     ap.add_argument("--log-n", type=int, default=20, help="--case msm_g1: log2 of the number of points")
     ap.add_argument("--gpus", type=int, default=1)

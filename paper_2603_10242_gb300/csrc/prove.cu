@@ -141,18 +141,38 @@ struct PkTabs {
     const g1_aff *alpha1, *beta1, *delta1;
     const g2_aff* delta2;
 };
+// k P from the 8-bit window table of P (tab[w 255 + d - 1] = d 2^(8w) P):
+// the 32 byte-windows' table points summed on four lanes (the same sum as
+// fixed_mul_tab, bit for bit); all four lanes of `mask` call with the same k
+template <class F>
+__device__ Xyzz<F> fixed_mul_tab_quad(const Affine<F>* tab, const uint32_t* k, int sub, unsigned mask) {
+    Xyzz<F> acc = xyzz_inf<F>();
+#pragma unroll 1
+    for (int w = 0; w < 32; w++) {
+        const uint32_t d = (k[w >> 2] >> ((w & 3) * 8)) & 255u;
+        if (d) acc = quad_add(acc, xyzz_from_aff(tab[w * 255 + d - 1]), sub, mask);
+    }
+    return acc;
+}
+// fixed-base term w (0..4) on lanes 0..3 of the calling warp; lane 0 writes it
 __device__ __forceinline__ void fixed_term(const PkTabs& t, const fr_t& r, const fr_t& s, const fr_t& rs, int w,
                                            g1_xyzz* fx1, g2_xyzz* fx2) {
-    switch (w) {
-        case 0: fx1[0] = fixed_mul_tab(t.delta1, r.v); break;
-        case 1: fx1[1] = fixed_mul_tab(t.alpha1, s.v); break;
-        case 2: fx1[2] = fixed_mul_tab(t.beta1, r.v); break;
-        case 3: fx1[3] = fixed_mul_tab(t.delta1, rs.v); break;
-        default: fx2[0] = fixed_mul_tab(t.delta2, s.v); break;
+    const int lane = threadIdx.x & 31;
+    if (lane >= 4) return;
+    const unsigned mask = 0xfu;
+    if (w == 4) {
+        g2_xyzz v = fixed_mul_tab_quad(t.delta2, s.v, lane, mask);
+        if (lane == 0) fx2[0] = v;
+        return;
     }
+    const g1_aff* tab = w == 1 ? t.alpha1 : w == 2 ? t.beta1 : t.delta1;
+    const uint32_t* k = w == 1 ? s.v : w == 3 ? rs.v : r.v;
+    g1_xyzz v = fixed_mul_tab_quad(tab, k, lane, mask);
+    if (lane == 0) fx1[w] = v;
 }
-__global__ void k_prove_fixed(PkTabs t, fr_t r, fr_t s, fr_t rs, g1_xyzz* fx1, g2_xyzz* fx2) {
-    if ((threadIdx.x & 31) != 0) return;
+// one term per warp (160 threads)
+__global__ void __launch_bounds__(160) k_prove_fixed(PkTabs t, fr_t r, fr_t s, fr_t rs, g1_xyzz* fx1,
+                                                     g2_xyzz* fx2) {
     fixed_term(t, r, s, rs, threadIdx.x >> 5, fx1, fx2);
 }
 
@@ -277,7 +297,6 @@ struct TailDesc {
 };
 // per proof q: fx1[4 q .. 4 q + 3], fx2[q]; 160 threads per block
 __global__ void __launch_bounds__(160) k_prove_fixed_batch(const TailDesc* d, g1_xyzz* fx1, g2_xyzz* fx2) {
-    if ((threadIdx.x & 31) != 0) return;
     const TailDesc& q = d[blockIdx.x];
     fixed_term(q.tabs, q.r, q.s, q.rs, threadIdx.x >> 5, fx1 + 4 * (size_t)blockIdx.x, fx2 + blockIdx.x);
 }

@@ -361,10 +361,14 @@ int ace_debug_serial_proofs(ace_ctx* ctx, int on);
  * independent circuits at once), here over proofs of any mix of keys and
  * sizes.  pks[i] and d_zs[i] (device, pks[i]'s m canonical values, 16-byte
  * aligned) give proof i, rs[i] and ss[i] its randomness (host, canonical).
- * Proofs go round-robin over the context's proving slots (ace_autotune_
- * batch_slots chooses their number), so consecutive proofs overlap on the
- * device.  Proof i goes to proofs + 256 i (host); status[i] (host) is 0, or 1
- * if witness i does not satisfy its R1CS.  Synchronous.  ACE_E_ARG for NULL
+ * Proofs go round-robin over the context's proving slots (up to 16;
+ * ace_autotune_batch_slots chooses their number and whether each proof's
+ * MSMs spread over its slot's auxiliary streams or all its stages run on one
+ * stream), so consecutive proofs overlap on the device.  The fixed-base
+ * terms of all proofs run in one launch beside the first MSMs, and the
+ * variable-base terms and the assembly in one launch each at the end.
+ * Proof i goes to proofs + 256 i (host); status[i] (host) is 0, or 1 if
+ * witness i does not satisfy its R1CS.  Synchronous.  ACE_E_ARG for NULL
  * pointers or non-canonical r, s; ACE_E_OOM if the slots' scratch cannot be
  * allocated.  Each proof equals the one ace_prove makes with the same inputs. */
 int ace_prove_batch(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,

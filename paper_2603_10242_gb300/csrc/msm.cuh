@@ -8,8 +8,10 @@
 //   2. counting sort of (bucket, point) pairs: histogram, exclusive scan,
 //      scatter;
 //   3. one mixed XYZZ addition per entry into its bucket;
-//   4. per window sum_b b S_b: running sums over segments of L = 16 buckets
-//      give W_j (weights 1..L inside segment j) and S_j; one thread per
+//   4. per window sum_b b S_b: running sums over segments of L buckets
+//      (16; 4 for one MSM whose windows hold at most 2^13 buckets, where the
+//      segment chain is the reduction's latency) give W_j (weights 1..L
+//      inside segment j) and S_j; one thread per
 //      segment adds j L S_j to W_j (at most c - 1 doublings), and block-wide
 //      trees sum the M segments of every window (256 to 1 per pass);
 //   5. Horner over windows (c doublings each) plus the ones-window total.
@@ -67,6 +69,9 @@ MsmPlan msm_plan(size_t n, int force_c = 0);
 MsmPlan msm_plan_tabled(size_t n, int force_c = 0);
 // G1 plan over the GLV split of n points (2 n virtual points, 128-bit scalars)
 MsmPlan msm_plan_glv(size_t n, int force_c = 0);
+// make p a plan for `batch` MSMs over the same points (segments of 16
+// buckets again when batch > 1; see plan_for)
+void msm_plan_set_batch(MsmPlan& p, uint32_t batch);
 // GLV inputs of a G1 MSM: for i < n, out[i] = +-P_i and out[n + i] =
 // +-phi(P_i) (Montgomery affine), osc[i] = |k1|, osc[n + i] = |k2| (8 limbs,
 // canonical) with k_i mod r = k1 + k2 lambda and the signs moved onto the

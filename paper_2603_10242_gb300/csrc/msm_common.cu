@@ -76,13 +76,29 @@ static MsmPlan plan_for(size_t n, int c, bool tabled, bool glv = false) {
     p.glv = glv;
     p.K = ((glv ? 128 : 255) + p.c - 1) / p.c;
     p.B = 1u << (p.c - 1);
-    p.lambda = p.c - 1 < 4 ? p.c - 1 : 4;  // segments of 16 buckets
+    // segments of 16 buckets; of 4 when a window holds at most 2^13 buckets:
+    // there a segment's sequential running sum (2 additions per bucket, one
+    // thread) is the longest chain of the reduction, and four times as many
+    // threads still leave the GPU mostly idle
+    p.lambda = p.c - 1 < 4 ? p.c - 1 : 4;
+    if (p.c <= 14) p.lambda = 2;
     p.L = 1u << p.lambda;
     p.M = p.B / p.L;
     p.tabled = tabled;
     p.B1 = 1;
     while (p.B1 < p.B && (size_t)p.B1 * 64 < n) p.B1 *= 2;
     return p;
+}
+
+void msm_plan_set_batch(MsmPlan& p, uint32_t batch) {
+    p.batch = batch;
+    // many MSMs at once give the reduction threads enough: back to segments
+    // of 16 buckets (fewer segments to weight)
+    if (batch > 1) {
+        p.lambda = p.c - 1 < 4 ? p.c - 1 : 4;
+        p.L = 1u << p.lambda;
+        p.M = p.B / p.L;
+    }
 }
 
 static int best_window(size_t n, bool tabled, int bits = 255) {

@@ -618,7 +618,7 @@ static ManyPlans many_plans(const ace_pk* pk, uint32_t count) {
     p.A = pk->A.plan;
     p.B = pk->B1.plan;
     p.L = pk->L.plan;
-    p.H.batch = p.A.batch = p.B.batch = p.L.batch = count;
+    for (MsmPlan* q : {&p.H, &p.A, &p.B, &p.L}) msm_plan_set_batch(*q, count);
     const size_t N = pk->N, fr = sizeof(fr_t);
     // arena 0: a, b, c and h of every proof, the H MSM, all per-proof points
     p.arena[0] = 4 * N * count * fr + msm_scratch_bytes<fp_t>(p.H, true) +

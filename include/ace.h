@@ -364,9 +364,11 @@ int ace_debug_serial_proofs(ace_ctx* ctx, int on);
  * Proofs go round-robin over the context's proving slots (up to 16;
  * ace_autotune_batch_slots chooses their number and whether each proof's
  * MSMs spread over its slot's auxiliary streams or all its stages run on one
- * stream), so consecutive proofs overlap on the device.  The fixed-base
- * terms of all proofs run in one launch beside the first MSMs, and the
- * variable-base terms and the assembly in one launch each at the end.
+ * stream), so consecutive proofs overlap on the device.  When a call has
+ * more proofs than slots, the fixed-base terms of all proofs run in one
+ * launch beside the first MSMs and the variable-base terms and the assembly
+ * in one launch each at the end; otherwise each proof finishes on its slot
+ * as a lone proof does.
  * Proof i goes to proofs + 256 i (host); status[i] (host) is 0, or 1 if
  * witness i does not satisfy its R1CS.  Synchronous.  ACE_E_ARG for NULL
  * pointers or non-canonical r, s; ACE_E_OOM if the slots' scratch cannot be

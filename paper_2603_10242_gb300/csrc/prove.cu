@@ -874,18 +874,24 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
         for (int a = 0; a < PROVE_ARENAS; a++) ACE_TRY(slot_arena_ensure(ctx, q, a, need[a]));
         if (host) ACE_TRY(slot_witness_ensure(ctx, q, wit));
     }
-    // the fixed-base terms of every proof in one launch, on slot 0's fifth
-    // auxiliary stream (unused by proofs whose tails are batched), beside the
-    // proofs' MSMs
-    ACE_TRY_CUDA(cudaMemcpyAsync(d_desc, desc.data(), k * sizeof(TailDesc), cudaMemcpyHostToDevice, st));
+    // With more proofs than slots the tails are batched: the fixed-base terms
+    // of every proof in one launch, on slot 0's fifth auxiliary stream (unused
+    // by proofs whose tails are batched), beside the proofs' MSMs, and V and
+    // the assembly in one launch each at the end.  With at most one proof per
+    // slot each proof keeps its own tail, which starts as soon as its own
+    // MSMs allow (lower latency for a lone proof).
+    const bool batched_tails = k > (size_t)nslots;
     ProveSlot& s0 = ctx->slots[0];
     cudaStream_t tail = s0.lv[0].aux[4];
-    ACE_TRY_CUDA(cudaEventRecord(s0.ev_aux[4], st));
-    ACE_TRY_CUDA(cudaStreamWaitEvent(tail, s0.ev_aux[4], 0));
-    int pf = prof_begin(PROF_ASSEMBLY, tail);
-    k_prove_fixed_batch<<<(unsigned)k, 160, 0, tail>>>(d_desc, fx1, fx2); ::ace::note_launch();
-    prof_end(pf, tail, nullptr, k);
-    ACE_TRY_CUDA(cudaGetLastError());
+    if (batched_tails) {
+        ACE_TRY_CUDA(cudaMemcpyAsync(d_desc, desc.data(), k * sizeof(TailDesc), cudaMemcpyHostToDevice, st));
+        ACE_TRY_CUDA(cudaEventRecord(s0.ev_aux[4], st));
+        ACE_TRY_CUDA(cudaStreamWaitEvent(tail, s0.ev_aux[4], 0));
+        int pf = prof_begin(PROF_ASSEMBLY, tail);
+        k_prove_fixed_batch<<<(unsigned)k, 160, 0, tail>>>(d_desc, fx1, fx2); ::ace::note_launch();
+        prof_end(pf, tail, nullptr, k);
+        ACE_TRY_CUDA(cudaGetLastError());
+    }
     for (size_t i = 0; i < k; i++) {
         const fr_t& rr = desc[i].r;
         const fr_t& sv = desc[i].s;
@@ -902,20 +908,23 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
             z = stage;
         }
         MsmOut mo{res1 + 4 * i, res2 + i};
-        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false, &mo,
-                          ctx->batch_one_stream));
+        ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false,
+                          batched_tails ? &mo : nullptr, ctx->batch_one_stream));
     }
-    // V and the assembly of every proof once all MSMs and fixed terms are done
     for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));
-    ACE_TRY_CUDA(cudaEventRecord(s0.ev_aux[4], tail));
-    ACE_TRY_CUDA(cudaStreamWaitEvent(st, s0.ev_aux[4], 0));
-    fp_t beta;
-    memcpy(beta.v, GLV_BETA, 32);
-    int pv = prof_begin(PROF_ASSEMBLY, st);
-    k_prove_var_batch<<<(unsigned)k, 128, 0, st>>>(d_desc, res1, fe_to_mont(beta), vterm); ::ace::note_launch();
-    k_assemble_batch<<<(unsigned)k, 96, 0, st>>>(d_desc, res1, res2, fx1, fx2, vterm, d_proofs); ::ace::note_launch();
-    prof_end(pv, st, nullptr, k);
-    ACE_TRY_CUDA(cudaGetLastError());
+    if (batched_tails) {
+        // V and the assembly of every proof once all MSMs and fixed terms are done
+        ACE_TRY_CUDA(cudaEventRecord(s0.ev_aux[4], tail));
+        ACE_TRY_CUDA(cudaStreamWaitEvent(st, s0.ev_aux[4], 0));
+        fp_t beta;
+        memcpy(beta.v, GLV_BETA, 32);
+        int pv = prof_begin(PROF_ASSEMBLY, st);
+        k_prove_var_batch<<<(unsigned)k, 128, 0, st>>>(d_desc, res1, fe_to_mont(beta), vterm); ::ace::note_launch();
+        k_assemble_batch<<<(unsigned)k, 96, 0, st>>>(d_desc, res1, res2, fx1, fx2, vterm, d_proofs);
+        ::ace::note_launch();
+        prof_end(pv, st, nullptr, k);
+        ACE_TRY_CUDA(cudaGetLastError());
+    }
     ACE_TRY_CUDA(cudaMemcpyAsync(proofs, d_proofs, k * 256, cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaMemcpyAsync(status, d_status, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     ACE_TRY_CUDA(cudaStreamSynchronize(st));

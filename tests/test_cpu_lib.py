@@ -217,3 +217,25 @@ def test_msm_plan_invariants(lib, kind):
         ace.msm_plan(1000, kind, 5)
     with pytest.raises(ace.AceError):
         ace.msm_plan(1000, 7)
+
+
+def test_msm_plan_segment_length(lib):
+    """Segments of 4 buckets for single MSMs whose windows hold at most 2^13
+    buckets (c <= 14), 16 above."""
+    for kind in (ace.MSM_FULL, ace.MSM_TABLED, ace.MSM_GLV):
+        for c in range(8, 21):
+            p = ace.msm_plan(1 << 16, kind, c)
+            assert p["L"] == (4 if c <= 14 else 16), (kind, c)
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    """Argument checks that return before any CUDA call: NULL context or
+    arrays, empty batches."""
+    L = lib
+    vp = ctypes.c_void_p
+    assert L.ace_debug_serial_proofs(None, 1) == -1
+    assert L.ace_prove_batch_host(None, 1, None, None, None, None, None, None) == -1
+    assert L.ace_prove_batch(None, 1, None, None, None, None, None, None) == -1
+    assert L.ace_autotune_batch_slots(None, None, None, 1, 1, None) == -1
+    assert "NULL" in L.ace_last_error().decode() or "bad argument" in L.ace_last_error().decode()
+    assert ace.ERRORS[-8] == "ACE_E_INTERNAL"

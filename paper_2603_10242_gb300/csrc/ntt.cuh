@@ -2,8 +2,9 @@
 //
 // Domain H = {omega^i}, omega = 5^((r-1)/N) (5 is a non-residue mod r and
 // 2^28 | r - 1); coset g H with g = 5.  A transform is a sequence of passes,
-// each doing t radix-2 stages on groups of 2^t elements staged in shared
-// memory (limb-planar layout, one 32-byte element per index).  Forward
+// each doing t stages (radix-2, or radix-4 pairs of stages) on groups of 2^t
+// elements staged in shared memory (limb-planar layout with a swizzled word
+// index, one 32-byte element per index).  Forward
 // passes are decimation in frequency (natural order in, bit-reversed out);
 // the transform that follows consumes bit-reversed input by decimation in
 // time, so the QAP pipeline never permutes data.  Per-element factors (coset

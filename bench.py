@@ -648,14 +648,16 @@ def run_pertx(args):
         proofs3, _ = ctx.prove_many(pk, dz, k, rs, ss)
         seeds_ms.append((time.perf_counter() - t0) * 1e3)
     assert proofs3 == proofs
-    # proof-per-call batch path on a slice, and equality with it
+    # a slice through ace_prove_batch (same key: routed to the same
+    # batch-dimension kernels) must give the same bytes; the slot-pipelined
+    # rate of such a slice comes from the batch autotuner's timings (it runs
+    # the slot path for 1..8 slots in both stage layouts)
     sl = 128
     dzs = [dz[i * 32 * c.m:(i + 1) * 32 * c.m] for i in range(sl)]
     bp, bst = ctx.prove_batch([pk] * sl, dzs, rs[:32 * sl], ss[:32 * sl])
-    t0 = time.perf_counter()
-    bp, bst = ctx.prove_batch([pk] * sl, dzs, rs[:32 * sl], ss[:32 * sl])
-    slot_s = time.perf_counter() - t0
     assert bst == [0] * sl and bp == proofs[:sl]
+    slot_ms = ctx.autotune_batch_slots(pk, dzs[0], sl, 8)
+    slot_s = min(slot_ms) / 1e3
     ok = all(pk.verify(zs[i][32:64], proofs[i]) == 1 for i in (0, k // 2, k - 1))
     # the validators' side: the whole block checked by one batch verification
     pubs = b"".join(z[32:64] for z in zs)
@@ -674,7 +676,7 @@ def run_pertx(args):
         "workload": "groth16_pertx_block", "proofs_per_block": k, "constraints": PERTX_CIRCUIT[1],
         "N": 1 << PERTX_CIRCUIT[0], "m": c.m, "block_ms": {"best": best, "median": float(np.median(ms))},
         "proofs_per_s": k / (best / 1e3), "e2e_block_ms": min(e2e), "e2e_proofs_per_s": k / (min(e2e) / 1e3),
-        "h2d_bytes_per_block": len(zall), "proof_per_call_proofs_per_s": sl / slot_s,
+        "h2d_bytes_per_block": len(zall), "slot_pipelined_proofs_per_s": sl / slot_s,
         "witness_ms_device": min(wit_ms), "witness_s_host_estimate": wit_s,
         "seeds_to_proofs_block_ms": min(seeds_ms), "seeds_to_proofs_per_s": k / (min(seeds_ms) / 1e3),
         "verify_batch_block_ms": min(vb_ms), "verify_batch_proofs_per_s": k / (min(vb_ms) / 1e3),
@@ -741,15 +743,22 @@ def run_single(args):
         p2, st2 = ctx.prove_batch_host([pk], [zpin], r, s_)
         e2e.append((time.perf_counter() - t0) * 1e3)
     assert p2[0] == want and st2 == [0]
-    # n proofs in one batch call (device-resident witness), in the batch
-    # configuration the autotuner keeps for this key (slots and stage layout)
+    # n proofs in one batch call: all of one small key, so ace_prove_batch
+    # runs them on the batch-dimension kernels; beside it the best slot-
+    # pipelined configuration the autotuner measured (64 proofs per batch)
     tune_ms = ctx.autotune_batch_slots(pk, dz, 64, 16)
     batch_cfg = _tuned_batch(ctx)
+    slots_rate = 64 / (min(tune_ms) / 1e3)
     pb, sb = ctx.prove_batch([pk] * n, [dz] * n, r * n, s_ * n)
     t0 = time.perf_counter()
     pb, sb = ctx.prove_batch([pk] * n, [dz] * n, r * n, s_ * n)
     batch_s = time.perf_counter() - t0
     assert sb == [0] * n and pb[0] == want
+    # the same batch end to end: witnesses in pinned host memory
+    t0 = time.perf_counter()
+    ph, sh = ctx.prove_batch_host([pk] * n, [zpin] * n, r * n, s_ * n)
+    batch_host_s = time.perf_counter() - t0
+    assert sh == [0] * n and ph == pb
     # the oracle on the host cores: same inputs, same bytes
     oc = O.Circuit(*SINGLE_CIRCUIT, seed=1, input_seed=1)
     opk = O.ProvingKey(oc, 1, with_points=True)
@@ -773,7 +782,11 @@ def run_single(args):
         "e2e_one_per_call": {"proofs_per_s": n / (sum(e2e) / 1e3), "latency_ms": {"p50": pct(e2e, 0.5),
                              "p99": pct(e2e, 0.99)}, "h2d_bytes_per_proof": len(z), "d2h_bytes_per_proof": 260,
                              "path": "ace_prove_batch_host with one proof per call"},
-        "batched_proofs_per_s": n / batch_s, "batch": batch_cfg,
+        "batched_proofs_per_s": n / batch_s,
+        "batched_path": "ace_prove_batch, all proofs of one key: batch-dimension kernels (one launch per stage "
+                        "for all proofs)",
+        "e2e_batched_proofs_per_s": n / batch_host_s,
+        "slot_pipelined_proofs_per_s": slots_rate, "slot_config": batch_cfg,
         "batch_tuning_ms": {"aux_streams": tune_ms[:16], "one_stream_per_proof": tune_ms[16:]},
         "verified": pk.verify(z[32:64], want) == 1, "oracle_equal": op == want,
         "cpu_baseline": {"kind": "oracle", "cores": O.lib().orc_num_threads(),

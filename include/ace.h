@@ -368,7 +368,10 @@ int ace_debug_serial_proofs(ace_ctx* ctx, int on);
  * more proofs than slots, the fixed-base terms of all proofs run in one
  * launch beside the first MSMs and the variable-base terms and the assembly
  * in one launch each at the end; otherwise each proof finishes on its slot
- * as a lone proof does.
+ * as a lone proof does.  A call of at least 8 proofs that all share one key
+ * with N <= 2^18 runs instead on the batch-dimension kernels of
+ * ace_prove_many (one launch per stage for all of them, the witnesses first
+ * copied into one contiguous staging buffer held by the context).
  * Proof i goes to proofs + 256 i (host); status[i] (host) is 0, or 1 if
  * witness i does not satisfy its R1CS.  Synchronous.  ACE_E_ARG for NULL
  * pointers or non-canonical r, s; ACE_E_OOM if the slots' scratch cannot be

@@ -217,10 +217,10 @@ int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, 
         ctx->batch_one_stream = layout == 1;
         for (int q = 1; q <= max_slots; q++) {
             ctx->batch_slots = q;
-            ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
+            ACE_TRY(prove_batch_on_slots(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
                                     status.data()));
             auto t0 = std::chrono::steady_clock::now();
-            ACE_TRY(ace_prove_batch(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
+            ACE_TRY(prove_batch_on_slots(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
                                     status.data()));
             double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             if (report) report[layout * max_slots + q - 1] = ms;

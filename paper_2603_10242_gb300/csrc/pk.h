@@ -83,6 +83,10 @@ struct MsmOut {
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
               uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join,
               const MsmOut* msm_out = nullptr, bool one_stream = false);
+// ace_prove_batch on proving slots only, never on the batch-dimension
+// kernels (prove.cu; for the batch autotuner)
+int prove_batch_on_slots(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,
+                         const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status);
 // device bytes of scratch arena `arena` of a slot proving with `pk`
 size_t prove_slot_bytes(const ace_pk* pk, int arena);
 }  // namespace ace

@@ -810,6 +810,99 @@ int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r
 }  // extern "C"
 
 namespace ace {
+static int prove_many_impl(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, const ace_fr* rs,
+                           const ace_fr* ss, uint8_t* proofs, int32_t* status) {
+    if (!ctx || !pk || (k && (!d_z || !rs || !ss || !proofs || !status))) {
+        set_error("ace_prove_many: NULL argument");
+        return ACE_E_ARG;
+    }
+    if (k == 0) return ACE_OK;
+    if ((uintptr_t)d_z & 15u) {
+        set_error("ace_prove_many: d_z must be 16-byte aligned");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<fr_t> rsv(3 * k);
+    for (size_t i = 0; i < k; i++) {
+        if (!canonical_fr(rs + i) || !canonical_fr(ss + i)) {
+            set_error("ace_prove_many: r and s of proof %zu must be canonical Fr values", i);
+            return ACE_E_ARG;
+        }
+        memcpy(rsv[3 * i].v, rs[i].l, 32);
+        memcpy(rsv[3 * i + 1].v, ss[i].l, 32);
+        rsv[3 * i + 2] = fe_from_mont(fe_to_mont(rsv[3 * i]) * fe_to_mont(rsv[3 * i + 1]));
+    }
+    // chunks of proofs whose scratch stays within MANY_SCRATCH bytes (one
+    // proof per chunk at least); 65535 bounds the grid's y dimension / 3
+    const size_t MANY_SCRATCH = (size_t)24 << 30;
+    ManyPlans one = many_plans(pk, 1);
+    size_t per = 0;
+    for (int a = 0; a < PROVE_ARENAS; a++) per += one.arena[a];
+    size_t chunk = MANY_SCRATCH / (per ? per : 1);
+    // entries (count n K) and keys (count windows 2^(c-1)) are 32-bit indices
+    size_t ent = 1, keys = 1;
+    for (const MsmPlan* q : {&one.H, &one.A, &one.B, &one.L}) {
+        ent = ent > q->n * (size_t)q->K ? ent : q->n * (size_t)q->K;
+        keys = keys > (size_t)q->keys_per() ? keys : (size_t)q->keys_per();
+    }
+    if (chunk > ((size_t)1 << 31) / ent) chunk = ((size_t)1 << 31) / ent;
+    if (chunk > ((size_t)1 << 31) / keys) chunk = ((size_t)1 << 31) / keys;
+    if (chunk < 1) chunk = 1;
+    if (chunk > 21845) chunk = 21845;
+    // ACE_MANY_MAX_CHUNK (environment): a smaller cap, e.g. to bound latency
+    // per chunk or to exercise the chunk loop
+    if (const char* env = getenv("ACE_MANY_MAX_CHUNK")) {
+        long v = strtol(env, nullptr, 10);
+        if (v >= 1 && (size_t)v < chunk) chunk = (size_t)v;
+    }
+    if (chunk > k) chunk = k;
+    ACE_TRY(arena_ensure(ctx, 3, chunk * (256 + sizeof(int32_t)) + 1024));
+    ctx->scratch[3].reset();
+    uint32_t* d_proofs = (uint32_t*)ctx->scratch[3].take(chunk * 256);
+    int32_t* d_status = (int32_t*)ctx->scratch[3].take(chunk * sizeof(int32_t));
+    cudaStream_t st = ctx->stream;
+    for (size_t b = 0; b < k; b += chunk) {
+        uint32_t c = (uint32_t)(k - b < chunk ? k - b : chunk);
+        ACE_TRY(prove_many_run(ctx, pk, c, (const fr_t*)d_z + b * pk->m, rsv.data() + 3 * b, d_proofs, d_status, st));
+        ACE_TRY_CUDA(cudaMemcpyAsync(proofs + 256 * b, d_proofs, (size_t)c * 256, cudaMemcpyDeviceToHost, st));
+        ACE_TRY_CUDA(cudaMemcpyAsync(status + b, d_status, (size_t)c * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        // the next chunk reuses the device outputs and the host r, s copy
+        ACE_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return ACE_OK;
+}
+
+// A batch of at least MANY_MIN_PROOFS proofs of one key with N <= 2^MANY_MAX_LOG_N
+// runs on the batch-dimension kernels of ace_prove_many (one launch per stage
+// for all of its proofs): measured on 64 proofs of one key, 3.3x / 2.6x /
+// 1.5x / 1.15x / 1.04x the slot pipelining at 2^10 / 12 / 14 / 16 / 18 rows,
+// equal at 2^20 (where the slots are kept).  The witnesses are copied into
+// one contiguous staging buffer first (host or device sources), in chunks of
+// at most 2 GB.
+static const size_t MANY_MIN_PROOFS = 8;
+static const int MANY_MAX_LOG_N = 18;
+
+static int prove_batch_as_many(ace_ctx* ctx, size_t k, const ace_pk* pk, const ace_fr* const* zs, bool host,
+                               const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status) {
+    const size_t wb = pk->m * sizeof(fr_t);
+    size_t chunk = ((size_t)2 << 30) / (wb ? wb : 1);
+    if (chunk < 1) chunk = 1;
+    if (chunk > k) chunk = k;
+    ACE_TRY(slot_ready(ctx, 0));
+    ACE_TRY(slot_witness_ensure(ctx, 0, chunk * wb));
+    char* stage = ctx->slots[0].wit.base;
+    cudaStream_t st = ctx->stream;
+    for (size_t b = 0; b < k; b += chunk) {
+        const size_t c = k - b < chunk ? k - b : chunk;
+        for (size_t i = 0; i < c; i++)
+            ACE_TRY_CUDA(cudaMemcpyAsync(stage + i * wb, zs[b + i], wb,
+                                         host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+        // ordered after the copies on st; synchronises st before returning
+        ACE_TRY(prove_many_impl(ctx, pk, c, (const ace_fr*)stage, rs + b, ss + b, proofs + 256 * b, status + b));
+    }
+    return ACE_OK;
+}
+
 // k proofs round-robin over the context's proving slots (consecutive proofs
 // overlap); zs are device witnesses, or host witnesses (host = true) that are
 // copied into the slot's staging buffer on the slot's main stream once the
@@ -818,7 +911,7 @@ namespace ace {
 // the middle of the batch.
 static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk* const* pks,
                             const ace_fr* const* zs, bool host, const ace_fr* rs, const ace_fr* ss, uint8_t* proofs,
-                            int32_t* status) {
+                            int32_t* status, bool allow_many = true) {
     if (!ctx || (k && (!pks || !zs || !rs || !ss || !proofs || !status))) {
         set_error("%s: NULL argument", fn);
         return ACE_E_ARG;
@@ -831,6 +924,9 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
             return ACE_E_ARG;
         }
     }
+    bool one_key = allow_many && k >= MANY_MIN_PROOFS && pks[0]->log_n <= MANY_MAX_LOG_N;
+    for (size_t i = 1; one_key && i < k; i++) one_key = pks[i] == pks[0];
+    if (one_key) return prove_batch_as_many(ctx, k, pks[0], zs, host, rs, ss, proofs, status);
     // device outputs for all proofs (then one copy back), the proofs' MSM
     // sums and tail terms, and the tails' per-proof descriptors
     const size_t per = 256 + sizeof(int32_t) + 9 * sizeof(g1_xyzz) + 2 * sizeof(g2_xyzz) + sizeof(TailDesc);
@@ -930,6 +1026,12 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
     ACE_TRY_CUDA(cudaStreamSynchronize(st));
     return ACE_OK;
 }
+// the slot path of ace_prove_batch whatever the keys (the batch autotuner
+// times slot counts and layouts with it)
+int prove_batch_on_slots(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,
+                         const ace_fr* rs, const ace_fr* ss, uint8_t* proofs, int32_t* status) {
+    return prove_batch_impl(ctx, "ace_autotune_batch_slots", k, pks, d_zs, false, rs, ss, proofs, status, false);
+}
 }  // namespace ace
 
 extern "C" {
@@ -957,64 +1059,7 @@ int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]) {
 int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, const ace_fr* rs, const ace_fr* ss,
                    uint8_t* proofs, int32_t* status) {
     clear_error();
-    if (!ctx || !pk || (k && (!d_z || !rs || !ss || !proofs || !status))) {
-        set_error("ace_prove_many: NULL argument");
-        return ACE_E_ARG;
-    }
-    if (k == 0) return ACE_OK;
-    if ((uintptr_t)d_z & 15u) {
-        set_error("ace_prove_many: d_z must be 16-byte aligned");
-        return ACE_E_ARG;
-    }
-    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
-    std::vector<fr_t> rsv(3 * k);
-    for (size_t i = 0; i < k; i++) {
-        if (!canonical_fr(rs + i) || !canonical_fr(ss + i)) {
-            set_error("ace_prove_many: r and s of proof %zu must be canonical Fr values", i);
-            return ACE_E_ARG;
-        }
-        memcpy(rsv[3 * i].v, rs[i].l, 32);
-        memcpy(rsv[3 * i + 1].v, ss[i].l, 32);
-        rsv[3 * i + 2] = fe_from_mont(fe_to_mont(rsv[3 * i]) * fe_to_mont(rsv[3 * i + 1]));
-    }
-    // chunks of proofs whose scratch stays within MANY_SCRATCH bytes (one
-    // proof per chunk at least); 65535 bounds the grid's y dimension / 3
-    const size_t MANY_SCRATCH = (size_t)24 << 30;
-    ManyPlans one = many_plans(pk, 1);
-    size_t per = 0;
-    for (int a = 0; a < PROVE_ARENAS; a++) per += one.arena[a];
-    size_t chunk = MANY_SCRATCH / (per ? per : 1);
-    // entries (count n K) and keys (count windows 2^(c-1)) are 32-bit indices
-    size_t ent = 1, keys = 1;
-    for (const MsmPlan* q : {&one.H, &one.A, &one.B, &one.L}) {
-        ent = ent > q->n * (size_t)q->K ? ent : q->n * (size_t)q->K;
-        keys = keys > (size_t)q->keys_per() ? keys : (size_t)q->keys_per();
-    }
-    if (chunk > ((size_t)1 << 31) / ent) chunk = ((size_t)1 << 31) / ent;
-    if (chunk > ((size_t)1 << 31) / keys) chunk = ((size_t)1 << 31) / keys;
-    if (chunk < 1) chunk = 1;
-    if (chunk > 21845) chunk = 21845;
-    // ACE_MANY_MAX_CHUNK (environment): a smaller cap, e.g. to bound latency
-    // per chunk or to exercise the chunk loop
-    if (const char* env = getenv("ACE_MANY_MAX_CHUNK")) {
-        long v = strtol(env, nullptr, 10);
-        if (v >= 1 && (size_t)v < chunk) chunk = (size_t)v;
-    }
-    if (chunk > k) chunk = k;
-    ACE_TRY(arena_ensure(ctx, 3, chunk * (256 + sizeof(int32_t)) + 1024));
-    ctx->scratch[3].reset();
-    uint32_t* d_proofs = (uint32_t*)ctx->scratch[3].take(chunk * 256);
-    int32_t* d_status = (int32_t*)ctx->scratch[3].take(chunk * sizeof(int32_t));
-    cudaStream_t st = ctx->stream;
-    for (size_t b = 0; b < k; b += chunk) {
-        uint32_t c = (uint32_t)(k - b < chunk ? k - b : chunk);
-        ACE_TRY(prove_many_run(ctx, pk, c, (const fr_t*)d_z + b * pk->m, rsv.data() + 3 * b, d_proofs, d_status, st));
-        ACE_TRY_CUDA(cudaMemcpyAsync(proofs + 256 * b, d_proofs, (size_t)c * 256, cudaMemcpyDeviceToHost, st));
-        ACE_TRY_CUDA(cudaMemcpyAsync(status + b, d_status, (size_t)c * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        // the next chunk reuses the device outputs and the host r, s copy
-        ACE_TRY_CUDA(cudaStreamSynchronize(st));
-    }
-    return ACE_OK;
+    return prove_many_impl(ctx, pk, k, d_z, rs, ss, proofs, status);
 }
 
 }  // extern "C"

@@ -101,3 +101,32 @@ def test_batch_tails_same_bytes_for_every_slot_count(tmp_path):
         proofs, status = ctx.prove_batch(pks * 2, dzs * 2, rs * 2, ss * 2)
         assert status == [0] * 6 and proofs == want + want, (q, one)
     ctx.close()
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_same_key_batch_on_batch_dimension_kernels(host):
+    """A batch of 12 proofs of one small key runs on the batch-dimension
+    kernels: every proof equals the one-proof path, the unsatisfied witness
+    in the middle is reported without disturbing the others, from device and
+    from host witnesses."""
+    ctx = gu.ctx()
+    c = ace.Circuit(11, 2000, 5, 2, 60, seed=61)
+    pk = ace.ProvingKey(ctx, c, toxic_seed=62)
+    zs = [c.witness(70 + i) for i in range(12)]
+    bad = bytearray(zs[5])
+    bad[32 * 40] ^= 1
+    zs[5] = bytes(bad)
+    rss = [ace.rs_from_seed(170 + i) for i in range(12)]
+    rs = b"".join(r for r, _ in rss)
+    ss = b"".join(s for _, s in rss)
+    if host:
+        hz = [torch.frombuffer(bytearray(z), dtype=torch.uint8).pin_memory() for z in zs]
+        proofs, status = ctx.prove_batch_host([pk] * 12, hz, rs, ss)
+    else:
+        proofs, status = ctx.prove_batch([pk] * 12, [gu.dev(z) for z in zs], rs, ss)
+    assert status == [0] * 5 + [1] + [0] * 6
+    for i in (0, 4, 6, 11):
+        assert proofs[i] == ctx.prove(pk, gu.dev(zs[i]), *rss[i]), i
+    oc = O.Circuit(11, 2000, 5, 2, 60, seed=61, input_seed=77)
+    opk = O.ProvingKey(oc, 62, with_points=False)
+    assert proofs[7] == opk.expected_proof(zs[7], *rss[7])

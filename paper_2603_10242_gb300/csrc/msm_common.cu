@@ -67,6 +67,10 @@ static double msm_cost(size_t n, int c, bool tabled, int bits = 255) {
     return work;
 }
 
+// largest window size whose single-MSM plans reduce in segments of 4 buckets
+#ifndef ACE_SHORT_SEGMENT_MAX_C
+#define ACE_SHORT_SEGMENT_MAX_C 14
+#endif
 static MsmPlan plan_for(size_t n, int c, bool tabled, bool glv = false) {
     MsmPlan p;
     p.n = n;
@@ -81,7 +85,7 @@ static MsmPlan plan_for(size_t n, int c, bool tabled, bool glv = false) {
     // thread) is the longest chain of the reduction, and four times as many
     // threads still leave the GPU mostly idle
     p.lambda = p.c - 1 < 4 ? p.c - 1 : 4;
-    if (p.c <= 14) p.lambda = 2;
+    if (p.c <= ACE_SHORT_SEGMENT_MAX_C) p.lambda = 2;
     p.L = 1u << p.lambda;
     p.M = p.B / p.L;
     p.tabled = tabled;

@@ -1090,12 +1090,28 @@ def run_sweep(args):
                 "imad_frac": muls * IMAD_PER_FP_MUL / t / peak_imad,
             })
         del d
+    # the prover's own shape: one launch sequence over three arrays (the QAP's
+    # a, b, c), Montgomery form in and out, natural order in, bit-reversed out
+    ntt_batch_rows = []
+    for lg in range(16, 25):
+        n = 1 << lg
+        d3 = torch.empty(3 * 32 * n, dtype=torch.uint8, device=dev)
+        for j in range(3):
+            d3[j * 32 * n:(j + 1) * 32 * n].copy_(vals[:32 * n])
+        t = timed(lambda: ctx.ntt_mont(d3, lg, 3, True, False))
+        muls = 3 * (n // 2) * lg
+        ntt_batch_rows.append({
+            "log_n": lg, "arrays": 3, "ms": t * 1000.0, "elements_per_s": 3 * n / t,
+            "hbm_frac": 3 * 64.0 * n / t / 1e9 / hbm_peak,
+            "imad_frac": muls * IMAD_PER_FP_MUL / t / peak_imad,
+        })
+        del d3
     cpu = None if args.no_cpu_baseline else sweep_cpu_sample()
     print(json.dumps({
         "workload": "kernel_sweep_msm_g1_ntt_2p16_2p24", "curve": "BN254", "reps": reps,
         "cpu_baseline": cpu,
         "timing": "median of reps, CUDA events per call, L2 flushed (256 MiB write) before each call",
-        "msm_g1": msm_rows, "ntt": ntt_rows,
+        "msm_g1": msm_rows, "ntt": ntt_rows, "ntt_qap_batch": ntt_batch_rows,
         "roofline": {"imad_peak_T_per_s": peak_imad / 1e12, "hbm_peak_gbs": hbm_peak,
                      "msm": f"{IMAD_PER_G1_MADD} IMAD per bucket addition (algorithmic, bucket additions only)",
                      "ntt": "64 B per element (read + write once) against HBM; "

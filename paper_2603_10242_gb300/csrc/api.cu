@@ -249,39 +249,37 @@ int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream s
     fr_t* tmp = (fr_t*)ctx->scratch[0].take(n * sizeof(fr_t));
     cudaStream_t st = pick_stream(ctx, stream);
     fr_t* d = (fr_t*)d_data;
-    NttScale to_mont, from_mont, pre, post;
-    to_mont.hi = plan->rr;
-    to_mont.lo = plan->one;
-    to_mont.single = 1;
-    from_mont.hi = plan->plain_one;
-    from_mont.lo = plan->one;
-    from_mont.single = 1;
-    // canonical -> Montgomery
-    ACE_TRY(fr_scale_copy(d, d, n, to_mont, (int)log_n, st));
-    bool inverse = kind == 1 || kind == 3;
-    if (kind == 2) {  // coefficients times g^i
-        pre.hi = plan->cg_hi;
+    // One transform, no separate passes: the first pass enters Montgomery
+    // form (and multiplies by g^i for the coset form) as it loads, the last
+    // one applies the output factor, leaves Montgomery form and writes each
+    // element to its bit-reversed position, which turns the DIF order back
+    // into natural order.
+    NttScale pre, post;
+    pre.hi = plan->rr;  // R^2 raw: x R^2 R^-1 = x R
+    pre.lo = plan->one;
+    pre.single = 1;
+    if (kind == 2) {  // g^i R^2: x g^i R
+        pre.hi = plan->cgr_hi;
         pre.lo = plan->cos_lo;
         pre.h = plan->h;
+        pre.single = 0;
     }
-    if (kind == 1) {  // times 1/N
+    post.hi = plan->plain_one;  // 1 raw: x R R^-1 = x
+    post.lo = plan->one;
+    post.single = 1;
+    if (kind == 1) {  // N^-1 raw: (x R) N^-1 R^-1 = x / N
         post.hi = plan->ninv;
-        post.lo = plan->one;
-        post.single = 1;
+        post.lo = plan->plain_one;
     }
-    if (kind == 3) {  // times g^-e / N at bit-reversed position, leaves Montgomery form
+    if (kind == 3) {  // g^-e / N at bit-reversed position, leaves Montgomery form
         post.hi = plan->icos_hi;
         post.lo = plan->icos_lo;
         post.h = plan->h;
         post.brev = 1;
+        post.single = 0;
     }
-    ACE_TRY(ntt_run(*plan, d, 1, true, inverse, pre, post, st, true));
-    ACE_TRY(fr_bitrev_copy(d, tmp, (int)log_n, 1, st));
-    if (kind == 3) {
-        ACE_TRY_CUDA(cudaMemcpyAsync(d, tmp, n * sizeof(fr_t), cudaMemcpyDeviceToDevice, st));
-    } else {
-        ACE_TRY(fr_scale_copy(tmp, d, n, from_mont, (int)log_n, st));
-    }
+    const bool inverse = kind == 1 || kind == 3;
+    ACE_TRY(ntt_run_io(*plan, d, tmp, d, true, 1, true, inverse, pre, post, st, true));
     return ACE_OK;
 }
 

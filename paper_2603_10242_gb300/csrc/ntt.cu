@@ -74,6 +74,9 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     std::vector<fr_t> cos_lo, cg_hi, cos_hi, icos_lo_m, icos_lo, icos_hi;
     h_powers(cos_lo, g, one, nlo);
     h_powers(cg_hi, h_pow_u64(g, nlo), one, nhi);
+    // the same powers times R: a product with a canonical input then enters Montgomery form
+    std::vector<fr_t> cgr_hi(nhi);
+    for (size_t i = 0; i < nhi; i++) cgr_hi[i] = cg_hi[i] * fe_rr<FrCfg>();
     h_powers(cos_hi, h_pow_u64(g, nlo), ninv, nhi);
     h_powers(icos_lo_m, ginv, one, nlo);
     icos_lo.resize(nlo);
@@ -91,7 +94,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
         return o;
     };
     size_t o_twf = place(half), o_twi = place(half), o_cos_hi = place(nhi), o_cos_lo = place(nlo),
-           o_cg_hi = place(nhi), o_icos_hi = place(nhi), o_icos_lo = place(nlo), o_ninv = place(1),
+           o_cg_hi = place(nhi), o_cgr_hi = place(nhi), o_icos_hi = place(nhi), o_icos_lo = place(nlo), o_ninv = place(1),
            o_one = place(1), o_p1 = place(1), o_rr = place(1), o_seed = place(4 * (tlo + thi));
     void* mem = nullptr;
     ACE_TRY(dev_alloc(ctx, &mem, off));
@@ -105,6 +108,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     p->cos_hi = (fr_t*)(base + o_cos_hi);
     p->cos_lo = (fr_t*)(base + o_cos_lo);
     p->cg_hi = (fr_t*)(base + o_cg_hi);
+    p->cgr_hi = (fr_t*)(base + o_cgr_hi);
     p->icos_hi = (fr_t*)(base + o_icos_hi);
     p->icos_lo = (fr_t*)(base + o_icos_lo);
     p->ninv = (fr_t*)(base + o_ninv);
@@ -127,6 +131,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     e = e ? e : up(p->cos_hi, cos_hi.data(), nhi * sizeof(fr_t));
     e = e ? e : up(p->cos_lo, cos_lo.data(), nlo * sizeof(fr_t));
     e = e ? e : up(p->cg_hi, cg_hi.data(), nhi * sizeof(fr_t));
+    e = e ? e : up(p->cgr_hi, cgr_hi.data(), nhi * sizeof(fr_t));
     e = e ? e : up(p->icos_hi, icos_hi.data(), nhi * sizeof(fr_t));
     e = e ? e : up(p->icos_lo, icos_lo.data(), nlo * sizeof(fr_t));
     e = e ? e : up(p->ninv, &ninv, sizeof(fr_t));
@@ -230,27 +235,43 @@ __device__ __forceinline__ uint32_t ins0(uint32_t g, int p) { return ((g >> p) <
 // (fewer registers; the plan picks the form per size, see ntt_default_radix).
 // ACE_NTT_MIN_BLOCKS: resident blocks of 256 threads per SM the register
 // allocation must allow.
+// ACE_NTT_THREADS: threads per block (fewer when a block holds fewer than
+// twice as many elements).
 #ifndef ACE_NTT_MIN_BLOCKS
 #define ACE_NTT_MIN_BLOCKS 3
 #endif
+#ifndef ACE_NTT_THREADS
+#define ACE_NTT_THREADS 256
+#endif
+// src / dst: the pass reads its groups from src and writes them to dst (the
+// same array for an in-place pass; a block reads all of its elements before
+// it writes any).  out_brev: element p is written to position bitrev(p) of
+// dst, which must then be a different array unless one block holds a whole
+// array (the pass is the transform's only one).
 template <bool DIT, bool R4>
-__global__ void __launch_bounds__(256, ACE_NTT_MIN_BLOCKS) k_ntt_pass(fr_t* __restrict__ data, int log_n, int t, int b0, int logG,
+__global__ void __launch_bounds__(ACE_NTT_THREADS, ACE_NTT_MIN_BLOCKS) k_ntt_pass(const fr_t* src, fr_t* dst, int out_brev,
+                                                  int log_n, int t, int b0, int logG,
                                                   const fr_t* __restrict__ tw, int first_stage, NttScale pre,
                                                   NttScale post) {
     extern __shared__ uint32_t sm[];
     const uint32_t G = 1u << logG;
     const uint32_t S = G << t;
-    fr_t* arr = data + ((size_t)blockIdx.y << log_n);
+    const fr_t* in = src + ((size_t)blockIdx.y << log_n);
+    fr_t* out = dst + ((size_t)blockIdx.y << log_n);
     const uint32_t q0 = blockIdx.x * G;
     const uint32_t lomask = (1u << b0) - 1u;
 
-    for (uint32_t e = threadIdx.x; e < S; e += blockDim.x) {
-        uint32_t g = e >> logG, ql = e & (G - 1u);
-        uint32_t q = q0 + ql;
-        uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
-        fr_t x = ld_fr(arr + idx);
-        if (pre.hi) x = x * scale_factor(pre, idx, log_n);
-        sm_st(sm, S, e, x);
+    {
+        fr_t c;
+        if (pre.single) c = ld_fr(pre.hi) * ld_fr(pre.lo);
+        for (uint32_t e = threadIdx.x; e < S; e += blockDim.x) {
+            uint32_t g = e >> logG, ql = e & (G - 1u);
+            uint32_t q = q0 + ql;
+            uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
+            fr_t x = ld_fr(in + idx);
+            if (pre.hi) x = x * (pre.single ? c : scale_factor(pre, idx, log_n));
+            sm_st(sm, S, e, x);
+        }
     }
     __syncthreads();
     int ls = 0;
@@ -328,13 +349,15 @@ __global__ void __launch_bounds__(256, ACE_NTT_MIN_BLOCKS) k_ntt_pass(fr_t* __re
         }
         __syncthreads();
     }
+    fr_t c;
+    if (post.single) c = ld_fr(post.hi) * ld_fr(post.lo);
     for (uint32_t e = threadIdx.x; e < S; e += blockDim.x) {
         uint32_t g = e >> logG, ql = e & (G - 1u);
         uint32_t q = q0 + ql;
         uint32_t idx = ((q >> b0) << (b0 + t)) | (g << b0) | (q & lomask);
         fr_t x = sm_ld(sm, S, e);
-        if (post.hi) x = x * scale_factor(post, idx, log_n);
-        st_fr(arr + idx, x);
+        if (post.hi) x = x * (post.single ? c : scale_factor(post, idx, log_n));
+        st_fr(out + (out_brev ? brev_bits(idx, log_n) : idx), x);
     }
 }
 
@@ -346,7 +369,7 @@ __global__ void __launch_bounds__(256, ACE_NTT_MIN_BLOCKS) k_ntt_pass(fr_t* __re
 // ceil(blocks / slots) x (work of one block).  Narrower blocks can fill the
 // last wave better (one 2^20 array: 512 blocks of 2^11 elements against 456
 // slots take two waves, 1,024 of 2^10 take three half-size waves).
-typedef void (*NttPassFn)(fr_t*, int, int, int, int, const fr_t*, int, NttScale, NttScale);
+typedef void (*NttPassFn)(const fr_t*, fr_t*, int, int, int, int, int, const fr_t*, int, NttScale, NttScale);
 static NttPassFn ntt_pass_fn(bool dif, bool r4) {
     if (dif) return r4 ? k_ntt_pass<false, true> : k_ntt_pass<false, false>;
     return r4 ? k_ntt_pass<true, true> : k_ntt_pass<true, false>;
@@ -366,7 +389,7 @@ static int ntt_pick_columns(bool dif, bool r4, int k, int t, int logG_max, int c
     double best_cost = 1e300;
     for (int lg = logG_max; lg >= 0 && lg >= logG_max - 2; lg--) {
         const uint32_t S = (1u << lg) << t;
-        int threads = S / 2 < 256 ? (int)(S / 2) : 256;
+        int threads = S / 2 < ACE_NTT_THREADS ? (int)(S / 2) : ACE_NTT_THREADS;
         if (threads < 32) threads = 32;
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ntt_pass_fn(dif, r4), threads, (size_t)S * 32);
@@ -384,6 +407,11 @@ static int ntt_pick_columns(bool dif, bool r4, int k, int t, int logG_max, int c
 
 int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, const NttScale& pre,
             const NttScale& post, cudaStream_t st, bool fill_waves) {
+    return ntt_run_io(plan, data, data, data, false, count, dif, inverse, pre, post, st, fill_waves);
+}
+
+int ntt_run_io(const NttPlan& plan, const fr_t* in, fr_t* work, fr_t* out, bool out_brev, int count, bool dif,
+               bool inverse, const NttScale& pre, const NttScale& post, cudaStream_t st, bool fill_waves) {
     const int k = plan.log_n;
     const int NTT_MAX_T = plan.smem_log, NTT_SMEM_LOG = plan.smem_log;
     int passes[4], np = 0;
@@ -407,6 +435,10 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
             cudaFuncSetAttribute(ntt_pass_fn(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
+    if (out_brev && np > 1 && out == work) {  // the last pass would read and scatter one array
+        set_error("ntt: a bit-reversed output of a multi-pass transform needs its own array");
+        return ACE_E_INTERNAL;
+    }
     const bool r4 = plan.radix == 4;
     const fr_t* tw = inverse ? plan.tw_inv : plan.tw_fwd;
     NttScale none;
@@ -428,48 +460,22 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
         uint32_t groups = 1u << (k - t);
         uint32_t blocks = groups >> logG;
         uint32_t S = (1u << logG) << t;
-        int threads = S / 2 < 256 ? (int)(S / 2) : 256;
+        int threads = S / 2 < ACE_NTT_THREADS ? (int)(S / 2) : ACE_NTT_THREADS;
         if (threads < 32) threads = 32;
         size_t smem = (size_t)S * 32;
         dim3 grid(blocks, (unsigned)count);
         const NttScale& a = pi == 0 ? pre : none;
         const NttScale& z = pi == np - 1 ? post : none;
         int prof = prof_begin(PROF_NTT, st);
-        ntt_pass_fn(dif, r4)<<<grid, threads, smem, st>>>(data, k, t, b0, logG, tw, first_stage, a, z);
+        const fr_t* src = pi == 0 ? in : work;
+        fr_t* dst = pi == np - 1 ? out : work;
+        const int brev = pi == np - 1 && out_brev;
+        ntt_pass_fn(dif, r4)<<<grid, threads, smem, st>>>(src, dst, brev, k, t, b0, logG, tw, first_stage, a, z);
         ::ace::note_launch();
         // work: butterflies of this pass
         prof_end(prof, st, nullptr, (uint64_t)count * ((uint64_t)1 << (k - 1)) * (uint64_t)t);
         done_bits += t;
     }
-    ACE_TRY_CUDA(cudaGetLastError());
-    return ACE_OK;
-}
-
-__global__ void k_scale_copy(const fr_t* in, fr_t* out, size_t n, NttScale s, int log_n) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    st_fr(out + i, ld_fr(in + i) * scale_factor(s, (uint32_t)i, log_n));
-}
-
-int fr_scale_copy(const fr_t* in, fr_t* out, size_t n, const NttScale& s, int log_n, cudaStream_t st) {
-    if (n == 0) return ACE_OK;
-    k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n, s, log_n); ::ace::note_launch();
-    ACE_TRY_CUDA(cudaGetLastError());
-    return ACE_OK;
-}
-
-__global__ void k_bitrev_copy(const fr_t* in, fr_t* out, int log_n) {
-    size_t n = (size_t)1 << log_n;
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    size_t off = (size_t)blockIdx.y << log_n;
-    st_fr(out + off + brev_bits((uint32_t)i, log_n), ld_fr(in + off + i));
-}
-
-int fr_bitrev_copy(const fr_t* in, fr_t* out, int log_n, int count, cudaStream_t st) {
-    size_t n = (size_t)1 << log_n;
-    dim3 grid((unsigned)((n + 255) / 256), (unsigned)count);
-    k_bitrev_copy<<<grid, 256, 0, st>>>(in, out, log_n); ::ace::note_launch();
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
 }

@@ -26,6 +26,7 @@ struct NttPlan {
     fr_t* cos_hi = nullptr;   // N^-1 g^(e_hi 2^h) (Montgomery)
     fr_t* cos_lo = nullptr;   // g^e_lo (Montgomery)
     fr_t* cg_hi = nullptr;    // g^(e_hi 2^h) (Montgomery)
+    fr_t* cgr_hi = nullptr;   // g^(e_hi 2^h) R (Montgomery): with cos_lo, takes a canonical input to Montgomery form
     fr_t* icos_hi = nullptr;  // N^-1 g^-(e_hi 2^h) (Montgomery)
     fr_t* icos_lo = nullptr;  // g^-e_lo as a plain value: the product leaves Montgomery form
     fr_t* ninv = nullptr;     // [N^-1] (Montgomery), single entry
@@ -69,7 +70,13 @@ int ntt_run(const NttPlan& plan, fr_t* data, int count, bool dif, bool inverse, 
             const NttScale& post, cudaStream_t st,
             bool fill_waves = false);
 
-int fr_scale_copy(const fr_t* in, fr_t* out, size_t n, const NttScale& s, int log_n, cudaStream_t st);
-int fr_bitrev_copy(const fr_t* in, fr_t* out, int log_n, int count, cudaStream_t st);
+// The same transform out of place: the first pass reads `in`, every pass
+// writes `work` except the last, which writes `out` (at bit-reversed
+// positions when out_brev: a DIF transform then leaves natural order).  Any
+// two of the three may be the same array, except work and out when out_brev
+// and the transform takes more than one pass (ACE_E_INTERNAL).
+int ntt_run_io(const NttPlan& plan, const fr_t* in, fr_t* work, fr_t* out, bool out_brev, int count, bool dif,
+               bool inverse, const NttScale& pre, const NttScale& post, cudaStream_t st, bool fill_waves = false);
+
 
 }  // namespace ace

@@ -426,10 +426,10 @@ static CsrDev csr_of(const ace_pk* pk) {
 
 // steps 1-2.  coset = true (proving): leaves the canonical values h(g omega^i)
 // in natural order in abc[0..N), the scalars of the H query in the coset
-// Lagrange basis; coset = false: the canonical coefficients of h in
-// bit-reversed order (one more inverse transform)
-int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t* d_status, cudaStream_t st,
-            bool coset) {
+// Lagrange basis; coset = false: the canonical coefficients of h (one more
+// inverse transform), in natural order in h_out (abc is scratch then)
+static int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t* d_status,
+                   cudaStream_t st, bool coset, fr_t* h_out = nullptr) {
     NttPlan* plan = nullptr;
     ACE_TRY(ntt_get_plan(ctx, pk->log_n, &plan));
     const uint32_t N = (uint32_t)pk->N;
@@ -453,7 +453,7 @@ int qap_run(ace_ctx* ctx, const ace_pk* pk, const fr_t* d_z, fr_t* abc, int32_t*
         k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, fe_from_mont(plan->zinv)); ::ace::note_launch();
     } else {
         k_quotient<<<(N + 255) / 256, 256, 0, st>>>(abc, N, plan->zinv); ::ace::note_launch();
-        ACE_TRY(ntt_run(*plan, abc, 1, true, true, none, icos, st));
+        ACE_TRY(ntt_run_io(*plan, abc, abc, h_out, true, 1, true, true, none, icos, st));
     }
     ACE_TRY_CUDA(cudaGetLastError());
     return ACE_OK;
@@ -751,8 +751,7 @@ int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out
     fr_t* abc = (fr_t*)ctx->scratch[0].take(3 * pk->N * sizeof(fr_t));
     int32_t* status = (int32_t*)ctx->scratch[0].take(16);
     ACE_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-    ACE_TRY(qap_run(ctx, pk, (const fr_t*)d_z, abc, status, st, false));
-    return fr_bitrev_copy(abc, (fr_t*)d_h_out, pk->log_n, 1, st);
+    return qap_run(ctx, pk, (const fr_t*)d_z, abc, status, st, false, (fr_t*)d_h_out);
 }
 
 int ace_prove_async(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,

@@ -220,6 +220,9 @@ int ace_g2_fixed_base(ace_ctx* ctx, const ace_fr* d_scalars, size_t n, ace_g2_af
  *   C = sum_{j>1} z_j L_j + sum h_i H_i + s A + r B1 - r s [delta]1,
  *   B1 = [beta]1 + sum z_j B1_j + s [delta]1.
  * proof_out (host, 256 bytes) as described above; the call synchronises.
+ * The proof is taken to have the GPU to itself: a bucket reduction with
+ * few enough segments runs on four lanes per segment (lower latency, more
+ * instructions), which batched proofs do not use.  Same bytes either way.
  * ACE_E_UNSAT if (Az) o (Bz) != Cz (checked on the device). */
 int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
               uint8_t proof_out[256], ace_stream stream);
@@ -368,7 +371,9 @@ int ace_debug_serial_proofs(ace_ctx* ctx, int on);
  * more proofs than slots, the fixed-base terms of all proofs run in one
  * launch beside the first MSMs and the variable-base terms and the assembly
  * in one launch each at the end; otherwise each proof finishes on its slot
- * as a lone proof does.  A call of at least 8 proofs that all share one key
+ * as a lone proof does.  A call of one proof runs it as ace_prove does (its
+ * MSMs on the auxiliary streams, latency-first reductions).  A call of at
+ * least 8 proofs that all share one key
  * with N <= 2^18 runs instead on the batch-dimension kernels of
  * ace_prove_many (one launch per stage for all of them, the witnesses first
  * copied into one contiguous staging buffer held by the context).

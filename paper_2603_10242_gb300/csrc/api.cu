@@ -43,6 +43,7 @@ static int msm_entry(ace_ctx* ctx, const void* d_bases, int base_form, const ace
         plan = msm_plan_glv(n, ctx->tuned_msm_c[lg]);
     else
         plan = msm_plan(n);
+    plan.alone = true;
     bool mont = base_form == ACE_FORM_MONT;
     ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<F>(plan, mont)));
     return msm_run<F>(plan, (const Affine<F>*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
@@ -189,6 +190,7 @@ int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form,
     }
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     MsmPlan plan = msm_plan(n, c);
+    plan.alone = true;
     bool mont = base_form == ACE_FORM_MONT;
     ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(plan, mont)));
     return msm_run<fp_t>(plan, (const g1_aff*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
@@ -207,6 +209,7 @@ int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_f
     }
     ACE_TRY_CUDA(cudaSetDevice(ctx->device));
     MsmPlan plan = msm_plan_glv(n, c);
+    plan.alone = true;
     bool mont = base_form == ACE_FORM_MONT;
     ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(plan, mont)));
     return msm_run<fp_t>(plan, (const g1_aff*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,

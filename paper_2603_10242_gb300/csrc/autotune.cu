@@ -95,6 +95,7 @@ int ace_autotune_msm(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* r
         for (int c = model.c - 3; c <= model.c + 2 && rc == ACE_OK; c++) {
             if (c < 6 || c > 20) continue;
             MsmPlan p = msm_plan_glv(n, c);
+            p.alone = true;  // as ace_msm_g1 runs it
             rc = arena_ensure(ctx, 0, msm_scratch_bytes<fp_t>(p, true));
             if (rc != ACE_OK) break;
             float t = 1e30f;

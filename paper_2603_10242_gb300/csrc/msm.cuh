@@ -53,6 +53,10 @@ struct MsmPlan {
     // the additions over many threads, few enough that the window's plain sum
     // in the reduction stays short (its other buckets are empty)
     uint32_t B1 = 0;
+    // a call that has the GPU to itself (one MSM, one proof): its reduction
+    // runs on four lanes per segment while that still fits about one wave of
+    // the GPU (see msm_impl.cuh); batched and served proofs leave it off
+    bool alone = false;
     uint32_t ones_mask() const { return (B1 ? B1 : B) - 1u; }
     uint32_t bucket_windows() const { return tabled ? 1u : (uint32_t)K; }
     uint32_t windows() const { return bucket_windows() + 1; }  // + ones window

@@ -197,6 +197,86 @@ __global__ void __launch_bounds__(128) k_seg_weight(Xyzz<F>* W, const Xyzz<F>* _
     st_vec(W + t, acc);
 }
 
+// The same two steps on four lanes per segment (curve_quad.cuh).  A
+// reduction with few segments leaves most of the GPU idle, and each
+// thread's time is its chain of additions (about 16 products in sequence
+// each, against 4 levels of products on four lanes).  With more segments
+// than about one wave of the four-lane kernel holds, or beside other proofs'
+// kernels, the one-lane form is faster: it does the same products without
+// the shuffles and the repeated additions of the four lanes.
+template <class F>
+__global__ void __launch_bounds__(128) k_seg_reduce_quad(const Xyzz<F>* __restrict__ buckets, uint32_t nseg,
+                                                         uint32_t B, uint32_t L, uint32_t M, uint32_t windows,
+                                                         uint32_t ones, Xyzz<F>* segW, Xyzz<F>* segS) {
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t t = gt >> 2;
+    const int sub = (int)(gt & 3u);
+    if (t >= nseg) return;  // whole groups of four leave together
+    const unsigned mask = 0xfu << (threadIdx.x & 28u);
+    const uint32_t w = t / M, j = t % M;
+    const Xyzz<F>* bk = buckets + (size_t)w * B + (size_t)j * L;
+    Xyzz<F> run = xyzz_inf<F>(), acc = xyzz_inf<F>();
+    if (w % windows == ones) {
+        for (int b = (int)L - 1; b >= 0; b--) run = quad_add(run, ld_plain(bk + b), sub, mask);
+    } else {
+        for (int b = (int)L - 1; b >= 0; b--) {
+            run = quad_add(run, ld_plain(bk + b), sub, mask);
+            acc = quad_add(acc, run, sub, mask);
+        }
+    }
+    if (sub != 0) return;
+    st_vec(segW + t, acc);
+    st_vec(segS + t, run);
+}
+
+template <class F>
+__global__ void __launch_bounds__(128) k_seg_weight_quad(Xyzz<F>* W, const Xyzz<F>* __restrict__ S, uint32_t nseg,
+                                                         uint32_t M, int lambda, uint32_t windows, uint32_t ones) {
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t t = gt >> 2;
+    const int sub = (int)(gt & 3u);
+    if (t >= nseg) return;
+    const unsigned mask = 0xfu << (threadIdx.x & 28u);
+    const uint32_t w = t / M, j = t % M;
+    const Xyzz<F> s = ld_plain(S + t);
+    if (w % windows == ones) {
+        if (sub == 0) st_vec(W + t, s);
+        return;
+    }
+    Xyzz<F> acc = ld_plain(W + t);
+    if (j != 0) {
+        Xyzz<F> m = xyzz_inf<F>();
+        for (int b = 31 - __clz(j); b >= 0; b--) {
+            m = quad_dbl(m, sub, mask);
+            if ((j >> b) & 1u) m = quad_add(m, s, sub, mask);
+        }
+        for (int k = 0; k < lambda; k++) m = quad_dbl(m, sub, mask);
+        acc = quad_add(acc, m, sub, mask);
+    }
+    // every lane has read W[t] before the shuffles above; with j = 0 the
+    // value written is the one read
+    if (sub == 0) st_vec(W + t, acc);
+}
+
+// Four lanes for a plan that runs alone, while 4 nseg threads fit in 1.25
+// waves of the four-lane kernel (resident threads per device, cached).
+template <class F>
+bool reduce_on_quads(const MsmPlan& p, uint32_t nseg) {
+    if (!p.alone) return false;
+    static double res_of[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    double res = dev >= 0 && dev < 64 ? res_of[dev] : 0.0;
+    if (res <= 0.0) {
+        int sms = 0, nb = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_reduce_quad<F>, 128, 0);
+        res = (double)(sms > 0 ? sms : 1) * (nb > 0 ? nb : 1) * 128.0;
+        if (dev >= 0 && dev < 64) res_of[dev] = res;
+    }
+    return 4.0 * nseg <= 1.25 * res;
+}
+
 // out[g nb + b] = sum of in[g n + 256 b .. g n + 256 b + 255] (within n),
 // nb = ceil(n / 256): block (b, g), 128 threads, a tree in shared memory
 template <class F>
@@ -345,10 +425,18 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     }
     uint32_t nseg = plan.all_windows() * plan.M;
     int prof_red = prof_begin(PROF_REDUCE, st);
-    k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, plan.windows(),
-                                                        plan.bucket_windows(), b.segW, b.segS); ::ace::note_launch();
-    k_seg_weight<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.segW, b.segS, nseg, plan.M, plan.lambda, plan.windows(),
-                                                        plan.bucket_windows()); ::ace::note_launch();
+    if (reduce_on_quads<F>(plan, nseg)) {
+        const unsigned blocks = (unsigned)((4ull * nseg + 127) / 128);
+        k_seg_reduce_quad<F><<<blocks, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, plan.windows(),
+                                                     plan.bucket_windows(), b.segW, b.segS); ::ace::note_launch();
+        k_seg_weight_quad<F><<<blocks, 128, 0, st>>>(b.segW, b.segS, nseg, plan.M, plan.lambda, plan.windows(),
+                                                     plan.bucket_windows()); ::ace::note_launch();
+    } else {
+        k_seg_reduce<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, plan.windows(),
+                                                            plan.bucket_windows(), b.segW, b.segS); ::ace::note_launch();
+        k_seg_weight<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.segW, b.segS, nseg, plan.M, plan.lambda,
+                                                            plan.windows(), plan.bucket_windows()); ::ace::note_launch();
+    }
     // sum each window's M weighted segments: 256 to 1 per pass, ping-pong
     // between the two segment arrays
     Xyzz<F>*src = b.segW, *dst = b.segS;

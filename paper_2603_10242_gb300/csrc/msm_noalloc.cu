@@ -85,6 +85,7 @@ int ace_msm_g1_noalloc(const ace_g1_affine* d_bases, int base_form, const ace_fr
     ACE_TRY(scratch_address(&base));
     MsmPlan plan = msm_plan(n, NOALLOC_C);
     plan.max_split = 1;  // the fixed scratch holds no partial bucket sums
+    plan.alone = true;
     bool mont = base_form == ACE_FORM_MONT;
     if (msm_scratch_bytes<fp_t>(plan, mont) > NOALLOC_BYTES) {
         set_error("ace_msm_g1_noalloc: internal scratch bound exceeded");

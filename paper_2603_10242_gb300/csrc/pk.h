@@ -80,9 +80,11 @@ struct MsmOut {
 // (prove.cu); with msm_out, only its QAP and MSMs
 // one_stream: every stage on the slot's main stream in turn (no auxiliary
 // streams), for batches whose proofs overlap across slots instead
+// alone: the proof has the GPU to itself (one proof per call); its MSM plans
+// are marked so (MsmPlan::alone)
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
               uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join,
-              const MsmOut* msm_out = nullptr, bool one_stream = false);
+              const MsmOut* msm_out = nullptr, bool one_stream = false, bool alone = false);
 // ace_prove_batch on proving slots only, never on the batch-dimension
 // kernels (prove.cu; for the batch autotuner)
 int prove_batch_on_slots(ace_ctx* ctx, size_t k, const ace_pk* const* pks, const ace_fr* const* d_zs,

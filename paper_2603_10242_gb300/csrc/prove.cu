@@ -509,7 +509,7 @@ static int gathered_msm(const MsmPlan& plan, const Query<F>& q, const fr_t* d_z,
 // are left to the batch's tail kernels (d_proof is not written).
 int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_z, const fr_t& r, const fr_t& s,
               uint32_t* d_proof, int32_t* d_status, cudaStream_t st_in, bool join, const MsmOut* msm_out,
-              bool one_stream) {
+              bool one_stream, bool alone) {
     if (prio < 0 || prio >= PRIO_LEVELS || slot < 0 || slot >= MAX_SLOTS) {
         set_error("prove: slot %d / priority level %d out of range", slot, prio);
         return ACE_E_ARG;
@@ -522,6 +522,7 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     if (ctx->serial || one_stream)
         for (int k = 0; k < 5; k++) ss.aux[k] = ss.main;
     ProvePlans pl = prove_plans(pk);
+    pl.A.alone = pl.B.alone = pl.L.alone = pl.H.alone = alone;
     for (int k = 0; k < PROVE_ARENAS; k++) ACE_TRY(slot_arena_ensure(ctx, slot, k, pl.slot_bytes[k]));
     Arena& a0 = sl.ar[0];
     fr_t* abc = (fr_t*)a0.take(3 * pk->N * sizeof(fr_t));
@@ -774,7 +775,7 @@ int ace_prove_async(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace
     memcpy(rr.v, r->l, 32);
     memcpy(ss.v, s->l, 32);
     return prove_run(ctx, 0, 0, pk, (const fr_t*)d_z, rr, ss, (uint32_t*)d_proof_out, d_status,
-                     pick_stream(ctx, stream), true);
+                     pick_stream(ctx, stream), true, nullptr, false, true);
 }
 
 int ace_prove(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, const ace_fr* r, const ace_fr* s,
@@ -1003,8 +1004,10 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
             z = stage;
         }
         MsmOut mo{res1 + 4 * i, res2 + i};
+        // a batch of one proof has the GPU to itself: it runs as ace_prove does
+        const bool lone = k == 1;
         ACE_TRY(prove_run(ctx, q, 0, pks[i], z, rr, sv, d_proofs + 64 * i, d_status + i, st_in, false,
-                          batched_tails ? &mo : nullptr, ctx->batch_one_stream));
+                          batched_tails ? &mo : nullptr, lone ? false : ctx->batch_one_stream, lone));
     }
     for (int q = 0; q < nslots; q++) ACE_TRY_CUDA(cudaStreamWaitEvent(st, ctx->slots[q].ev_done, 0));
     if (batched_tails) {

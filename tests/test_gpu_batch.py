@@ -130,3 +130,26 @@ def test_same_key_batch_on_batch_dimension_kernels(host):
     oc = O.Circuit(11, 2000, 5, 2, 60, seed=61, input_seed=77)
     opk = O.ProvingKey(oc, 62, with_points=False)
     assert proofs[7] == opk.expected_proof(zs[7], *rss[7])
+
+
+def test_one_proof_batch_runs_as_a_lone_proof():
+    """A batch of one proof takes the single-proof path (its MSMs on the
+    slot's auxiliary streams, latency-first reductions): the same bytes as
+    ace_prove and as the oracle's in-the-exponent proof, from device and from
+    host witnesses, at a size whose tabled reductions run on four lanes."""
+    ctx = gu.ctx()
+    p = (14, 1 << 14, 40, 40, 172)
+    c = ace.Circuit(*p, seed=71)
+    pk = ace.ProvingKey(ctx, c, toxic_seed=72)
+    z = c.witness(73)
+    r, s = ace.rs_from_seed(74)
+    dz = gu.dev(z)
+    lone = ctx.prove(pk, dz, r, s)
+    proofs, status = ctx.prove_batch([pk], [dz], r, s)
+    assert status == [0] and proofs[0] == lone
+    hz = torch.frombuffer(bytearray(z), dtype=torch.uint8).pin_memory()
+    proofs_h, status_h = ctx.prove_batch_host([pk], [hz], r, s)
+    assert status_h == [0] and proofs_h[0] == lone
+    oc = O.Circuit(*p, seed=71, input_seed=73)
+    opk = O.ProvingKey(oc, 72, with_points=False)
+    assert lone == opk.expected_proof(z, r, s)

@@ -55,13 +55,14 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # launch, divided by the launch's mixed additions).  It describes one version
 # of the kernel: `kernel_version` must match G1_BUCKET_KERNEL_VERSION below,
 # otherwise the bench reports traffic as null (the counters predate the code).
-G1_BUCKET_KERNEL_VERSION = "xyzz-madd-v1"
+G1_BUCKET_KERNEL_VERSION = "xyzz-madd-v2-gather-l2-64b"
 G1_BUCKET_TRAFFIC = {
-    "kernel_version": "xyzz-madd-v1",
-    "bytes_per_unit": 1.828e9 / 13.619e6,
+    "kernel_version": "xyzz-madd-v2-gather-l2-64b",
+    "bytes_per_unit": 1.0754e9 / 13.619e6,
     "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
               "--clock-control none -k regex:k_bucket_acc -c 20 python bench.py --case prove20 --steps 4 "
-              "(GB300, 16 G1 launches of four 2^20 proofs: 1.828 GB per launch for 13.62 M additions)",
+              "(GB300, the 16 G1 launches of four 2^20 proofs: 1.075 GB per launch for 13.62 M additions, "
+              "79 B per addition)",
 }
 
 

@@ -19,6 +19,29 @@ __device__ __forceinline__ T ld_vec(const T* p) {
     for (int i = 0; i < (int)(sizeof(T) / 16); i++) d[i] = __ldg(s + i);
     return r;
 }
+// A random gather of one 64-byte point (G1) or 128-byte point (G2) from a
+// read-only table: the L2 prefetch-size hint asks for that many bytes from
+// DRAM.  Without it the L2 filled a whole 128-byte line for every 64-byte
+// point, almost twice the bytes the additions need.
+template <class T>
+__device__ __forceinline__ T ld_gather(const T* p) {
+    static_assert(sizeof(T) == 64 || sizeof(T) == 128, "a 64- or 128-byte point");
+    T r;
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4* d = reinterpret_cast<uint4*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); i++) {
+        if constexpr (sizeof(T) == 64)
+            asm("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                : "=r"(d[i].x), "=r"(d[i].y), "=r"(d[i].z), "=r"(d[i].w)
+                : "l"(s + i));
+        else
+            asm("ld.global.nc.L2::128B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                : "=r"(d[i].x), "=r"(d[i].y), "=r"(d[i].z), "=r"(d[i].w)
+                : "l"(s + i));
+    }
+    return r;
+}
 template <class T>
 __device__ __forceinline__ void st_vec(T* p, const T& v) {
     const uint4* s = reinterpret_cast<const uint4*>(&v);
@@ -100,7 +123,7 @@ __global__ void __launch_bounds__(128, sizeof(F) == sizeof(fp_t) ? ACE_BUCKET_MI
     Xyzz<F> acc = xyzz_inf<F>();
     for (uint32_t i = b; i < e; i++) {
         uint32_t v = __ldg(entries + i);
-        Affine<F> p = ld_vec(bases + (v & 0x7fffffffu));
+        Affine<F> p = ld_gather(bases + (v & 0x7fffffffu));
         if (v >> 31) p.y = fe_neg(p.y);
         acc = xyzz_add_aff(acc, p);
     }
@@ -295,6 +318,31 @@ __global__ void __launch_bounds__(128) k_group_sum(const Xyzz<F>* __restrict__ i
     if (threadIdx.x == 0) st_vec(out + (size_t)g * nb + b, sh[0]);
 }
 
+// The same sum on four lanes per value (a call that runs alone, see
+// reduce_on_quads): out[g nb + b] = sum of in[g n + 64 b .. g n + 64 b + 63]
+// (within n), nb = ceil(n / 64); block (b, g) is 32 groups of four lanes,
+// each adding two inputs, then a five-level tree in shared memory.
+template <class F>
+__global__ void __launch_bounds__(128) k_group_sum_quad(const Xyzz<F>* __restrict__ in, uint32_t n, Xyzz<F>* out) {
+    __shared__ Xyzz<F> sh[32];
+    const uint32_t g = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+    const uint32_t q = threadIdx.x >> 2;
+    const int sub = (int)(threadIdx.x & 3u);
+    const unsigned mask = 0xfu << (threadIdx.x & 28u);
+    const uint32_t i0 = 64 * b + q, i1 = i0 + 32;
+    Xyzz<F> v = i0 < n ? ld_plain(in + (size_t)g * n + i0) : xyzz_inf<F>();
+    if (i1 < n) v = quad_add(v, ld_plain(in + (size_t)g * n + i1), sub, mask);
+    if (sub == 0) sh[q] = v;
+    __syncthreads();
+    for (uint32_t h = 16; h > 0; h >>= 1) {
+        if (q < h) v = quad_add(sh[q], sh[q + h], sub, mask);
+        __syncthreads();  // every read of this level before its writes
+        if (q < h && sub == 0) sh[q] = v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st_vec(out + (size_t)g * nb + b, sh[0]);
+}
+
 // Horner over the K digit windows' totals, plus the ones-window total; four
 // lanes per MSM of a batch (T holds K + 1 totals per MSM): the c (K - 1)
 // sequential doublings are the longest chain of an MSM without window tables
@@ -425,7 +473,8 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     }
     uint32_t nseg = plan.all_windows() * plan.M;
     int prof_red = prof_begin(PROF_REDUCE, st);
-    if (reduce_on_quads<F>(plan, nseg)) {
+    const bool quads = reduce_on_quads<F>(plan, nseg);
+    if (quads) {
         const unsigned blocks = (unsigned)((4ull * nseg + 127) / 128);
         k_seg_reduce_quad<F><<<blocks, 128, 0, st>>>(b.buckets, nseg, plan.B, plan.L, plan.M, plan.windows(),
                                                      plan.bucket_windows(), b.segW, b.segS); ::ace::note_launch();
@@ -437,12 +486,17 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
         k_seg_weight<F><<<(nseg + 127) / 128, 128, 0, st>>>(b.segW, b.segS, nseg, plan.M, plan.lambda,
                                                             plan.windows(), plan.bucket_windows()); ::ace::note_launch();
     }
-    // sum each window's M weighted segments: 256 to 1 per pass, ping-pong
-    // between the two segment arrays
+    // sum each window's M weighted segments: 256 (four lanes: 64) to 1 per
+    // pass, ping-pong between the two segment arrays
     Xyzz<F>*src = b.segW, *dst = b.segS;
     for (uint32_t n = plan.M; n > 1;) {
-        uint32_t nb = (n + 255) / 256;
-        k_group_sum<F><<<dim3(nb, plan.all_windows()), 128, 0, st>>>(src, n, dst); ::ace::note_launch();
+        const uint32_t per = quads ? 64 : 256;
+        uint32_t nb = (n + per - 1) / per;
+        if (quads) {
+            k_group_sum_quad<F><<<dim3(nb, plan.all_windows()), 128, 0, st>>>(src, n, dst); ::ace::note_launch();
+        } else {
+            k_group_sum<F><<<dim3(nb, plan.all_windows()), 128, 0, st>>>(src, n, dst); ::ace::note_launch();
+        }
         Xyzz<F>* t = src;
         src = dst;
         dst = t;

@@ -306,6 +306,12 @@ int ace_debug_pairing_form(int form, const uint8_t g1[64], const uint8_t g2[128]
  * cube root of unity with (beta x, y) = lambda (x, y) on G1.  out[0..3] = |k1|,
  * out[4] = 1 if k1 < 0, out[5..8] = |k2|, out[9] = 1 if k2 < 0 (|k_i| < 2^128). */
 int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]);
+/* Host: the width-5 NAF the prover walks for each GLV half in s S_A + r S_B1:
+ * out[i] (i < 132, least significant first) in {0, +-1, +-3, ..., +-15}
+ * with sum_i out[i] 2^i = k, where k = k[0] + 2^32 k[1] + 2^64 k[2] + 2^96 k[3]
+ * (below 2^128), and at most one non-zero digit in any five consecutive ones.
+ * ACE_E_ARG for NULL pointers. */
+int ace_debug_wnaf5(const uint32_t k[4], int8_t out[132]);
 /* Host: the MSM plan the library picks for n points (no device call); a
  * diagnostic of this library, the paper has no counterpart.
  * kind: 0 full-width scalars without window tables (ace_msm_g2, and

@@ -84,6 +84,7 @@ def lib():
             "ace_verify_batch": (i32, [vp, vp, sz, cp, cp, u64]),
             "ace_debug_pairing_form": (i32, [i32, cp, cp, cp]),
             "ace_debug_glv_split": (i32, [cp, vp]),
+            "ace_debug_wnaf5": (i32, [vp, vp]),
             "ace_debug_msm_plan": (i32, [sz, i32, i32, vp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),

@@ -180,29 +180,51 @@ __global__ void __launch_bounds__(160) k_prove_fixed(PkTabs t, fr_t r, fr_t s, f
 // MSMs are done.  With the GLV endomorphism phi(x, y) = (beta x, y) = lambda
 // (x, y) on G1, s = s1 + s2 lambda and r = r1 + r2 lambda (mod r) with 128-bit
 // halves (split on the host), so V = s1 S_A + s2 phi(S_A) + r1 S_B1 +
-// r2 phi(S_B1): four 128-bit double-and-add chains, one per warp, each on
-// that warp's first four lanes with the four-lane point formulas (a doubling
-// takes 3 levels of products instead of 9, an addition 4 instead of 16).
+// r2 phi(S_B1): four 128-bit chains, one per warp, each on that warp's first
+// four lanes with the four-lane point formulas (a doubling takes 3 levels of
+// products instead of 9, an addition 4 instead of 16).  Each chain walks the
+// width-5 NAF of its half (digits 0, +-1, +-3, ..., +-15, at most one non-zero
+// digit in five): about 128 doublings and 22 additions of a table of the odd
+// multiples P, 3P, ..., 15P, instead of 64 additions for the binary digits.
 // Each chain has a warp to itself, so one chain's additions do not hold up
-// another's doublings.  The result equals the one-lane chains bit for bit.
+// another's doublings.
+#define GLV_NAF_LEN 132
 struct GlvScalars {
     uint32_t k[4][4];  // |s1|, |s2|, |r1|, |r2|
     uint32_t neg[4];
+    int8_t naf[4][GLV_NAF_LEN];  // width-5 NAF of each |k_t|, least significant digit first
 };
 // block of 128 threads; sa, sb: S_A and S_B1; writes V to *v
 __device__ __forceinline__ void var_term_quad(const g1_xyzz& sa, const g1_xyzz& sb, const GlvScalars& g,
                                               const fp_t& beta, g1_xyzz* v) {
     __shared__ g1_xyzz part[4];
+    __shared__ g1_xyzz odd[4][8];  // (2 j + 1) P of chain t
     const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane < 4) {
         const unsigned mask = 0xfu;
         g1_xyzz P = t < 2 ? sa : sb;
         if (t & 1) P.X = P.X * beta;
         if (g.neg[t]) P.Y = fe_neg(P.Y);
+        const g1_xyzz P2 = quad_dbl(P, lane, mask);
+        g1_xyzz m = P;
+        if (lane == 0) odd[t][0] = m;
+        for (int j = 1; j < 8; j++) {
+            m = quad_add(m, P2, lane, mask);
+            if (lane == 0) odd[t][j] = m;
+        }
+        __syncwarp(mask);
+        const int8_t* naf = g.naf[t];
+        int top = GLV_NAF_LEN - 1;
+        while (top > 0 && naf[top] == 0) top--;
         g1_xyzz acc = xyzz_inf<fp_t>();
-        for (int i = 127; i >= 0; i--) {
+        for (int i = top; i >= 0; i--) {
             acc = quad_dbl(acc, lane, mask);
-            if ((g.k[t][i >> 5] >> (i & 31)) & 1u) acc = quad_add(acc, P, lane, mask);
+            const int d = naf[i];
+            if (d) {
+                g1_xyzz q = odd[t][(d > 0 ? d : -d) >> 1];
+                if (d < 0) q.Y = fe_neg(q.Y);
+                acc = quad_add(acc, q, lane, mask);
+            }
         }
         if (lane == 0) part[t] = acc;
     }
@@ -215,7 +237,8 @@ __device__ __forceinline__ void var_term_quad(const g1_xyzz& sa, const g1_xyzz& 
         if (lane == 0) *v = x;
     }
 }
-__global__ void __launch_bounds__(128) k_prove_var(const g1_xyzz* res1, GlvScalars g, fp_t beta, g1_xyzz* v) {
+__global__ void __launch_bounds__(128) k_prove_var(const g1_xyzz* res1, const __grid_constant__ GlvScalars g,
+                                                   fp_t beta, g1_xyzz* v) {
     var_term_quad(res1[1], res1[2], g, beta, v);
 }
 
@@ -243,6 +266,43 @@ __global__ void k_prove_var_joint(const g1_xyzz* res1, fr_t r, fr_t s, g1_xyzz* 
 static const uint32_t GLV_BETA[8] = ACE_GLV_BETA;
 static bool glv_split(const fr_t& k, uint32_t k1[4], uint32_t* n1, uint32_t k2[4], uint32_t* n2) {
     return glv_split_limbs(k.v, k1, n1, k2, n2);
+}
+
+// Width-5 NAF of a value below 2^128 (the window-w NAF of Solinas, in the
+// form of Guide to Elliptic Curve Cryptography, Algorithm 3.35): while x > 0,
+// an odd x gives the digit d = x mods 32 (in -15..15) and x -= d; then x /= 2.
+// sum_i out[i] 2^i = k; false if the digits do not fit GLV_NAF_LEN.
+static bool wnaf5(const uint32_t k[4], int8_t out[GLV_NAF_LEN]) {
+    uint32_t x[5] = {k[0], k[1], k[2], k[3], 0};
+    for (int i = 0; i < GLV_NAF_LEN; i++) {
+        int d = 0;
+        if (x[0] & 1u) {
+            d = (int)(x[0] & 31u);
+            if (d >= 16) d -= 32;
+            // x -= d over five limbs (x + 15 < 2^129 stays in range)
+            uint64_t c = d > 0 ? (uint64_t)(uint32_t)d : 0, a = d < 0 ? (uint64_t)(uint32_t)(-d) : 0;
+            for (int l = 0; l < 5; l++) {
+                uint64_t v = (uint64_t)x[l] + a - c;
+                x[l] = (uint32_t)v;
+                // carry (+1), borrow (-1) or neither into the next limb
+                a = (v >> 32) == 1 ? 1 : 0;
+                c = (v >> 32) > 1 ? 1 : 0;
+            }
+        }
+        out[i] = (int8_t)d;
+        for (int l = 0; l < 4; l++) x[l] = (x[l] >> 1) | (x[l + 1] << 31);
+        x[4] >>= 1;
+    }
+    return (x[0] | x[1] | x[2] | x[3] | x[4]) == 0;
+}
+
+// The GLV halves of s and r and their NAFs (false if a split or a recoding failed)
+static bool glv_scalars(const fr_t& r, const fr_t& s, GlvScalars& g) {
+    if (!glv_split(s, g.k[0], &g.neg[0], g.k[1], &g.neg[1]) || !glv_split(r, g.k[2], &g.neg[2], g.k[3], &g.neg[3]))
+        return false;
+    for (int t = 0; t < 4; t++)
+        if (!wnaf5(g.k[t], g.naf[t])) return false;
+    return true;
 }
 
 __device__ void write_g1(uint32_t* dst, const g1_xyzz& p) {
@@ -582,8 +642,7 @@ int prove_run(ace_ctx* ctx, int slot, int prio, const ace_pk* pk, const fr_t* d_
     ACE_TRY_CUDA(cudaStreamWaitEvent(ss.aux[4], sl.ev_aux[1], 0));
     int pv = prof_begin(PROF_ASSEMBLY, ss.aux[4]);
     GlvScalars glv;
-    if (glv_split(s, glv.k[0], &glv.neg[0], glv.k[1], &glv.neg[1]) &&
-        glv_split(r, glv.k[2], &glv.neg[2], glv.k[3], &glv.neg[3])) {
+    if (glv_scalars(r, s, glv)) {
         fp_t beta;
         memcpy(beta.v, GLV_BETA, 32);
         k_prove_var<<<1, 128, 0, ss.aux[4]>>>(res1, glv, fe_to_mont(beta), vterm);
@@ -953,8 +1012,7 @@ static int prove_batch_impl(ace_ctx* ctx, const char* fn, size_t k, const ace_pk
         memcpy(d.r.v, rs[i].l, 32);
         memcpy(d.s.v, ss[i].l, 32);
         d.rs = fe_from_mont(fe_to_mont(d.r) * fe_to_mont(d.s));
-        d.glv_ok = glv_split(d.s, d.glv.k[0], &d.glv.neg[0], d.glv.k[1], &d.glv.neg[1]) &&
-                   glv_split(d.r, d.glv.k[2], &d.glv.neg[2], d.glv.k[3], &d.glv.neg[3]);
+        d.glv_ok = glv_scalars(d.r, d.s, d.glv);
     }
     cudaStream_t st = ctx->stream;
     int nslots = (int)(k < (size_t)ctx->batch_slots ? k : (size_t)ctx->batch_slots);
@@ -1056,6 +1114,12 @@ int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]) {
     memcpy(x.v, k->l, 32);
     if (fe_geq_mod(x)) return ACE_E_ARG;
     return glv_split(x, out, &out[4], out + 5, &out[9]) ? ACE_OK : ACE_E_ARG;
+}
+
+int ace_debug_wnaf5(const uint32_t k[4], int8_t out[132]) {
+    static_assert(GLV_NAF_LEN == 132, "the declared digit count");
+    if (!k || !out) return ACE_E_ARG;
+    return wnaf5(k, out) ? ACE_OK : ACE_E_INTERNAL;
 }
 
 int ace_prove_many(ace_ctx* ctx, const ace_pk* pk, size_t k, const ace_fr* d_z, const ace_fr* rs, const ace_fr* ss,

@@ -176,6 +176,33 @@ def test_glv_split(lib):
         assert (k1 + k2 * lam - k) % Y.R == 0
 
 
+def test_wnaf5_digits(lib):
+    """The width-5 NAF of the variable-base term's 128-bit GLV halves: the
+    digits rebuild k, each is 0 or odd with |d| <= 15, and no five
+    consecutive digits hold two non-zero ones (so the chain adds about
+    once in six doublings)."""
+    import random
+    f = lib.ace_debug_wnaf5
+    f.restype = ctypes.c_int
+    rng = random.Random(11)
+    ks = [0, 1, 15, 16, 17, 31, 32, (1 << 128) - 1, 1 << 127, (1 << 127) - 1, 0x5555 << 100]
+    ks += [rng.getrandbits(128) for _ in range(300)]
+    nonzero = 0
+    for k in ks:
+        words = (ctypes.c_uint32 * 4)(*[(k >> (32 * i)) & 0xFFFFFFFF for i in range(4)])
+        out = (ctypes.c_int8 * 132)()
+        assert f(words, out) == 0
+        d = list(out)
+        assert sum(x << i for i, x in enumerate(d)) == k
+        assert all(x == 0 or (x % 2 == 1 and -15 <= x <= 15) for x in d)
+        nz = [i for i, x in enumerate(d) if x]
+        assert all(b - a >= 5 for a, b in zip(nz, nz[1:]))
+        assert not nz or nz[-1] <= 128
+        nonzero += len(nz)
+    # random 128-bit values: about 128 / 6 non-zero digits each
+    assert 18 < nonzero / len(ks) < 25
+
+
 # window choices measured on the GB300 (G1 MSM sweep, block-proof keys)
 MEASURED_PLANS = [
     (1 << 16, ace.MSM_GLV, 16), (1 << 20, ace.MSM_GLV, 16), (1 << 24, ace.MSM_GLV, 19),

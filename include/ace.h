@@ -259,9 +259,12 @@ int ace_verify_batch(ace_ctx* ctx, const ace_vk* vk, size_t k, const ace_fr* pub
 /* NTT of N = 2^log_n canonical Fr values in natural order, in place on the
  * device: the transforms of the QAP step of Groth16.Prove (Section 3.1,
  * Algorithm 1; H = {omega^i}, omega = 5^((r-1)/N), coset g H with g = 5).
- * Each pass picks its block width to fill the GPU's last wave of blocks.  kind: 0 forward (coefficients -> values on H),
- * 1 inverse, 2 coset forward (coefficients -> values on g H), 3 coset inverse.
- * 1 <= log_n <= 28.  Scratch: N elements from the context. */
+ * The values must be canonical (below r): the passes transform them as they
+ * are, with no conversion, and a larger value gives an undefined result.
+ * Each pass picks its block width to fill the GPU's last wave of blocks.
+ * kind: 0 forward (coefficients -> values on H), 1 inverse, 2 coset forward
+ * (coefficients -> values on g H), 3 coset inverse.  1 <= log_n <= 28.
+ * Scratch: N elements from the context. */
 int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream stream);
 
 /* The transform passes the QAP step is built from, without scaling: `count`

@@ -252,34 +252,29 @@ int ace_ntt(ace_ctx* ctx, ace_fr* d_data, uint32_t log_n, int kind, ace_stream s
     fr_t* tmp = (fr_t*)ctx->scratch[0].take(n * sizeof(fr_t));
     cudaStream_t st = pick_stream(ctx, stream);
     fr_t* d = (fr_t*)d_data;
-    // One transform, no separate passes: the first pass enters Montgomery
-    // form (and multiplies by g^i for the coset form) as it loads, the last
-    // one applies the output factor, leaves Montgomery form and writes each
-    // element to its bit-reversed position, which turns the DIF order back
-    // into natural order.
+    // The transform runs on the canonical values themselves: a Montgomery
+    // product of a canonical value by a Montgomery-form factor (a twiddle,
+    // g^i, 1/N) is the canonical product, and the butterflies' additions do
+    // not depend on the form.  So the passes convert nothing; the first
+    // applies the coset factor as it loads (kind 2), the last the output
+    // factor (kinds 1, 3) and writes each element to its bit-reversed
+    // position, which turns the DIF order back into natural order.
     NttScale pre, post;
-    pre.hi = plan->rr;  // R^2 raw: x R^2 R^-1 = x R
-    pre.lo = plan->one;
-    pre.single = 1;
-    if (kind == 2) {  // g^i R^2: x g^i R
-        pre.hi = plan->cgr_hi;
+    if (kind == 2) {  // g^e
+        pre.hi = plan->cg_hi;
         pre.lo = plan->cos_lo;
         pre.h = plan->h;
-        pre.single = 0;
     }
-    post.hi = plan->plain_one;  // 1 raw: x R R^-1 = x
-    post.lo = plan->one;
-    post.single = 1;
-    if (kind == 1) {  // N^-1 raw: (x R) N^-1 R^-1 = x / N
+    if (kind == 1) {  // 1 / N
         post.hi = plan->ninv;
-        post.lo = plan->plain_one;
+        post.lo = plan->one;
+        post.single = 1;
     }
-    if (kind == 3) {  // g^-e / N at bit-reversed position, leaves Montgomery form
+    if (kind == 3) {  // g^-e / N at bit-reversed position
         post.hi = plan->icos_hi;
-        post.lo = plan->icos_lo;
+        post.lo = plan->icos_lo_m;
         post.h = plan->h;
         post.brev = 1;
-        post.single = 0;
     }
     const bool inverse = kind == 1 || kind == 3;
     ACE_TRY(ntt_run_io(*plan, d, tmp, d, true, 1, true, inverse, pre, post, st, true));

@@ -74,9 +74,6 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     std::vector<fr_t> cos_lo, cg_hi, cos_hi, icos_lo_m, icos_lo, icos_hi;
     h_powers(cos_lo, g, one, nlo);
     h_powers(cg_hi, h_pow_u64(g, nlo), one, nhi);
-    // the same powers times R: a product with a canonical input then enters Montgomery form
-    std::vector<fr_t> cgr_hi(nhi);
-    for (size_t i = 0; i < nhi; i++) cgr_hi[i] = cg_hi[i] * fe_rr<FrCfg>();
     h_powers(cos_hi, h_pow_u64(g, nlo), ninv, nhi);
     h_powers(icos_lo_m, ginv, one, nlo);
     icos_lo.resize(nlo);
@@ -94,7 +91,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
         return o;
     };
     size_t o_twf = place(half), o_twi = place(half), o_cos_hi = place(nhi), o_cos_lo = place(nlo),
-           o_cg_hi = place(nhi), o_cgr_hi = place(nhi), o_icos_hi = place(nhi), o_icos_lo = place(nlo), o_ninv = place(1),
+           o_cg_hi = place(nhi), o_icos_lo_m = place(nlo), o_icos_hi = place(nhi), o_icos_lo = place(nlo), o_ninv = place(1),
            o_one = place(1), o_p1 = place(1), o_rr = place(1), o_seed = place(4 * (tlo + thi));
     void* mem = nullptr;
     ACE_TRY(dev_alloc(ctx, &mem, off));
@@ -108,7 +105,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     p->cos_hi = (fr_t*)(base + o_cos_hi);
     p->cos_lo = (fr_t*)(base + o_cos_lo);
     p->cg_hi = (fr_t*)(base + o_cg_hi);
-    p->cgr_hi = (fr_t*)(base + o_cgr_hi);
+    p->icos_lo_m = (fr_t*)(base + o_icos_lo_m);
     p->icos_hi = (fr_t*)(base + o_icos_hi);
     p->icos_lo = (fr_t*)(base + o_icos_lo);
     p->ninv = (fr_t*)(base + o_ninv);
@@ -131,7 +128,7 @@ int ntt_get_plan(ace_ctx* ctx, int log_n, NttPlan** out) {
     e = e ? e : up(p->cos_hi, cos_hi.data(), nhi * sizeof(fr_t));
     e = e ? e : up(p->cos_lo, cos_lo.data(), nlo * sizeof(fr_t));
     e = e ? e : up(p->cg_hi, cg_hi.data(), nhi * sizeof(fr_t));
-    e = e ? e : up(p->cgr_hi, cgr_hi.data(), nhi * sizeof(fr_t));
+    e = e ? e : up(p->icos_lo_m, icos_lo_m.data(), nlo * sizeof(fr_t));
     e = e ? e : up(p->icos_hi, icos_hi.data(), nhi * sizeof(fr_t));
     e = e ? e : up(p->icos_lo, icos_lo.data(), nlo * sizeof(fr_t));
     e = e ? e : up(p->ninv, &ninv, sizeof(fr_t));

@@ -26,9 +26,9 @@ struct NttPlan {
     fr_t* cos_hi = nullptr;   // N^-1 g^(e_hi 2^h) (Montgomery)
     fr_t* cos_lo = nullptr;   // g^e_lo (Montgomery)
     fr_t* cg_hi = nullptr;    // g^(e_hi 2^h) (Montgomery)
-    fr_t* cgr_hi = nullptr;   // g^(e_hi 2^h) R (Montgomery): with cos_lo, takes a canonical input to Montgomery form
     fr_t* icos_hi = nullptr;  // N^-1 g^-(e_hi 2^h) (Montgomery)
     fr_t* icos_lo = nullptr;  // g^-e_lo as a plain value: the product leaves Montgomery form
+    fr_t* icos_lo_m = nullptr;  // g^-e_lo (Montgomery): with icos_hi, the factor for canonical data
     fr_t* ninv = nullptr;     // [N^-1] (Montgomery), single entry
     fr_t* one = nullptr;      // [1] (Montgomery), single entry
     fr_t* plain_one = nullptr;  // [1] as a plain value: multiplying by it leaves Montgomery form

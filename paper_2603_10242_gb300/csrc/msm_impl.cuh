@@ -281,23 +281,27 @@ __global__ void __launch_bounds__(128) k_seg_weight_quad(Xyzz<F>* W, const Xyzz<
     if (sub == 0) st_vec(W + t, acc);
 }
 
-// Four lanes for a plan that runs alone, while 4 nseg threads fit in 1.25
-// waves of the four-lane kernel (resident threads per device, cached).
-template <class F>
-bool reduce_on_quads(const MsmPlan& p, uint32_t nseg) {
-    if (!p.alone) return false;
-    static double res_of[64] = {};
+// Resident threads of a 128-thread-block kernel on the current device
+// (cached per device ordinal in res_of, always with that device's value).
+static inline double resident_threads(const void* kernel, double* res_of) {
     int dev = 0;
     cudaGetDevice(&dev);
     double res = dev >= 0 && dev < 64 ? res_of[dev] : 0.0;
     if (res <= 0.0) {
         int sms = 0, nb = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_reduce_quad<F>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, 128, 0);
         res = (double)(sms > 0 ? sms : 1) * (nb > 0 ? nb : 1) * 128.0;
         if (dev >= 0 && dev < 64) res_of[dev] = res;
     }
-    return 4.0 * nseg <= 1.25 * res;
+    return res;
+}
+// Four lanes for a plan that runs alone, while 4 nseg threads fit in 1.25
+// waves of the four-lane segment kernel.
+template <class F>
+bool reduce_on_quads(const MsmPlan& p, uint32_t nseg) {
+    static double res_of[64] = {};
+    return p.alone && 4.0 * nseg <= 1.25 * resident_threads((const void*)k_seg_reduce_quad<F>, res_of);
 }
 
 // out[g nb + b] = sum of in[g n + 256 b .. g n + 256 b + 255] (within n),
@@ -341,6 +345,15 @@ __global__ void __launch_bounds__(128) k_group_sum_quad(const Xyzz<F>* __restric
         __syncthreads();
     }
     if (threadIdx.x == 0) st_vec(out + (size_t)g * nb + b, sh[0]);
+}
+
+// The group sum on four lanes runs about 2 nseg threads in its first pass,
+// half as many as the segment kernels: a plan that runs alone takes it while
+// those fit 1.25 waves, even when its segments stay on one lane.
+template <class F>
+bool group_sum_on_quads(const MsmPlan& p, uint32_t nseg) {
+    static double res_of[64] = {};
+    return p.alone && 2.0 * nseg <= 1.25 * resident_threads((const void*)k_group_sum_quad<F>, res_of);
 }
 
 // Horner over the K digit windows' totals, plus the ones-window total; four
@@ -488,11 +501,12 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
     }
     // sum each window's M weighted segments: 256 (four lanes: 64) to 1 per
     // pass, ping-pong between the two segment arrays
+    const bool quad_sum = quads || group_sum_on_quads<F>(plan, nseg);
     Xyzz<F>*src = b.segW, *dst = b.segS;
     for (uint32_t n = plan.M; n > 1;) {
-        const uint32_t per = quads ? 64 : 256;
+        const uint32_t per = quad_sum ? 64 : 256;
         uint32_t nb = (n + per - 1) / per;
-        if (quads) {
+        if (quad_sum) {
             k_group_sum_quad<F><<<dim3(nb, plan.all_windows()), 128, 0, st>>>(src, n, dst); ::ace::note_launch();
         } else {
             k_group_sum<F><<<dim3(nb, plan.all_windows()), 128, 0, st>>>(src, n, dst); ::ace::note_launch();

@@ -187,7 +187,13 @@ int ace_qap_h(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, ace_fr* d_h_out
  * context. */
 int ace_msm_g1(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
                size_t n, ace_g1_affine* d_out, ace_stream stream);
-/* Same over G2 (coordinates in Fp2): the B query of the proof. */
+/* Same over G2 (coordinates in Fp2): the B query of the proof.  For
+ * n <= 2^16 the scalars are split four ways by the endomorphism psi of G2
+ * (k = k0 + k1 lambda + k2 lambda^2 + k3 lambda^3, parts below 2^66, over
+ * the points psi^t(Q_i)), which cuts the digit windows from 17 to 7; any
+ * 256-bit scalar is then taken modulo r.  Larger MSMs use full-width
+ * scalars.  Scratch (buckets, sorted digits, 4n prepared points and parts)
+ * is drawn from the context. */
 int ace_msm_g2(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const ace_fr* d_scalars,
                size_t n, ace_g2_affine* d_out, ace_stream stream);
 
@@ -283,6 +289,11 @@ int ace_msm_g1_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form,
  * library; the paper has no counterpart. */
 int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_form, const ace_fr* d_scalars,
                           size_t n, int c, ace_g1_affine* d_out, ace_stream stream);
+/* ace_msm_g2 (scalars split four ways by psi, K = ceil(67 / c) windows over
+ * 4n points) with the window size forced to c (6 <= c <= 20); n < 2^29.  A
+ * diagnostic of this library; the paper has no counterpart. */
+int ace_msm_g2_gls_window(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const ace_fr* d_scalars,
+                          size_t n, int c, ace_g2_affine* d_out, ace_stream stream);
 
 /* ---- diagnostics and measurement ------------------------------------------- */
 
@@ -315,15 +326,24 @@ int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]);
  * (below 2^128), and at most one non-zero digit in any five consecutive ones.
  * ACE_E_ARG for NULL pointers. */
 int ace_debug_wnaf5(const uint32_t k[4], int8_t out[132]);
+/* Host: the split ace_msm_g2 applies to each scalar, by the endomorphism
+ * psi(x, y) = (conj(x) gx, conj(y) gy) of G2 (multiplication by
+ * lambda = 6 x^2 on G2, x = 4965661367192848881 the BN parameter):
+ * k = k0 + k1 lambda + k2 lambda^2 + k3 lambda^3 (mod r) with |k_i| < 2^66.
+ * out[4 i .. 4 i + 2] = |k_i| (3 little-endian 32-bit limbs), out[4 i + 3] =
+ * 1 if k_i < 0.  ACE_E_ARG for NULL pointers or k >= r. */
+int ace_debug_gls_split(const ace_fr* k, uint32_t out[16]);
 /* Host: the MSM plan the library picks for n points (no device call); a
  * diagnostic of this library, the paper has no counterpart.
- * kind: 0 full-width scalars without window tables (ace_msm_g2, and
- * ace_msm_g1 for n >= 2^30), 1 window tables (proving-key queries), 2 the
- * GLV split of ace_msm_g1.  force_c: 0 for the cost model's window, else
- * 6..20.  out: [c, K digit windows, buckets per window 2^(c-1), bucket
- * windows + 1 (the {0,1} window), segment length L, segments per window M,
- * virtual buckets of the {0,1} window, points (2n for the GLV split, low 32
- * bits)].  ACE_E_ARG for a bad kind or force_c. */
+ * kind: 0 full-width scalars without window tables (ace_msm_g1 for
+ * n >= 2^30, ace_msm_g2 for n > 2^16), 1 window tables (proving-key
+ * queries), 2 the GLV split of ace_msm_g1, 3 the four-way psi split of
+ * ace_msm_g2.  force_c: 0 for the library's window (the cost model's; for
+ * kind 3 a measured constant), else 6..20.
+ * out: [c, K digit windows, buckets per window 2^(c-1), bucket windows + 1
+ * (the {0,1} window), segment length L, segments per window M, virtual
+ * buckets of the {0,1} window, points (2n for the GLV split, 4n for the psi
+ * split, low 32 bits)].  ACE_E_ARG for a bad kind or force_c. */
 int ace_debug_msm_plan(size_t n, int kind, int force_c, uint32_t out[8]);
 /* Measured 32-bit multiply-add throughput of the device (operations/s):
  * mode 0 mad.lo, 1 mad.hi, 2 carry-chained lo/hi pairs, 3 mad.wide.u32

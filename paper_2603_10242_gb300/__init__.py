@@ -54,6 +54,7 @@ def lib():
             "ace_msm_g2": (i32, [vp, vp, i32, vp, sz, vp, vp]),
             "ace_msm_g1_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
             "ace_msm_g1_glv_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
+            "ace_msm_g2_gls_window": (i32, [vp, vp, i32, vp, sz, i32, vp, vp]),
             "ace_msm_g1_noalloc": (i32, [vp, i32, vp, sz, vp, vp]),
             "ace_g1_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
             "ace_g2_fixed_base": (i32, [vp, vp, sz, vp, i32, vp]),
@@ -85,6 +86,7 @@ def lib():
             "ace_debug_pairing_form": (i32, [i32, cp, cp, cp]),
             "ace_debug_glv_split": (i32, [cp, vp]),
             "ace_debug_wnaf5": (i32, [vp, vp]),
+            "ace_debug_gls_split": (i32, [cp, vp]),
             "ace_debug_msm_plan": (i32, [sz, i32, i32, vp]),
             "ace_autotune_msm": (i32, [vp, u32, u32, vp]),
             "ace_autotune_ntt": (i32, [vp, u32, u32, vp]),
@@ -191,6 +193,10 @@ class Context:
 
     def msm_g1_glv_window(self, bases, scalars, n: int, c: int, out, base_form: int = FORM_CANONICAL, stream=None):
         check(lib().ace_msm_g1_glv_window(self.h, _ptr(bases), base_form, _ptr(scalars), n, c, _ptr(out),
+                                          _stream(stream)))
+
+    def msm_g2_gls_window(self, bases, scalars, n: int, c: int, out, base_form: int = FORM_CANONICAL, stream=None):
+        check(lib().ace_msm_g2_gls_window(self.h, _ptr(bases), base_form, _ptr(scalars), n, c, _ptr(out),
                                           _stream(stream)))
 
     def g1_fixed_base(self, scalars, n: int, out, out_form: int = FORM_CANONICAL, stream=None):
@@ -301,7 +307,7 @@ def debug_curve_op(group: int, op: int, d_a, d_b, d_k, d_out, n: int, stream=Non
     check(lib().ace_debug_curve_op(group, op, _ptr(d_a), _ptr(d_b), _ptr(d_k), _ptr(d_out), n, _stream(stream)))
 
 
-MSM_FULL, MSM_TABLED, MSM_GLV = 0, 1, 2
+MSM_FULL, MSM_TABLED, MSM_GLV, MSM_GLS = 0, 1, 2, 3
 
 
 def msm_plan(n: int, kind: int, force_c: int = 0) -> dict:

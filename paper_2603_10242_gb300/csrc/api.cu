@@ -36,11 +36,17 @@ static int msm_entry(ace_ctx* ctx, const void* d_bases, int base_form, const ace
     int lg = 0;
     while (lg < 31 && ((size_t)1 << (lg + 1)) <= n) lg++;
     // G1: scalars split by the GLV endomorphism (half the windows; the 2 n
-    // virtual points need n < 2^30), with the autotuned window if any; G2:
-    // full-width scalars, window from the cost model
+    // virtual points need n < 2^30), with the autotuned window if any; G2 up
+    // to 2^16 points: scalars split four ways by psi, whose 4 n virtual points
+    // (32 MB at 2^16) stay in L2 and whose 7 windows of 2^10 buckets cut the
+    // reduction and the Horner chain (60 G2 doublings instead of 225);
+    // larger G2 MSMs keep full-width scalars (at 2^18 the 128 MB of virtual
+    // points made the split 8.0 ms against 6.0), window from the cost model
     MsmPlan plan;
     if (sizeof(F) == sizeof(fp_t) && n < (1ull << 30))
         plan = msm_plan_glv(n, ctx->tuned_msm_c[lg]);
+    else if (sizeof(F) == sizeof(fp2_t) && n <= (1ull << 16))
+        plan = msm_plan_gls(n);
     else
         plan = msm_plan(n);
     plan.alone = true;
@@ -216,14 +222,35 @@ int ace_msm_g1_glv_window(ace_ctx* ctx, const ace_g1_affine* d_bases, int base_f
                          (g1_aff*)d_out, pick_stream(ctx, stream));
 }
 
+// Diagnostic: the G2 MSM of ace_msm_g2 (psi split) with an explicit window
+// size c (6..20).
+int ace_msm_g2_gls_window(ace_ctx* ctx, const ace_g2_affine* d_bases, int base_form, const ace_fr* d_scalars,
+                          size_t n, int c, ace_g2_affine* d_out, ace_stream stream) {
+    clear_error();
+    if (!ctx || !d_out || (n && (!d_bases || !d_scalars)) || c < 6 || c > 20 || n >= (1ull << 29) ||
+        (base_form != ACE_FORM_CANONICAL && base_form != ACE_FORM_MONT)) {
+        set_error("ace_msm_g2_gls_window: bad argument");
+        return ACE_E_ARG;
+    }
+    ACE_TRY_CUDA(cudaSetDevice(ctx->device));
+    MsmPlan plan = msm_plan_gls(n, c);
+    plan.alone = true;
+    bool mont = base_form == ACE_FORM_MONT;
+    ACE_TRY(arena_ensure(ctx, 0, msm_scratch_bytes<fp2_t>(plan, mont)));
+    return msm_run<fp2_t>(plan, (const g2_aff*)d_bases, mont, (const uint32_t*)d_scalars, ctx->scratch[0], nullptr,
+                          (g2_aff*)d_out, pick_stream(ctx, stream));
+}
+
 int ace_debug_msm_plan(size_t n, int kind, int force_c, uint32_t out[8]) {
     clear_error();
-    if (!out || kind < 0 || kind > 2 || force_c < 0 || (force_c != 0 && (force_c < 6 || force_c > 20))) {
+    if (!out || kind < 0 || kind > 3 || force_c < 0 || (force_c != 0 && (force_c < 6 || force_c > 20))) {
         set_error("ace_debug_msm_plan: bad argument");
         return ACE_E_ARG;
     }
-    const MsmPlan p = kind == 0 ? msm_plan(n, force_c) : kind == 1 ? msm_plan_tabled(n, force_c)
-                                                                   : msm_plan_glv(n, force_c);
+    const MsmPlan p = kind == 0   ? msm_plan(n, force_c)
+                      : kind == 1 ? msm_plan_tabled(n, force_c)
+                      : kind == 2 ? msm_plan_glv(n, force_c)
+                                  : msm_plan_gls(n, force_c);
     out[0] = (uint32_t)p.c;
     out[1] = (uint32_t)p.K;
     out[2] = p.B;

@@ -48,6 +48,11 @@ struct MsmPlan {
     // of n / 2 input points, whose scalars are the 128-bit halves of the GLV
     // split (glv.cuh); K = ceil(128 / c) windows
     bool glv = false;
+    // gls (G2 without window tables): n counts the points psi^t(Q_i), t < 4,
+    // of n / 4 input points, whose scalars are the four parts of the split by
+    // the endomorphism psi (glv.cuh, below 2^66); K = ceil(67 / c) windows
+    bool gls = false;
+    int bits() const { return glv ? 128 : gls ? 67 : 255; }
     // virtual buckets the ones window uses (a power of two <= B, about n / 64):
     // scalar 1 of point i goes to bucket i mod B1.  Enough buckets to spread
     // the additions over many threads, few enough that the window's plain sum
@@ -73,6 +78,9 @@ MsmPlan msm_plan(size_t n, int force_c = 0);
 MsmPlan msm_plan_tabled(size_t n, int force_c = 0);
 // G1 plan over the GLV split of n points (2 n virtual points, 128-bit scalars)
 MsmPlan msm_plan_glv(size_t n, int force_c = 0);
+// G2 plan over the four-way split of n points by psi (4 n virtual points,
+// scalars below 2^66)
+MsmPlan msm_plan_gls(size_t n, int force_c = 0);
 // make p a plan for `batch` MSMs over the same points (segments of 16
 // buckets again when batch > 1; see plan_for)
 void msm_plan_set_batch(MsmPlan& p, uint32_t batch);
@@ -81,6 +89,13 @@ void msm_plan_set_batch(MsmPlan& p, uint32_t batch);
 // canonical) with k_i mod r = k1 + k2 lambda and the signs moved onto the
 // points.  in: n affine points (Montgomery if in_mont); sc: n scalars < 2^256.
 int glv_prepare(const Affine<fp_t>* in, bool in_mont, const uint32_t* sc, size_t n, Affine<fp_t>* out,
+                uint32_t* osc, cudaStream_t st);
+// psi inputs of a G2 MSM: for i < n and t < 4, out[t n + i] = +-psi^t(Q_i)
+// (Montgomery affine) and osc[t n + i] = |k_t| (8 limbs, canonical) with
+// k_i mod r = k_0 + k_1 lambda + k_2 lambda^2 + k_3 lambda^3 and the signs
+// moved onto the points.  in: n affine points (Montgomery if in_mont); sc: n
+// scalars < 2^256.
+int gls_prepare(const Affine<fp2_t>* in, bool in_mont, const uint32_t* sc, size_t n, Affine<fp2_t>* out,
                 uint32_t* osc, cudaStream_t st);
 // window table of n Montgomery affine points: tab[w n + i] = 2^(c w) pts[i]
 // for w < K (pts may be tab itself, i.e. window 0 already in place)

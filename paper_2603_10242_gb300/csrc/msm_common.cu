@@ -53,7 +53,7 @@ __device__ __forceinline__ T ld_plain(const T* p) {
 static const double MSM_TOP_LOAD = 512.0;
 static const double MSM_SEQ_MADD = 2.0e4;
 // bits: 255 for full Fr scalars (254 bits and the top digit's carry), 128
-// for GLV halves (below 2^127).
+// for GLV halves (below 2^127), 67 for the G2 split's parts (below 2^66).
 static double msm_cost(size_t n, int c, bool tabled, int bits = 255) {
     const int K = (bits + c - 1) / c;
     const double B = (double)(1u << (c - 1));
@@ -71,14 +71,15 @@ static double msm_cost(size_t n, int c, bool tabled, int bits = 255) {
 #ifndef ACE_SHORT_SEGMENT_MAX_C
 #define ACE_SHORT_SEGMENT_MAX_C 14
 #endif
-static MsmPlan plan_for(size_t n, int c, bool tabled, bool glv = false) {
+static MsmPlan plan_for(size_t n, int c, bool tabled, bool glv = false, bool gls = false) {
     MsmPlan p;
     p.n = n;
     if (c < 6) c = 6;
     if (c > 20) c = 20;
     p.c = c;
     p.glv = glv;
-    p.K = ((glv ? 128 : 255) + p.c - 1) / p.c;
+    p.gls = gls;
+    p.K = (p.bits() + p.c - 1) / p.c;
     p.B = 1u << (p.c - 1);
     // segments of 16 buckets; of 4 when a window holds at most 2^13 buckets:
     // there a segment's sequential running sum (2 additions per bucket, one
@@ -124,6 +125,19 @@ MsmPlan msm_plan(size_t n, int force_c) { return plan_for(n, force_c > 0 ? force
 
 MsmPlan msm_plan_glv(size_t n, int force_c) {
     return plan_for(2 * n, force_c > 0 ? force_c : best_window(2 * n, false, 128), false, true);
+}
+
+// Window of the G2 split, measured: the parts lie below 2^65 in practice
+// (2^66 is the proven bound the 67-bit digit windows cover), so the window
+// holding bit 64 decides the balance.  c = 11 leaves it 10 value bits and no
+// carry into the (empty) window above; c = 13 fills it and carries into the
+// next one for half the points, c = 12, 15, 16 leave it 1-5 bits: buckets of
+// thousands of entries.  Measured per G2 MSM over 2^12 / 2^14 / 2^16 points:
+// c = 11 1.5 / 1.7 / 2.6 ms, c = 17 (what the G1 cost model picks) 3.2 /
+// 3.0 / 3.9 ms, the full-width MSM 3.9 / 3.8 / 4.0 ms.
+static const int MSM_GLS_C = 11;
+MsmPlan msm_plan_gls(size_t n, int force_c) {
+    return plan_for(4 * n, force_c > 0 ? force_c : MSM_GLS_C, false, false, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -244,7 +258,8 @@ __device__ __forceinline__ int scalar_kind(const uint32_t s[8]) {
 // (precomputed window tables); otherwise window w's buckets hold entry i.
 // A batch of MSMs over the same n points: scalar t belongs to MSM t / n and
 // multiplies point t mod n; each MSM has its own keys_per keys.
-// BITS: 255 for Fr scalars, 128 for GLV halves (magnitudes below 2^127).
+// BITS: 255 for Fr scalars, 128 for GLV halves (magnitudes below 2^127), 67
+// for the parts of the G2 split (below 2^66).
 template <int C, bool SCATTER, bool TAB, int BITS = 255>
 __global__ void k_msm_digits(const uint32_t* __restrict__ sc, size_t total, size_t n, uint32_t keys_per,
                              uint32_t ones_mask, uint32_t* cnt, uint32_t* entries) {
@@ -302,6 +317,19 @@ void launch_digits(const MsmPlan& plan, const uint32_t* sc, uint32_t* cnt, uint3
     const size_t total = plan.scalars(), n = plan.n;
     const uint32_t kp = plan.keys_per(), om = plan.ones_mask();
     unsigned grid = (unsigned)((total + 255) / 256);
+    if (plan.gls) {
+        switch (plan.c) {
+#define ACE_DIGITS_GLS(CC) \
+    case CC: k_msm_digits<CC, SCATTER, false, 67><<<grid, 256, 0, st>>>(sc, total, n, kp, om, cnt, entries); break;
+            ACE_DIGITS_GLS(6) ACE_DIGITS_GLS(7) ACE_DIGITS_GLS(8) ACE_DIGITS_GLS(9) ACE_DIGITS_GLS(10)
+            ACE_DIGITS_GLS(11) ACE_DIGITS_GLS(12) ACE_DIGITS_GLS(13) ACE_DIGITS_GLS(14) ACE_DIGITS_GLS(15)
+            ACE_DIGITS_GLS(16) ACE_DIGITS_GLS(17) ACE_DIGITS_GLS(18) ACE_DIGITS_GLS(19) ACE_DIGITS_GLS(20)
+#undef ACE_DIGITS_GLS
+            default: break;
+        }
+        ::ace::note_launch();
+        return;
+    }
     if (plan.glv) {
         switch (plan.c) {
 #define ACE_DIGITS_GLV(CC) \

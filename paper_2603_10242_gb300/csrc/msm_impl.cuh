@@ -77,11 +77,11 @@ bool MsmBufs<F, A>::carve(Alloc& a, const MsmPlan& p, bool need_conv) {
     partial = split > 1 ? (Xyzz<F>*)a.take(keys * split * sizeof(Xyzz<F>)) : buckets;
     segW = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
     segS = (Xyzz<F>*)a.take((size_t)p.all_windows() * p.M * sizeof(Xyzz<F>));
-    need_conv = need_conv || p.glv;
+    need_conv = need_conv || p.glv || p.gls;
     conv = need_conv ? (Affine<F>*)a.take(p.n * sizeof(Affine<F>)) : nullptr;
-    gsc = p.glv ? (uint32_t*)a.take(p.n * 32) : nullptr;
+    gsc = p.glv || p.gls ? (uint32_t*)a.take(p.n * 32) : nullptr;
     return offsets && cursor && scan_tmp && entries && order && size_bins && buckets && partial && segW && segS &&
-           (!need_conv || conv) && (!p.glv || gsc);
+           (!need_conv || conv) && (!(p.glv || p.gls) || gsc);
 }
 
 template <class F>
@@ -449,6 +449,16 @@ int msm_run(const MsmPlan& plan, const Affine<F>* d_bases, bool base_mont, const
             d_scalars = b.gsc;
         } else {
             set_error("msm: the GLV plan is for G1 only");
+            return ACE_E_ARG;
+        }
+    } else if (plan.gls) {
+        if constexpr (sizeof(F) == sizeof(fp2_t)) {
+            ACE_TRY(gls_prepare((const Affine<fp2_t>*)d_bases, base_mont, d_scalars, plan.n / 4,
+                                (Affine<fp2_t>*)b.conv, b.gsc, st));
+            bases = b.conv;
+            d_scalars = b.gsc;
+        } else {
+            set_error("msm: the psi split is for G2 only");
             return ACE_E_ARG;
         }
     } else if (!base_mont) {

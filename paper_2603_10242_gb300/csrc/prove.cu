@@ -1116,6 +1116,20 @@ int ace_debug_glv_split(const ace_fr* k, uint32_t out[10]) {
     return glv_split(x, out, &out[4], out + 5, &out[9]) ? ACE_OK : ACE_E_ARG;
 }
 
+int ace_debug_gls_split(const ace_fr* k, uint32_t out[16]) {
+    if (!k || !out) return ACE_E_ARG;
+    fr_t x;
+    memcpy(x.v, k->l, 32);
+    if (fe_geq_mod(x)) return ACE_E_ARG;
+    uint32_t mag[4][3], neg[4];
+    if (!gls_split_limbs(x.v, mag, neg)) return ACE_E_INTERNAL;
+    for (int i = 0; i < 4; i++) {
+        for (int l = 0; l < 3; l++) out[4 * i + l] = mag[i][l];
+        out[4 * i + 3] = neg[i];
+    }
+    return ACE_OK;
+}
+
 int ace_debug_wnaf5(const uint32_t k[4], int8_t out[132]) {
     static_assert(GLV_NAF_LEN == 132, "the declared digit count");
     if (!k || !out) return ACE_E_ARG;

@@ -176,6 +176,69 @@ def test_glv_split(lib):
         assert (k1 + k2 * lam - k) % Y.R == 0
 
 
+def _gls_constants():
+    """gx, gy of the psi map as written in glv.cuh (two Fp coefficients each)."""
+    text = open(os.path.join(os.path.dirname(__file__), "..", "paper_2603_10242_gb300", "csrc", "glv.cuh")).read()
+    vals = {}
+    for name in ("GX0", "GX1", "GY0", "GY1"):
+        m = re.search(r"#define ACE_GLS_%s \{([^}]*)\}" % name, text)
+        limbs = [int(w.strip().rstrip("u"), 16) for w in m.group(1).split(",")]
+        vals[name] = sum(v << (32 * i) for i, v in enumerate(limbs))
+    return (vals["GX0"], vals["GX1"]), (vals["GY0"], vals["GY1"])
+
+
+def test_gls_psi_constants():
+    """The constants the G2 MSM's psi uses satisfy their definitions and make
+    psi(x, y) = (conj(x) gx, conj(y) gy) the multiplication by lambda = 6 x^2
+    on G2 points, the identity the split relies on."""
+    x = 4965661367192848881
+    assert 36 * x**4 + 36 * x**3 + 18 * x**2 + 6 * x + 1 == Y.R
+    assert 36 * x**4 + 36 * x**3 + 24 * x**2 + 6 * x + 1 == Y.P
+    gx, gy = _gls_constants()
+
+    def f2_pow(a, e):
+        r = (1, 0)
+        while e:
+            if e & 1:
+                r = Y.f2_mul(r, a)
+            a = Y.f2_mul(a, a)
+            e >>= 1
+        return r
+
+    assert gx == f2_pow((9, 1), (Y.P - 1) // 3) and gy == f2_pow((9, 1), (Y.P - 1) // 2)
+    lam = 6 * x * x
+    for k in (1, 7, 123456789, Y.R - 2):
+        q = Y.g2_mul(Y.G2, k)
+        conj = lambda a: (a[0], (-a[1]) % Y.P)
+        psi = (Y.f2_mul(conj(q[0]), gx), Y.f2_mul(conj(q[1]), gy))
+        assert Y.g2_on_curve(psi) and psi == Y.g2_mul(q, lam)
+
+
+def test_gls_split(lib):
+    """k = k0 + k1 lambda + k2 lambda^2 + k3 lambda^3 (mod r) with every
+    |k_i| < 2^66, the bound the G2 plan's 67-bit digit windows assume."""
+    import random
+    x = 4965661367192848881
+    lam = 6 * x * x
+    f = lib.ace_debug_gls_split
+    f.restype = ctypes.c_int
+    rng = random.Random(13)
+    worst = 0
+    ks = [0, 1, 2, Y.R - 1, Y.R // 2, lam, lam * lam % Y.R, x, (1 << 253) + 5]
+    for k in ks + [rng.randrange(Y.R) for _ in range(400)]:
+        out = (ctypes.c_uint32 * 16)()
+        assert f(k.to_bytes(32, "little"), out) == 0
+        parts = []
+        for i in range(4):
+            mag = out[4 * i] | (out[4 * i + 1] << 32) | (out[4 * i + 2] << 64)
+            parts.append(-mag if out[4 * i + 3] else mag)
+        assert all(abs(v) < 1 << 66 for v in parts)
+        assert sum(v * pow(lam, i, Y.R) for i, v in enumerate(parts)) % Y.R == k
+        worst = max(worst, max(abs(v) for v in parts))
+    assert worst.bit_length() <= 66
+    assert f((Y.R).to_bytes(32, "little"), (ctypes.c_uint32 * 16)()) != 0
+
+
 def test_wnaf5_digits(lib):
     """The width-5 NAF of the variable-base term's 128-bit GLV halves: the
     digits rebuild k, each is 0 or odd with |d| <= 15, and no five
@@ -216,13 +279,15 @@ def test_msm_plan_pinned_choices(lib, n, kind, c):
     assert ace.msm_plan(n, kind)["c"] == c
 
 
-@pytest.mark.parametrize("kind", [ace.MSM_FULL, ace.MSM_TABLED, ace.MSM_GLV])
+@pytest.mark.parametrize("kind", [ace.MSM_FULL, ace.MSM_TABLED, ace.MSM_GLV, ace.MSM_GLS])
 def test_msm_plan_invariants(lib, kind):
     """Digit windows cover the scalar bits with no carry out of the top
-    window (254-bit scalars: c K >= 255; GLV halves below 2^127: c K >= 128),
-    the GLV plan runs 2n points with about half the windows, segments tile
-    the buckets, and the {0,1} window's virtual buckets stay within B."""
-    bits = 128 if kind == ace.MSM_GLV else 255
+    window (254-bit scalars: c K >= 255; GLV halves below 2^127: c K >= 128;
+    the parts of the G2 split below 2^66: c K >= 67), the GLV plan runs 2n
+    points with about half the windows and the G2 split 4n points, segments
+    tile the buckets, and the {0,1} window's virtual buckets stay within B."""
+    bits = {ace.MSM_GLV: 128, ace.MSM_GLS: 67}.get(kind, 255)
+    mult = {ace.MSM_GLV: 2, ace.MSM_GLS: 4}.get(kind, 1)
     for lg in range(4, 26):
         for n in (1 << lg, (1 << lg) - 3, 3 * (1 << lg) // 2):
             for force in (0, 6, 11, 20):
@@ -239,7 +304,7 @@ def test_msm_plan_invariants(lib, kind):
                 assert p["windows"] == (2 if kind == ace.MSM_TABLED else K + 1)
                 ob = p["ones_buckets"]
                 assert ob & (ob - 1) == 0 and 1 <= ob <= p["B"]
-                assert p["points"] == ((2 * n) if kind == ace.MSM_GLV else n) & 0xFFFFFFFF
+                assert p["points"] == (mult * n) & 0xFFFFFFFF
     with pytest.raises(ace.AceError):
         ace.msm_plan(1000, kind, 5)
     with pytest.raises(ace.AceError):

@@ -306,6 +306,31 @@ def test_msm_g2_sparse_dlog():
     assert gu.host(out) == O.g2_mul(O.g2_generator(), s)
 
 
+@pytest.mark.parametrize("n,c,dist", [(1, 6, "uniform"), (7, 9, "sparse"), (333, 11, "uniform"),
+                                      (1 << 12, 13, "sparse"), ((1 << 14) + 3, 17, "uniform"),
+                                      ((1 << 15) - 1, 20, "uniform")])
+def test_msm_g2_psi_split_windows(n, c, dist):
+    """The G2 MSM over the four-way psi split (points psi^t(Q_i), parts below
+    2^66) with forced windows, every digit kernel width from the smallest to
+    the largest, ragged sizes and both scalar distributions, against the
+    discrete-log sum computed on the host; canonical scalars >= r (reduced
+    mod r first) included."""
+    cx = gu.ctx()
+    kb = inputs.sample_fr(40 + c, inputs.PURPOSE["bases"], n)
+    sc = inputs.sample_scalars(60 + c, n, dist)
+    ss = inputs.limbs_to_int(sc)
+    if n >= 7:
+        ss[3] = ss[3] + R if ss[3] + R < 1 << 256 else ss[3]  # a scalar above r
+        ss[5] = 0
+        ss[6] = R - 1
+    bases = gu.empty(128 * n)
+    cx.g2_fixed_base(gu.dev(kb), n, bases, ace.FORM_MONT)
+    out = gu.empty(128)
+    cx.msm_g2_gls_window(bases, gu.dev(gu.ints_bytes(ss)), n, c, out, ace.FORM_MONT)
+    s = sum(a * b for a, b in zip(inputs.limbs_to_int(kb), ss)) % R
+    assert gu.host(out) == O.g2_mul(O.g2_generator(), s)
+
+
 NTT_KINDS = {0: "ntt", 1: "intt", 2: "coset_ntt", 3: "coset_intt"}
 
 

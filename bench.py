@@ -534,7 +534,7 @@ def batch_sizes(base_seed: int, k: int):
 
 
 def run_batch_workload(args):
-    """BASELINE config 4: 64 independent proofs of uneven sizes (2^12..2^18
+    """The batched workload: 64 independent proofs of uneven sizes (2^12..2^18
     rows), each with its own circuit, key and seed; one batch call (proofs
     pipelined over proving slots) against one proof per call."""
     import torch
@@ -691,7 +691,7 @@ SINGLE_CIRCUIT = (10, 1 << 10, 4, 0, 0)  # 4 permutations + chain to 2^10 rows
 
 
 def run_single(args):
-    """BASELINE config 1: the plain single proof of the 2^10 circuit (4
+    """The single-proof workload: the plain proof of the 2^10 circuit (4
     Poseidon-style permutations and the chain), seed 1 for the circuit,
     witness, toxic waste and (r, s).  One proof per call: per-call latency
     from the host (witness already on the device, proof bytes back on the
@@ -808,7 +808,7 @@ def serve_class_params(log_n):
 
 
 def run_serve(args):
-    """BASELINE config 5: Poisson arrivals (mean 400 ms) of block-proof jobs
+    """The served workload: Poisson arrivals (mean 400 ms) of block-proof jobs
     with 1,000..16,000 transactions, each proved under the smallest size class
     (2^19..2^23) that holds it, by the continuous-batching server; keys of all
     classes resident.  Reports p50/p99 latency (submission -> proof bytes on
@@ -1005,10 +1005,11 @@ def run_case(args):
 
 
 def run_sweep(args):
-    """BASELINE config 3, the kernel sweep: G1 MSM at 2^16..2^24 points (bases
-    k_i G stored affine in Montgomery form, k_i seeded) in the uniform and the
-    70%-{0,1} scalar distributions, and the Fr NTT, inverse NTT and coset NTT
-    at 2^16..2^24 elements (uniform inputs).  Every timed call is bracketed by
+    """The kernel sweep: G1 MSM at 2^16..2^24 points (bases k_i G stored
+    affine in Montgomery form, k_i seeded) in the uniform and the 70%-{0,1}
+    scalar distributions, the G2 MSM at 2^12..2^18 points (uniform), and the
+    Fr NTT, inverse NTT and coset NTT at 2^16..2^24 elements (uniform inputs),
+    alone and in the prover's three-array shape.  Every timed call is bracketed by
     CUDA events on the launching stream; a 256 MiB buffer (larger than the
     129 MB L2) is written between timed calls, so no call starts with its
     inputs in L2.  Sizes are prefixes of one seeded stream per distribution."""
@@ -1073,6 +1074,25 @@ def run_sweep(args):
     del bases
     torch.cuda.empty_cache()
 
+    # G2 MSM (the generic entry point: the psi split up to 2^16 points,
+    # full-width scalars above), uniform scalars
+    g2_rows = []
+    n2 = 1 << 18
+    kb2 = inputs.sample_fr(21, inputs.PURPOSE["bases"], n2)
+    bases2 = torch.empty(128 * n2, dtype=torch.uint8, device=dev)
+    ctx.g2_fixed_base(torch.from_numpy(kb2.view(np.uint8).reshape(-1)).to(dev), n2, bases2, ace.FORM_MONT)
+    sc2 = torch.from_numpy(inputs.sample_scalars(21, n2, "uniform").view(np.uint8).reshape(-1)).to(dev)
+    out2 = torch.empty(128, dtype=torch.uint8, device=dev)
+    for lg in (12, 14, 16, 18):
+        n = 1 << lg
+        t = timed(lambda: ctx.msm_g2(bases2, sc2, n, out2, ace.FORM_MONT))
+        split = n <= 1 << 16
+        g2_rows.append({"log_n": lg, "scalars": "uniform", "ms": t * 1000.0, "points_per_s": n / t,
+                        "plan": "psi split, 4n points" if split else "full-width scalars",
+                        "c": ace.msm_plan(n, ace.MSM_GLS if split else ace.MSM_FULL)["c"]})
+    del bases2, sc2
+    torch.cuda.empty_cache()
+
     ntt_rows = []
     kinds = {0: "ntt", 1: "intt", 2: "coset_ntt", 3: "coset_intt"}
     vals = torch.from_numpy(inputs.sample_fr(24, 7, 1 << 24).view(np.uint8).reshape(-1)).to(dev)
@@ -1112,7 +1132,7 @@ def run_sweep(args):
         "workload": "kernel_sweep_msm_g1_ntt_2p16_2p24", "curve": "BN254", "reps": reps,
         "cpu_baseline": cpu,
         "timing": "median of reps, CUDA events per call, L2 flushed (256 MiB write) before each call",
-        "msm_g1": msm_rows, "ntt": ntt_rows, "ntt_qap_batch": ntt_batch_rows,
+        "msm_g1": msm_rows, "msm_g2": g2_rows, "ntt": ntt_rows, "ntt_qap_batch": ntt_batch_rows,
         "roofline": {"imad_peak_T_per_s": peak_imad / 1e12, "hbm_peak_gbs": hbm_peak,
                      "msm": f"{IMAD_PER_G1_MADD} IMAD per bucket addition (algorithmic, bucket additions only)",
                      "ntt": "64 B per element (read + write once) against HBM; "

@@ -504,7 +504,7 @@ int ace_autotune_ntt(ace_ctx* ctx, uint32_t log_min, uint32_t log_max, double* r
  * two stage layouts (a proof's MSMs spread over its slot's auxiliary
  * streams, or every stage of a proof on one stream with proofs overlapping
  * across slots only), and keep for ace_prove_batch, among the configurations
- * within 2% of the fastest, the one-stream layout first and then the fewest
+ * within 1% of the fastest, the one-stream layout first and then the fewest
  * slots (fewer kernels share the SMs and fewer slots hold scratch, at the same
  * throughput).  The proofs do not change.  1 <= max_slots <= 16 (ACE_E_ARG
  * otherwise).  report (optional, 2 x max_slots doubles): ms per batch for

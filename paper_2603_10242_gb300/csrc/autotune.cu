@@ -220,22 +220,30 @@ int ace_autotune_batch_slots(ace_ctx* ctx, const ace_pk* pk, const ace_fr* d_z, 
             ctx->batch_slots = q;
             ACE_TRY(prove_batch_on_slots(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
                                     status.data()));
-            auto t0 = std::chrono::steady_clock::now();
-            ACE_TRY(prove_batch_on_slots(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
-                                    status.data()));
-            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            // the faster of two timed batches (one alone varied by about 1%)
+            double ms = 1e30;
+            for (int rep = 0; rep < 2; rep++) {
+                auto t0 = std::chrono::steady_clock::now();
+                ACE_TRY(prove_batch_on_slots(ctx, k, pks.data(), zs.data(), rs.data(), ss.data(), proofs.data(),
+                                        status.data()));
+                const double t =
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                if (t < ms) ms = t;
+            }
             if (report) report[layout * max_slots + q - 1] = ms;
             ms_of[layout][q] = ms;
             if (ms < best_ms) best_ms = ms;
         }
     }
-    // among the configurations within 2% of the fastest: one stream per proof
+    // among the configurations within 1% of the fastest: one stream per proof
     // first (its kernels share the SMs with fewer others, at the same
-    // throughput), then the fewest slots (each holds a proof's scratch)
+    // throughput), then the fewest slots (each holds a proof's scratch).  A
+    // 2% band let 2 slots win at 2^20 block proofs, 2% slower than 3 in the
+    // timed batch.
     int best_layout = 0, best = max_slots;
     for (int layout = 1, found = 0; layout >= 0 && !found; layout--)
         for (int q = 1; q <= max_slots && !found; q++)
-            if (ms_of[layout][q] <= 1.02 * best_ms) {
+            if (ms_of[layout][q] <= 1.01 * best_ms) {
                 best_layout = layout;
                 best = q;
                 found = 1;

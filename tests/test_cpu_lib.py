@@ -331,3 +331,16 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert L.ace_autotune_batch_slots(None, None, None, 1, 1, None) == -1
     assert "NULL" in L.ace_last_error().decode() or "bad argument" in L.ace_last_error().decode()
     assert ace.ERRORS[-8] == "ACE_E_INTERNAL"
+    # the G2 split's window diagnostic: NULL context, window out of range,
+    # too many points, unknown base form (all before any CUDA call)
+    out = ctypes.create_string_buffer(128)
+    f = L.ace_msm_g2_gls_window
+    assert f(None, vp(1), 1, vp(1), 4, 11, out, None) == -1
+    assert f(vp(1), vp(1), 1, vp(1), 4, 5, out, None) == -1
+    assert f(vp(1), vp(1), 1, vp(1), 4, 21, out, None) == -1
+    assert f(vp(1), vp(1), 1, vp(1), 1 << 29, 11, out, None) == -1
+    assert f(vp(1), vp(1), 7, vp(1), 4, 11, out, None) == -1
+    assert "ace_msm_g2_gls_window" in L.ace_last_error().decode()
+    assert L.ace_debug_gls_split(None, None) == -1
+    assert L.ace_debug_wnaf5(None, None) == -1
+    assert L.ace_debug_msm_plan(16, 4, 0, (ctypes.c_uint32 * 8)()) == -1
